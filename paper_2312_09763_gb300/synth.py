@@ -1,0 +1,179 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module draws random inputs only: antenna layouts, source catalogues,
+beam grids, LST and frequency lists.  It holds none of the simulator's
+arithmetic, imports nothing else from this package, and feeds the same arrays
+to the CUDA path and to the FP64 oracle.
+
+Every quantity draws from its own stream, keyed by (20231209 + workload id,
+quantity name), so that changing one quantity never shifts another.
+
+The paper's own inputs (a GLEAM-like catalogue, the GSM, the CST HERA beam;
+Sec. 5.1) are not available; these stand in for them with the counts, flux
+distributions and beam widths of the workloads below.
+
+Workloads (all angles in radians, frequencies in Hz, lengths in metres):
+
+0. tiny: 10 antennas uniform in a 50 m square (Up = 0); 1000 sources uniform on
+   the sphere, dN/dS ~ S^-1.6 on [0.1, 10] Jy, flat spectra; 1 channel at
+   150 MHz; 4 LSTs spanning 10 min; latitude -30.7 deg; analytic Gaussian
+   E-field beam, FWHM 10 deg.
+1. HERA-like: 350 antennas, the triangular-lattice points (14.6 m spacing)
+   nearest the origin; 1e5 sources uniform on the sphere, dN/dS ~ S^-1.6 on
+   [0.01, 100] Jy, spectral index ~ N(-0.8, 0.2) about 150 MHz; 64 channels
+   centred in 100-200 MHz; 60 LSTs one minute apart; scalar gridded beam on a
+   1 deg x 1 deg az/za grid and a 1 MHz frequency grid (98-202 MHz), a
+   Gaussian with FWHM 10 deg x (150 MHz / nu) times (1 + 0.05 r), r a seeded
+   smooth ripple with |r| <= 1.
+"""
+from __future__ import annotations
+
+import zlib
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+SEED_BASE = 20231209
+DEG = np.pi / 180.0
+SIDEREAL_MINUTE = 2.0 * np.pi / 1440.0  # radians of LST per minute of sidereal time
+HERA_LAT = -30.7 * DEG
+
+
+def rng(workload: int, quantity: str) -> np.random.Generator:
+    """Independent generator for one quantity of one workload."""
+    key = zlib.crc32(quantity.encode("utf-8"))
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE + workload, key])))
+
+
+# ------------------------------------------------------------------ arrays
+
+def square_array(n: int, side: float, g: np.random.Generator) -> np.ndarray:
+    """n antennas uniform in a side x side square about the origin, Up = 0."""
+    enu = np.zeros((n, 3))
+    enu[:, :2] = g.uniform(-side / 2, side / 2, size=(n, 2))
+    return enu
+
+
+def hex_array(n: int, spacing: float) -> np.ndarray:
+    """The n points of a triangular lattice nearest the origin (ties broken by
+    angle), Up = 0.  A HERA-like compact, highly redundant layout."""
+    r = int(np.ceil(np.sqrt(n))) + 2
+    i, j = np.meshgrid(np.arange(-r, r + 1), np.arange(-r, r + 1), indexing="ij")
+    e = spacing * (i + 0.5 * j)
+    no = spacing * (np.sqrt(3.0) / 2.0) * j
+    e, no = e.ravel(), no.ravel()
+    rad = np.round(np.hypot(e, no) / spacing, 9)
+    ang = np.round(np.mod(np.arctan2(no, e), 2 * np.pi), 9)
+    order = np.lexsort((ang, rad))[:n]
+    enu = np.zeros((n, 3))
+    enu[:, 0], enu[:, 1] = e[order], no[order]
+    return enu
+
+
+# ------------------------------------------------------------------- skies
+
+def uniform_sphere(n: int, g: np.random.Generator):
+    """(ra, dec) uniform on the sphere."""
+    ra = g.uniform(0.0, 2.0 * np.pi, size=n)
+    dec = np.arcsin(g.uniform(-1.0, 1.0, size=n))
+    return ra, dec
+
+
+def powerlaw_flux(n: int, smin: float, smax: float, gamma: float, g: np.random.Generator) -> np.ndarray:
+    """Fluxes with dN/dS ~ S^-gamma on [smin, smax] (inverse CDF)."""
+    a, b = smin ** (1.0 - gamma), smax ** (1.0 - gamma)
+    u = g.uniform(0.0, 1.0, size=n)
+    return (a + u * (b - a)) ** (1.0 / (1.0 - gamma))
+
+
+# ------------------------------------------------------------------- beams
+
+def ripple_field(az, za, nu_norm, g: np.random.Generator, n_terms: int = 8):
+    """Seeded smooth ripple r(az, za, nu) with |r| <= 1.
+
+    Terms are c_m sin(za)^k_m cos(k_m az + phi_m) cos(l_m za) cos(w_m nu + psi_m)
+    with sum |c_m| = 1.  The sin(za)^k factor makes each azimuthal harmonic
+    regular at the zenith pole."""
+    k = g.integers(0, 4, size=n_terms)
+    l = g.uniform(0.5, 3.0, size=n_terms)
+    w = g.uniform(0.5, 4.0, size=n_terms)
+    phi = g.uniform(0, 2 * np.pi, size=n_terms)
+    psi = g.uniform(0, 2 * np.pi, size=n_terms)
+    c = g.uniform(-1.0, 1.0, size=n_terms)
+    c = c / np.sum(np.abs(c))
+    r = np.zeros(np.broadcast(az, za, nu_norm).shape)
+    for m in range(n_terms):
+        r = r + c[m] * np.sin(za) ** k[m] * np.cos(k[m] * az + phi[m]) * np.cos(l[m] * za) \
+            * np.cos(w[m] * nu_norm + psi[m])
+    return r
+
+
+def gaussian_ripple_grid(nu_grid: np.ndarray, n_za: int, n_az: int, fwhm_ref: float,
+                         nu_ref: float, ripple: float, g: np.random.Generator) -> np.ndarray:
+    """Scalar beam grid, complex64 [1][1][1][nu][za][az]: a Gaussian with
+    FWHM(nu) = fwhm_ref * nu_ref / nu times (1 + ripple * r)."""
+    za = np.arange(n_za) * (np.pi / 2 / (n_za - 1))
+    az = np.arange(n_az) * (2 * np.pi / n_az)
+    nun = (nu_grid - nu_ref) / nu_ref
+    NU, ZA, AZ = np.meshgrid(nun, za, az, indexing="ij")
+    fwhm = fwhm_ref * nu_ref / nu_grid
+    env = np.exp(-4.0 * np.log(2.0) * ZA ** 2 / (fwhm[:, None, None] ** 2))
+    vals = env * (1.0 + ripple * ripple_field(AZ, ZA, NU, g))
+    return vals.astype(np.complex64).reshape(1, 1, 1, len(nu_grid), n_za, n_az)
+
+
+# ---------------------------------------------------------------- workloads
+
+@dataclass
+class Workload:
+    """Inputs of one workload; beam is ("gaussian", fwhm) or
+    ("grid", values c64 [beam][feed][ax][nu][za][az], nu0, dnu, dza, daz, interp)."""
+    name: str
+    ra: np.ndarray
+    dec: np.ndarray
+    flux_ref: np.ndarray
+    spec_idx: Optional[np.ndarray]
+    nu_ref: float
+    enu: np.ndarray
+    lat: float
+    beam: tuple
+    lsts: np.ndarray
+    freqs: np.ndarray
+    beam_idx: Optional[np.ndarray] = None
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def n_ant(self) -> int:
+        return self.enu.shape[0]
+
+    @property
+    def n_src(self) -> int:
+        return self.ra.size
+
+
+def tiny(n_ant: int = 10, n_src: int = 1000, n_times: int = 4) -> Workload:
+    """Workload 0 (see module docstring)."""
+    enu = square_array(n_ant, 50.0, rng(0, "antennas"))
+    ra, dec = uniform_sphere(n_src, rng(0, "positions"))
+    flux = powerlaw_flux(n_src, 0.1, 10.0, 1.6, rng(0, "flux"))
+    lsts = np.arange(n_times) * (10.0 * SIDEREAL_MINUTE / max(n_times - 1, 1))
+    return Workload("tiny: 10 ant x 1000 src x 1 ch x 4 t, gaussian beam",
+                    ra, dec, flux, None, 150e6, enu, HERA_LAT,
+                    ("gaussian", 10.0 * DEG), lsts, np.array([150e6]))
+
+
+def hera_like(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times: int = 60,
+              n_za: int = 91, n_az: int = 360) -> Workload:
+    """Workload 1 (see module docstring); smaller sizes give its test cases."""
+    enu = hex_array(n_ant, 14.6)
+    ra, dec = uniform_sphere(n_src, rng(1, "positions"))
+    flux = powerlaw_flux(n_src, 0.01, 100.0, 1.6, rng(1, "flux"))
+    alpha = rng(1, "spectral_index").normal(-0.8, 0.2, size=n_src)
+    freqs = 100e6 + (np.arange(n_chan) + 0.5) * (100e6 / n_chan)
+    lsts = np.arange(n_times) * SIDEREAL_MINUTE
+    nu_grid = 98e6 + np.arange(105) * 1e6
+    grid = gaussian_ripple_grid(nu_grid, n_za, n_az, 10.0 * DEG, 150e6, 0.05, rng(1, "beam_ripple"))
+    beam = ("grid", grid, 98e6, 1e6, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
+    return Workload(f"hera_like: {n_ant} ant x {n_src} src x {n_chan} ch x {n_times} t, bicubic grid beam",
+                    ra, dec, flux, alpha, 150e6, enu, HERA_LAT, beam, lsts, freqs)
