@@ -1,0 +1,179 @@
+/*
+ * matvis.h -- C-ABI of a single-GPU (sm_103a) matrix-based visibility
+ * simulator after Kittiwisit et al., "matvis: a matrix-based visibility
+ * simulator for fast forward modelling of many-element 21 cm arrays"
+ * (arXiv:2312.09763).
+ *
+ * For every (time, frequency) instance the library runs Algorithm 2 of the
+ * paper (Sec. 3.1) on the GPU:
+ *   (i)   rotate the sources to East-North-Up with the FP64 matrix R(t) of
+ *         eq. "rotation" (Sec. 2.3) and drop those with Up <= 0;
+ *   (ii)  evaluate the beam of every unique antenna type at the live sources
+ *         (analytic Gaussian, or a gridded beam interpolated as Sec. 2.4);
+ *   (iii) form the per-antenna phase (nu/c) x_a . s_hat in FP64 and reduce it
+ *         exactly modulo one turn;
+ *   (iv)  build Z[(a,p),(s,k)] = sqrt(I_s) A^{pk}_{beta(a)}(s) exp(-2 pi i phase)
+ *         (eq. "littlez"; Sec. 2.2);
+ *   (v)   expand V = Z Z^dagger (eq. "zz") on the tensor cores (BF16 x3 split
+ *         precision, FP32 accumulation) or on the CUDA cores (FP32).
+ *
+ * Conventions (all calls):
+ *   - Every call returns an mv_status; no C++ exception crosses this ABI.
+ *     On failure mv_last_error() describes the problem (thread-local string,
+ *     valid until the next call on the same thread).
+ *   - Input arrays are borrowed for the duration of the call and copied; the
+ *     caller keeps ownership.  Output buffers are caller-owned.
+ *   - A context is bound to one device and is not thread-safe.  Work is
+ *     ordered on the stream given to mv_simulate (NULL = the context's own
+ *     stream).
+ *   - Angles are radians, lengths metres, frequencies Hz, fluxes Jy.
+ *   - Output V for one instance is the full N x N Hermitian matrix,
+ *     N = n_feed * n_ant, complex64 (interleaved re, im float), row-major,
+ *     row/column index (a, p) = a * n_feed + p; V[a][b] = sum_s Z_a conj(Z_b),
+ *     i.e. the baseline is b_ab = x_a - x_b (Sec. 2.2, fringe factorisation).
+ */
+#ifndef MATVIS_GB300_H
+#define MATVIS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mv_ctx mv_ctx; /* opaque; owns all device state of one simulator */
+
+typedef enum {
+    MV_OK = 0,
+    MV_ERR_ARG = 1,            /* invalid argument (size, range, NaN, negative flux, ...) */
+    MV_ERR_OOM = 2,            /* device or host allocation failed */
+    MV_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    MV_ERR_STATE = 4,          /* call out of order (e.g. simulate before set-up) */
+    MV_ERR_DEVICE_TIMEOUT = 5, /* a bounded device-side wait gave up; results invalid */
+    MV_ERR_UNSUPPORTED = 6     /* feature not available on this device / build */
+} mv_status;
+
+typedef enum {
+    MV_PREC_FP32 = 0,   /* Z and V = Z Z^H in FP32 on CUDA cores */
+    MV_PREC_BF16X3 = 1, /* Z split as hi + lo BF16; hi hi^T + hi lo^T + lo hi^T on tcgen05, FP32 accumulate */
+    MV_PREC_FP16X3 = 2  /* as BF16X3 with FP16 halves (11-bit each) after an exact per-instance
+                           power-of-two scaling of Z into FP16 range */
+} mv_precision;
+
+typedef enum {
+    MV_INTERP_CUBIC = 0,    /* Keys cubic convolution in az, za and frequency */
+    MV_INTERP_BILINEAR = 1  /* linear in az and za, Keys cubic in frequency */
+} mv_interp;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer or NULL; both run on the host thread that called
+ * into the library, outside any kernel. */
+typedef struct {
+    void *(*alloc)(size_t bytes, int device, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, int device, void *stream, void *user);
+    void *user;
+} mv_allocator;
+
+typedef struct {
+    int interp;                 /* mv_interp for gridded beams (default cubic) */
+    int max_batch;              /* channels of one time processed per launch (0 = auto) */
+    int herk_flush_kblocks;     /* tensor-core HERK: 64-column k-blocks accumulated in one
+                                   TMEM buffer before it is added into the FP32 running
+                                   sum (0 = auto = 4) */
+    int herk_split;             /* split of the source axis across CTAs (0 = auto) */
+    mv_allocator allocator;     /* alloc == NULL: cudaMalloc / cudaFree */
+} mv_options;
+
+/* Fill *opt with defaults. */
+void mv_default_options(mv_options *opt);
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * Fails with MV_ERR_UNSUPPORTED unless the device is compute capability 10.3. */
+mv_status mv_create(mv_ctx **out, int device, const mv_options *opt);
+
+/* Release every device buffer of the context.  NULL is accepted. */
+void mv_destroy(mv_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mv_last_error(void);
+
+/* Sky model (Sec. 3.1 inputs: X_eq from eq. "xeq", intensities I >= 0).
+ * ra, dec: [n_src] radians.  flux_ref: [n_src] Jy at nu_ref, finite and >= 0
+ * (the paper requires a positive intensity vector).  spec_idx: [n_src]
+ * spectral indices alpha (NULL = 0), I_s(nu) = flux_ref_s (nu / nu_ref)^alpha_s.
+ * n_src >= 1.  Host pointers; copied. */
+mv_status mv_init_sky(mv_ctx *ctx, int64_t n_src, const double *ra, const double *dec,
+                      const double *flux_ref, const double *spec_idx, double nu_ref);
+
+/* Analytic unpolarised Gaussian E-field beam, the same for every antenna:
+ * A(za) = exp(-4 ln2 za^2 / fwhm^2) (Sec. 2.4 analytic beams).  fwhm > 0. */
+mv_status mv_set_beam_gaussian(mv_ctx *ctx, double fwhm_rad);
+
+/* Gridded beams (Sec. 2.4): values complex64 [n_beam][n_feed][n_ax][n_nu][n_za][n_az]
+ * (interleaved re, im), az-fastest.  Axes: nu_m = nu0 + m dnu, za_i = i dza
+ * (the zenith is the grid's pole, row 0), az_j = j daz with n_az * daz = 2 pi
+ * (periodic; n_az even).  n_feed, n_ax in {1, 2}; n_ax = 2 means the columns
+ * are (theta, phi) E-field components, which change sign across the pole.
+ * Interpolation per mv_options.interp.  Rows past the last za node repeat the
+ * last row.  Host pointer; copied. */
+mv_status mv_set_beam_grid(mv_ctx *ctx, int n_beam, int n_feed, int n_ax, int n_nu, int n_za,
+                           int n_az, const float *values_c64, double nu0, double dnu,
+                           double dza, double daz);
+
+/* Antenna layout (Sec. 3.1 inputs D and a_i): enu [n_ant][3] East-North-Up
+ * metres; beam_idx [n_ant] index of each antenna's unique beam (NULL = all
+ * 0); latitude of the array.  Host pointers; copied. */
+mv_status mv_set_antennas(mv_ctx *ctx, int n_ant, const double *enu, const int32_t *beam_idx,
+                          double latitude_rad);
+
+/* Simulate n_t x n_nu instances (Algorithm 2 for every LST and frequency).
+ * lst: [n_t] local sidereal times (radians; they define R(t), Sec. 3.1);
+ * nu: [n_nu] Hz, inside the beam grid's cubic margin for gridded beams.
+ * V: complex64 [n_t][n_nu][N][N]; a device pointer if V_on_device, else host
+ * memory written before the call returns.  stream: cudaStream_t or NULL.
+ * With V on the device the call returns once the work is queued; device-side
+ * wait timeouts are reported by mv_check_device_status. */
+mv_status mv_simulate(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const double *nu,
+                      mv_precision prec, void *V, int V_on_device, void *stream);
+
+/* Simulate an explicit list of (lst, nu) pairs: V complex64 [n_pairs][N][N]. */
+mv_status mv_simulate_pairs(mv_ctx *ctx, int n_pairs, const double *lst, const double *nu,
+                            mv_precision prec, void *V, int V_on_device, void *stream);
+
+/* Synchronise the context's work and report (and clear) a device-side error
+ * flag (MV_ERR_DEVICE_TIMEOUT) or a pending CUDA error. */
+mv_status mv_check_device_status(mv_ctx *ctx, void *stream);
+
+/* Number of live (Up > 0) sources at each LST, as the last mv_simulate or
+ * mv_simulate_pairs call computed them on the device (its instances, in
+ * order): out [n] int64.  Synchronises. */
+mv_status mv_last_live_counts(mv_ctx *ctx, int n, int64_t *out);
+
+/* Number of kernel launches the last simulate call issued. */
+int64_t mv_last_launch_count(mv_ctx *ctx);
+
+/* Kernel timing (the paper profiles each step of Algorithm 2 separately,
+ * Sec. 4.1).  When enabled, every launch is bracketed by two CUDA events
+ * recorded on the stream it is launched on; counters accumulate across
+ * simulate calls until the next mv_profile_enable.  Kinds follow the steps
+ * of Algorithm 2. */
+typedef enum {
+    MV_KERNEL_CULL = 0,    /* step (i): rotation, horizon cut, compaction */
+    MV_KERNEL_BEAM = 1,    /* step (ii): beam planes and beam x sqrt(I) at live sources */
+    MV_KERNEL_ZBUILD = 2,  /* steps (iii)-(iv): FP64 phase, Z */
+    MV_KERNEL_HERK = 3,    /* step (v): V = Z Z^dagger */
+    MV_KERNEL_KINDS = 4
+} mv_kernel_kind;
+
+/* enable != 0 switches timing on and clears the counters; 0 switches it off. */
+mv_status mv_profile_enable(mv_ctx *ctx, int enable);
+
+/* Synchronise and read the counters of one kind: number of launches and the
+ * sum of their event-measured durations in milliseconds. */
+mv_status mv_profile_read(mv_ctx *ctx, int kind, int64_t *launches, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MATVIS_GB300_H */

@@ -1,0 +1,251 @@
+"""ctypes binding of the C-ABI in ``include/matvis.h`` (argument marshalling only).
+
+Every step of the simulation runs in the CUDA library.  Output V lands in a
+torch CUDA tensor (complex64 ``[n_t, n_nu, N, N]``) or, with ``host=True``,
+in a numpy array written by the library's device-to-host copy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmatvis_gb300.so")
+
+MV_OK = 0
+_STATUS = {0: "MV_OK", 1: "MV_ERR_ARG", 2: "MV_ERR_OOM", 3: "MV_ERR_CUDA", 4: "MV_ERR_STATE",
+           5: "MV_ERR_DEVICE_TIMEOUT", 6: "MV_ERR_UNSUPPORTED"}
+PRECISION = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
+_CUDA_STREAM_LEGACY = 0x1
+INTERP = {"cubic": 0, "bilinear": 1}
+
+# exported symbols of include/matvis.h
+EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv_init_sky",
+           "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas", "mv_simulate",
+           "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts", "mv_last_launch_count",
+           "mv_profile_enable", "mv_profile_read"]
+KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
+
+
+class MatvisError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC), ("free", _FREE), ("user", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("interp", ctypes.c_int), ("max_batch", ctypes.c_int), ("herk_flush_kblocks", ctypes.c_int),
+                ("herk_split", ctypes.c_int), ("allocator", _Allocator)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2312_09763_gb300._build.build() "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.mv_default_options.argtypes = [ctypes.POINTER(_Options)]
+    lib.mv_default_options.restype = None
+    lib.mv_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(_Options)]
+    lib.mv_destroy.argtypes = [vp]
+    lib.mv_destroy.restype = None
+    lib.mv_last_error.restype = ctypes.c_char_p
+    lib.mv_last_error.argtypes = []
+    lib.mv_init_sky.argtypes = [vp, i64, vp, vp, vp, vp, dp]
+    lib.mv_set_beam_gaussian.argtypes = [vp, dp]
+    lib.mv_set_beam_grid.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, dp, dp, dp, dp]
+    lib.mv_set_antennas.argtypes = [vp, i32, vp, vp, dp]
+    lib.mv_simulate.argtypes = [vp, i32, vp, i32, vp, i32, vp, i32, vp]
+    lib.mv_simulate_pairs.argtypes = [vp, i32, vp, vp, i32, vp, i32, vp]
+    lib.mv_check_device_status.argtypes = [vp, vp]
+    lib.mv_last_live_counts.argtypes = [vp, i32, vp]
+    lib.mv_last_launch_count.argtypes = [vp]
+    lib.mv_last_launch_count.restype = i64
+    lib.mv_profile_enable.argtypes = [vp, i32]
+    lib.mv_profile_read.argtypes = [vp, i32, vp, vp]
+    for name in ("mv_create", "mv_init_sky", "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas",
+                 "mv_simulate", "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts",
+                 "mv_profile_enable", "mv_profile_read"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Simulator:
+    """One simulator context on one CUDA device (see include/matvis.h)."""
+
+    def __init__(self, device: int = 0, interp: str = "cubic", max_batch: int = 0, herk_flush_kblocks: int = 0,
+                 torch_allocator: bool = True):
+        import torch  # device memory and streams
+        self._torch = torch
+        self._lib = load_library()
+        self.device = device
+        opt = _Options()
+        self._lib.mv_default_options(ctypes.byref(opt))
+        opt.interp = INTERP[interp]
+        opt.max_batch = max_batch
+        opt.herk_flush_kblocks = herk_flush_kblocks
+        self._cb = None
+        if torch_allocator:
+            def _alloc(nbytes, dev, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), int(dev), stream or 0)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, dev, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb = (_ALLOC(_alloc), _FREE(_free))
+            opt.allocator.alloc, opt.allocator.free = self._cb
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        self._check(self._lib.mv_create(ctypes.byref(h), device, ctypes.byref(opt)))
+        self._h = h
+        self.n_ant = 0
+        self.n_feed = 1
+
+    def _check(self, status: int):
+        if status != MV_OK:
+            raise MatvisError(status, self._lib.mv_last_error().decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- set-up
+    def init_sky(self, ra, dec, flux_ref, spec_idx=None, nu_ref: float = 150e6):
+        ra, dec, fl = _f64(ra), _f64(dec), _f64(flux_ref)
+        si = None if spec_idx is None else _f64(spec_idx)
+        self._check(self._lib.mv_init_sky(self._h, ra.size, _p(ra), _p(dec), _p(fl), _p(si), float(nu_ref)))
+
+    def set_beam_gaussian(self, fwhm: float):
+        self._check(self._lib.mv_set_beam_gaussian(self._h, float(fwhm)))
+        self.n_feed = 1
+
+    def set_beam_grid(self, values, nu0: float, dnu: float, dza: float, daz: float):
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.complex64))
+        if v.ndim != 6:
+            raise ValueError("values must be [beam][feed][ax][nu][za][az]")
+        nb, nf, na, nn, nz, naz = v.shape
+        self._check(self._lib.mv_set_beam_grid(self._h, nb, nf, na, nn, nz, naz, _p(v), float(nu0), float(dnu),
+                                               float(dza), float(daz)))
+        self.n_feed = nf
+
+    def set_beam(self, beam: tuple):
+        """beam = ("gaussian", fwhm) or ("grid", values, nu0, dnu, dza, daz[, interp])."""
+        if beam[0] == "gaussian":
+            self.set_beam_gaussian(beam[1])
+        elif beam[0] == "grid":
+            self.set_beam_grid(*beam[1:6])
+        else:
+            raise ValueError(beam[0])
+
+    def set_antennas(self, enu, beam_idx=None, lat: float = 0.0):
+        enu = _f64(enu).reshape(-1, 3)
+        bi = None if beam_idx is None else np.ascontiguousarray(beam_idx, dtype=np.int32)
+        self._check(self._lib.mv_set_antennas(self._h, enu.shape[0], _p(enu), _p(bi), float(lat)))
+        self.n_ant = enu.shape[0]
+
+    # ------------------------------------------------------------ simulate
+    def _out(self, shape, out, host):
+        torch = self._torch
+        if host:
+            if out is None:
+                out = np.empty(shape, dtype=np.complex64)
+            if isinstance(out, np.ndarray):
+                assert out.dtype == np.complex64 and out.flags.c_contiguous and out.shape == tuple(shape)
+                return out, out.ctypes.data_as(ctypes.c_void_p), 0
+            # a (pinned) torch CPU tensor
+            assert (not out.is_cuda) and out.dtype == torch.complex64 and out.is_contiguous()
+            return out, ctypes.c_void_p(out.data_ptr()), 0
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex64, device=f"cuda:{self.device}")
+        assert out.is_cuda and out.dtype == torch.complex64 and out.is_contiguous()
+        return out, ctypes.c_void_p(out.data_ptr()), 1
+
+    def _stream(self, stream):
+        torch = self._torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        # torch's default stream is the legacy NULL stream; name it explicitly
+        # (cudaStreamLegacy) since NULL means "the context's own stream" here
+        return ctypes.c_void_p(stream.cuda_stream or _CUDA_STREAM_LEGACY)
+
+    def simulate(self, lsts: Sequence[float], freqs: Sequence[float], precision: str = "bf16x3", out=None,
+                 host: bool = False, stream=None):
+        """V[t, f] for every LST and frequency: complex64 [n_t, n_nu, N, N]."""
+        lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()
+        N = self.n_feed * self.n_ant
+        arr, ptr, on_dev = self._out((lst.size, nu.size, N, N), out, host)
+        self._check(self._lib.mv_simulate(self._h, lst.size, _p(lst), nu.size, _p(nu), PRECISION[precision], ptr,
+                                          on_dev, None if host else self._stream(stream)))
+        return arr
+
+    def simulate_pairs(self, lsts, freqs, precision: str = "bf16x3", out=None, host: bool = False, stream=None):
+        """V for explicit (lst, nu) pairs: complex64 [n_pairs, N, N]."""
+        lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()
+        if lst.size != nu.size:
+            raise ValueError("lsts and freqs must have the same length")
+        N = self.n_feed * self.n_ant
+        arr, ptr, on_dev = self._out((lst.size, N, N), out, host)
+        self._check(self._lib.mv_simulate_pairs(self._h, lst.size, _p(lst), _p(nu), PRECISION[precision], ptr,
+                                                on_dev, None if host else self._stream(stream)))
+        return arr
+
+    def check_device_status(self, stream=None):
+        self._check(self._lib.mv_check_device_status(self._h, None if stream is None else self._stream(stream)))
+
+    def last_live_counts(self, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.int64)
+        self._check(self._lib.mv_last_live_counts(self._h, n, _p(out)))
+        return out
+
+    def last_launch_count(self) -> int:
+        return int(self._lib.mv_last_launch_count(self._h))
+
+    def profile_enable(self, enable: bool = True):
+        """Time every kernel launch with CUDA events (clears the counters)."""
+        self._check(self._lib.mv_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kind: (launches, total_ms)} for cull, beam, zbuild, herk."""
+        out = {}
+        for name, k in KERNEL_KINDS.items():
+            n, ms = ctypes.c_int64(), ctypes.c_double()
+            self._check(self._lib.mv_profile_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
+            out[name] = (int(n.value), float(ms.value))
+        return out

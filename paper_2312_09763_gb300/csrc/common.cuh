@@ -1,0 +1,118 @@
+// common.cuh -- shared declarations of the matvis GB300 library (device and
+// host side).  Nothing here is part of the public C-ABI (include/matvis.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace mv {
+
+constexpr double kCLight = 299792458.0;   // m/s
+constexpr double kPi = 3.14159265358979323846;
+
+// Column padding of the Z matrix along the source axis: every instance's
+// K = n_ax * n_live is rounded up to a multiple of this (the tensor-core
+// HERK's TMEM flush granularity is a multiple of its 64-wide k-blocks).
+constexpr int kKPad = 256;
+
+// Device-side error codes written into the context's status word.
+enum DevErr : int { kDevOk = 0, kDevTimeout = 1, kDevBadArg = 2 };
+
+// ----------------------------------------------------------------- tables
+// One (time, frequency) instance of a simulate call.
+struct Inst {
+    int t;            // index into the call's distinct times (live tables)
+    int c;            // index into the call's distinct channels
+    long long v_off;  // offset of this instance's V in complex64 elements
+};
+
+// One channel of a simulate call.
+struct Chan {
+    double kappa;     // nu / c  (turns of phase per metre of path difference)
+    float ln_ratio;   // ln(nu / nu_ref)
+    int m0;           // first frequency node of the beam-grid stencil
+    float w[4];       // frequency stencil weights (Keys cubic)
+};
+
+// Live-source tables of the distinct times of a call (structure of arrays,
+// one row of pitch `pitch` per time).
+struct LiveTables {
+    double* e;        // [n_times][pitch] East component of s_hat
+    double* n;        // North
+    double* u;        // Up
+    int* idx;         // catalogue index of each live source
+    float2* azza;     // (az, za) radians, FP32
+    int* n_live;      // [n_times]
+    long long pitch;
+};
+
+// Static description of the sky / array / beam on the device.
+struct Model {
+    // sky
+    long long n_src;
+    const double* xeq;       // [3][n_src] SoA: x, y, z (eq. "xeq")
+    const float* sqrt_flux;  // [n_src] sqrt(flux at nu_ref)
+    const float* half_alpha; // [n_src] spectral index / 2
+    // array
+    int n_ant;
+    const double* ant_e;     // [n_ant]
+    const double* ant_n;
+    const double* ant_u;
+    const int* beam_idx;     // [n_ant]
+    // beam
+    int beam_kind;           // 1 gaussian, 2 grid
+    float gauss_c;           // 4 ln2 / fwhm^2
+    int n_beam, n_feed, n_ax;
+    int n_nu, n_za, n_az;
+    float dza, daz;
+    int interp;              // 0 cubic, 1 bilinear
+};
+
+// ------------------------------------------------------------ host launchers
+// (defined in the .cu files; all enqueue on `st` and return the CUDA error)
+cudaError_t launch_cull(const Model& m, const double* d_R, int n_times, LiveTables lt,
+                        int* d_counts, int* d_offsets, int blocks_per_time, cudaStream_t st,
+                        long long* launches);
+cudaError_t launch_beam_planes(const Model& m, const float2* d_grid, const Chan* d_chan, int n_chan,
+                               float2* d_planes, cudaStream_t st, long long* launches);
+// WA[slot] = sqrt(I_s) A(s) for the live sources; amax[slot] (zeroed by the
+// caller) receives max |WA| over the slot's components, as float bits.
+cudaError_t launch_wa(const Model& m, const float2* d_planes, const Chan* d_chan, const Inst* d_inst,
+                      int inst0, int n_inst, LiveTables lt, float2* d_wa, long long wa_pitch,
+                      float* d_amax, cudaStream_t st, long long* launches);
+// A group of instances of one time whose Z matrices are built together (the
+// FP64 path length x_a . s_hat is formed once per antenna and source).
+struct ZGroup {
+    int inst0;        // first instance (into the call's instance table)
+    int n;            // instances in the group (same time, consecutive)
+    int slot0;        // workspace slot of the first instance
+    int uniform;      // channels are equally spaced: kappa_j = kappa0 + j dkappa
+    double kappa0, dkappa;
+};
+// Z build of a batch of groups: writes FP32 planes (prec 0) or BF16 hi/lo
+// planes (prec 1) of U into workspace slots.
+cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
+                          int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
+                          const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows,
+                          long long k_pitch, cudaStream_t st, long long* launches);
+cudaError_t launch_herk_fp32(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
+                             const float* d_u, int rows, long long k_pitch, float2* d_v, int N,
+                             int flush_k, cudaStream_t st, long long* launches);
+cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
+                           const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows,
+                           long long k_pitch, int n_slots, int fp16, const float* d_amax, float2* d_v,
+                           int N, int flush_kblocks, int* d_err, cudaStream_t st, long long* launches);
+bool herk_tc_available();
+
+// Exponent e of the exact power-of-two scale 2^e that brings max |Z| of an
+// instance into [2^13, 2^14) before the FP16 hi/lo split (the HERK epilogue
+// multiplies by 2^-2e).
+__device__ __forceinline__ int fp16_scale_exp(float amax) {
+    if (!(amax > 0.f) || !(amax < 3.0e38f)) return 0;
+    int e;
+    frexpf(amax, &e);
+    e = 14 - e;
+    return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+}  // namespace mv
