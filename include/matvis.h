@@ -166,6 +166,36 @@ typedef enum {
     MV_KERNEL_KINDS = 4
 } mv_kernel_kind;
 
+/* Rotation and horizon cut of one LST without any device allocation.
+ *
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory when they run this step -- code recording a CUDA graph by
+ * stream capture (cudaMalloc is not a stream operation), hosts whose device
+ * memory all belongs to a framework's own pool, and latency-critical loops
+ * that cannot take cudaMalloc's implicit device synchronisation.  It runs the
+ * same kernels as step (i) of mv_simulate, but their scratch (per-block live
+ * counts and offsets, and the 3 x 3 rotation) lives in a static device array
+ * of 64 KB that every GPU loading this library holds until the process exits.
+ *
+ * Limits and sharing: 1 <= n_src <= 2,097,152, else MV_ERR_ARG.  Every call
+ * on a device shares that array; calls that overlap on the GPU (for example
+ * on two unsynchronised streams) race and give wrong results.  Nothing in it
+ * needs clearing: a call writes every entry it reads.  The first call on each
+ * device resolves the array's device address with cudaGetSymbolAddress on the
+ * current device, so make that first call before any stream capture.
+ *
+ * Arguments (device pointers unless stated): xeq_dev [3][n_src] FP64 SoA
+ * (x, y, z of eq. "xeq"); lst_rad, latitude_rad host values; outputs, for the
+ * live sources (Up > 0) in catalogue order: live_idx_dev [n_src] int32
+ * catalogue indices, enu_dev [3][n_src] FP64 SoA (East, North, Up),
+ * azza_dev [n_src][2] FP32 (az, za; 8-byte aligned), n_live_dev [1] int32.
+ * Entries past n_live are left untouched.  Runs on the current device and on
+ * `stream` (NULL = legacy default stream); returns once the work is queued.
+ * Errors go to mv_last_error(). */
+mv_status mv_horizon_cull_static(int64_t n_src, const double *xeq_dev, double lst_rad, double latitude_rad,
+                                 int32_t *live_idx_dev, double *enu_dev, float *azza_dev,
+                                 int32_t *n_live_dev, void *stream);
+
 /* enable != 0 switches timing on and clears the counters; 0 switches it off. */
 mv_status mv_profile_enable(mv_ctx *ctx, int enable);
 

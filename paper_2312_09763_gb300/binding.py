@@ -26,7 +26,7 @@ INTERP = {"cubic": 0, "bilinear": 1}
 EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv_init_sky",
            "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas", "mv_simulate",
            "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts", "mv_last_launch_count",
-           "mv_profile_enable", "mv_profile_read"]
+           "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_last_launch_count.restype = i64
     lib.mv_profile_enable.argtypes = [vp, i32]
     lib.mv_profile_read.argtypes = [vp, i32, vp, vp]
+    lib.mv_horizon_cull_static.argtypes = [i64, vp, dp, dp, vp, vp, vp, vp, vp]
+    lib.mv_horizon_cull_static.restype = i32
     for name in ("mv_create", "mv_init_sky", "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas",
                  "mv_simulate", "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts",
                  "mv_profile_enable", "mv_profile_read"):

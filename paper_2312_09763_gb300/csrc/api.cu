@@ -37,6 +37,8 @@ struct Buf {
 
 }  // namespace
 
+void mv::set_last_error(const char* msg) { g_err = msg; }
+
 struct mv_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

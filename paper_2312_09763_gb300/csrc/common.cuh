@@ -104,6 +104,9 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                            int N, int flush_kblocks, int* d_err, cudaStream_t st, long long* launches);
 bool herk_tc_available();
 
+// Set the message mv_last_error() returns on this thread.
+void set_last_error(const char* msg);
+
 // Exponent e of the exact power-of-two scale 2^e that brings max |Z| of an
 // instance into [2^13, 2^14) before the FP16 hi/lo split (the HERK epilogue
 // multiplies by 2^-2e).
