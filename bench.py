@@ -36,11 +36,12 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp32"])
+    ap.add_argument("--precision", default="fp16x3", choices=["bf16x3", "fp16x3", "fp32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -81,8 +82,8 @@ class Dist:
 
 def workload(small: bool):
     from paper_2312_09763_gb300 import synth
-    if small:
-        return synth.hera_like(n_ant=350, n_src=100_000, n_chan=8, n_times=2)
+    if small:  # profiling captures: 64 channels of 1 LST, 1.5e4 sources (~2.7 GB of Z planes)
+        return synth.hera_like(n_ant=350, n_src=15_000, n_chan=64, n_times=1)
     return synth.hera_like()
 
 
@@ -209,6 +210,9 @@ def main():
     N = w.n_ant
     V = torch.empty((len(w.lsts), len(w.freqs), N, N), dtype=torch.complex64, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
+    tuning = None
+    if args.precision != "fp32" and not args.no_autotune:
+        tuning = sim.autotune(w.lsts, w.freqs, args.precision)
     for _ in range(args.warmup):
         sim.simulate(w.lsts, w.freqs, args.precision, out=V)
     torch.cuda.synchronize()
@@ -259,7 +263,7 @@ def main():
                        "live_sources_mean": float(K.mean()), "precision": args.precision,
                        "l2": "inputs larger than L2: Z planes of one batch ~4.5 GB, re-streamed each step",
                        "parallelism": f"{world} replica(s), instances simulated independently"},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "gpu_launches": launches, "roofline": roof, "clocks": clk, "herk_tuning": tuning,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
     if rank == 0 and not args.no_e2e:

@@ -83,7 +83,19 @@ typedef struct {
                                    sum (0 = auto = 4) */
     int herk_split;             /* split of the source axis across CTAs (0 = auto) */
     mv_allocator allocator;     /* alloc == NULL: cudaMalloc / cudaFree */
+    int herk_tile_n;            /* tensor-core HERK tile width: 128 or 256 columns (0 = auto) */
+    int use_graph;              /* capture each call shape's launch sequence in a CUDA graph and
+                                   replay it (default 1; calls with kernel timing run uncaptured) */
 } mv_options;
+
+/* A tensor-core HERK configuration chosen by mv_autotune. */
+typedef struct {
+    int tile_n;          /* 128 or 256 */
+    int split;           /* source-axis split */
+    int flush_kblocks;   /* 64-source k-blocks per TMEM flush */
+    int candidates;      /* configurations timed */
+    double herk_ms;      /* best time of one HERK launch of the first batch */
+} mv_tuning;
 
 /* Fill *opt with defaults. */
 void mv_default_options(mv_options *opt);
@@ -140,6 +152,18 @@ mv_status mv_simulate(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const d
 /* Simulate an explicit list of (lst, nu) pairs: V complex64 [n_pairs][N][N]. */
 mv_status mv_simulate_pairs(mv_ctx *ctx, int n_pairs, const double *lst, const double *nu,
                             mv_precision prec, void *V, int V_on_device, void *stream);
+
+/* Autotune the tensor-core HERK for calls shaped like this one (the paper
+ * leaves the matrix-product kernel to cuBLAS, Sec. 4.3; here it is the
+ * project's own and its tile width, source-axis split and flush interval are
+ * tuned).  Runs the first batch of the call (mv_simulate's plan, or
+ * mv_simulate_pairs' plan if pairs != 0 with n_t == n_nu pairs), times the
+ * HERK of that batch under each candidate with CUDA events on the context's
+ * stream, and keeps the fastest for later calls with the same matrix size,
+ * batch size and precision.  Synchronises.  prec must be a tensor-core
+ * precision.  out may be NULL. */
+mv_status mv_autotune(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const double *nu,
+                      mv_precision prec, int pairs, mv_tuning *out);
 
 /* Synchronise the context's work and report (and clear) a device-side error
  * flag (MV_ERR_DEVICE_TIMEOUT) or a pending CUDA error. */

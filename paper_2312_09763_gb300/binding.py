@@ -26,7 +26,7 @@ INTERP = {"cubic": 0, "bilinear": 1}
 EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv_init_sky",
            "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas", "mv_simulate",
            "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts", "mv_last_launch_count",
-           "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static"]
+           "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static", "mv_autotune"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -46,7 +46,13 @@ class _Allocator(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("interp", ctypes.c_int), ("max_batch", ctypes.c_int), ("herk_flush_kblocks", ctypes.c_int),
-                ("herk_split", ctypes.c_int), ("allocator", _Allocator)]
+                ("herk_split", ctypes.c_int), ("allocator", _Allocator), ("herk_tile_n", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("tile_n", ctypes.c_int), ("split", ctypes.c_int), ("flush_kblocks", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("herk_ms", ctypes.c_double)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -83,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_profile_read.argtypes = [vp, i32, vp, vp]
     lib.mv_horizon_cull_static.argtypes = [i64, vp, dp, dp, vp, vp, vp, vp, vp]
     lib.mv_horizon_cull_static.restype = i32
+    lib.mv_autotune.argtypes = [vp, i32, vp, i32, vp, i32, i32, vp]
+    lib.mv_autotune.restype = i32
     for name in ("mv_create", "mv_init_sky", "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas",
                  "mv_simulate", "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts",
                  "mv_profile_enable", "mv_profile_read"):
@@ -103,7 +111,7 @@ class Simulator:
     """One simulator context on one CUDA device (see include/matvis.h)."""
 
     def __init__(self, device: int = 0, interp: str = "cubic", max_batch: int = 0, herk_flush_kblocks: int = 0,
-                 torch_allocator: bool = True):
+                 herk_split: int = 0, herk_tile_n: int = 0, use_graph: bool = True, torch_allocator: bool = True):
         import torch  # device memory and streams
         self._torch = torch
         self._lib = load_library()
@@ -113,6 +121,9 @@ class Simulator:
         opt.interp = INTERP[interp]
         opt.max_batch = max_batch
         opt.herk_flush_kblocks = herk_flush_kblocks
+        opt.herk_split = herk_split
+        opt.herk_tile_n = herk_tile_n
+        opt.use_graph = 1 if use_graph else 0
         self._cb = None
         if torch_allocator:
             def _alloc(nbytes, dev, stream, user):
@@ -238,6 +249,16 @@ class Simulator:
 
     def last_launch_count(self) -> int:
         return int(self._lib.mv_last_launch_count(self._h))
+
+    def autotune(self, lsts, freqs, precision: str = "bf16x3", pairs: bool = False) -> dict:
+        """Time the tensor-core HERK configurations on the first batch of this
+        call shape and keep the fastest (see mv_autotune)."""
+        lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()
+        t = _Tuning()
+        self._check(self._lib.mv_autotune(self._h, lst.size, _p(lst), nu.size, _p(nu), PRECISION[precision],
+                                          1 if pairs else 0, ctypes.byref(t)))
+        return {"tile_n": t.tile_n, "split": t.split, "flush_kblocks": t.flush_kblocks,
+                "candidates": t.candidates, "herk_ms": t.herk_ms}
 
     def profile_enable(self, enable: bool = True):
         """Time every kernel launch with CUDA events (clears the counters)."""

@@ -35,6 +35,13 @@ struct Buf {
     size_t bytes = 0;
 };
 
+// Configuration of the tensor-core HERK for one call.
+struct HerkCfg {
+    int bn = 256;     // tile columns
+    int split = 1;    // source-axis split
+    int flush = 4;    // k-blocks per TMEM flush
+};
+
 }  // namespace
 
 void mv::set_last_error(const char* msg) { g_err = msg; }
@@ -52,7 +59,21 @@ struct mv_ctx {
     // model buffers
     Buf xeq, sqrt_flux, half_alpha, ant_e, ant_n, ant_u, bidx, grid;
     // workspace
-    Buf R, counts, offsets, le, ln, lu, lidx, lazza, nlive, chan, inst, groups, planes, wa, amax, u, ulo, vdev, err;
+    Buf R, counts, offsets, le, ln, lu, lidx, lazza, nlive, chan, inst, groups, planes, wa, amax, u, ulo, vdev, err,
+        partial, sched;
+    int n_sms = 148;
+    long long model_version = 0;  // bumped by every set-up call (kernel arguments embed the model)
+    // autotuned HERK configuration, valid for calls of the same shape
+    struct Tuned {
+        bool valid = false;
+        int rows = 0, slots = 0, zprec = 0;
+        HerkCfg cfg;
+        double ms = 0;
+    } tuned;
+    // captured launch sequence of the last call shape
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<long long> graph_key;
+    long long graph_launches = 0;
     long long launches = 0;
     std::vector<int> last_inst_t;
     // kernel timing
@@ -249,12 +270,81 @@ ZGroup make_group(const Plan& P, int i0, int n, int slot0) {
 
 int auto_batch(mv_ctx* c, long long slot_bytes) {
     if (c->opt.max_batch > 0) return c->opt.max_batch;
-    const long long budget = 8ll << 30;  // workspace for the Z planes
+    const long long budget = 20ll << 30;  // workspace for the Z planes
     long long b = budget / std::max(slot_bytes, 1ll);
-    return (int)std::max(1ll, std::min(b, 16ll));
+    return (int)std::max(1ll, std::min(b, 64ll));
 }
 
-mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, cudaStream_t st) {
+long long slot_bytes_of(mv_ctx* c) {
+    const long long N = (long long)c->model.n_feed * c->model.n_ant;
+    return 4ll * 2 * N * round_up((long long)c->model.n_ax * std::max<long long>(c->model.n_src, 1), kKPad);
+}
+
+// Every (LST, channel) pair; batches are up to B channels of one LST.
+void plan_grid(mv_ctx* c, int n_t, const double* lst, int n_nu, const double* nu, Plan& P) {
+    P.lst.assign(lst, lst + n_t);
+    P.nu.assign(nu, nu + n_nu);
+    const long long N = (long long)c->model.n_feed * c->model.n_ant;
+    for (int t = 0; t < n_t; ++t)
+        for (int f = 0; f < n_nu; ++f) P.inst.push_back(Inst{t, f, ((long long)t * n_nu + f) * N * N});
+    const int B = auto_batch(c, slot_bytes_of(c));
+    for (int t = 0; t < n_t; ++t)
+        for (int f0 = 0; f0 < n_nu; f0 += B) {
+            const int n = std::min(B, n_nu - f0);
+            const int i0 = t * n_nu + f0;
+            Plan::Batch b{i0, n, (int)P.groups.size(), 1};
+            P.groups.push_back(make_group(P, i0, n, 0));
+            P.batches.push_back(b);
+        }
+}
+
+// Explicit (LST, frequency) pairs; batches of up to B pairs, one group each.
+void plan_pairs(mv_ctx* c, int n_pairs, const double* lst, const double* nu, Plan& P) {
+    P.lst.assign(lst, lst + n_pairs);
+    P.nu.assign(nu, nu + n_pairs);
+    const long long N = (long long)c->model.n_feed * c->model.n_ant;
+    for (int i = 0; i < n_pairs; ++i) P.inst.push_back(Inst{i, i, (long long)i * N * N});
+    const int B = auto_batch(c, slot_bytes_of(c));
+    for (int i0 = 0; i0 < n_pairs; i0 += B) {
+        const int n = std::min(B, n_pairs - i0);
+        Plan::Batch b{i0, n, (int)P.groups.size(), n};
+        for (int j = 0; j < n; ++j) P.groups.push_back(make_group(P, i0 + j, 1, j));
+        P.batches.push_back(b);
+    }
+}
+
+// Everything one simulate call needs on the device, after validation and uploads.
+struct Prepared {
+    int n_times = 0, n_chan = 0, n_inst = 0;
+    int N = 0, rows = 0, bpt = 0, ncomp = 0, max_slots = 0, zprec = 0;
+    long long pitch = 0, k_pitch = 0;
+    LiveTables lt{};
+    float2* Vout = nullptr;
+    size_t v_bytes = 0;
+};
+
+// Heuristic HERK configuration: wide tiles unless the matrix is narrow; a
+// split giving the persistent grid about 16 units per SM while each unit keeps
+// at least 32 k-blocks of the expected live count (half the catalogue).
+HerkCfg heuristic_cfg(mv_ctx* c, const Prepared& p) {
+    HerkCfg h;
+    h.bn = c->opt.herk_tile_n == 128 || c->opt.herk_tile_n == 256 ? c->opt.herk_tile_n : (p.rows > 128 ? 256 : 128);
+    h.flush = c->opt.herk_flush_kblocks > 0 ? c->opt.herk_flush_kblocks : 4;
+    const int base = herk_tc_units(p.rows, p.max_slots, 1, h.bn);
+    const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
+    h.split = c->opt.herk_split > 0
+                  ? c->opt.herk_split
+                  : (int)std::max(1ll, std::min((long long)(16 * c->n_sms + base - 1) / base, est_kb / 32));
+    return h;
+}
+
+HerkCfg chosen_cfg(mv_ctx* c, const Prepared& p) {
+    if (c->tuned.valid && c->tuned.rows == p.rows && c->tuned.slots == p.max_slots && c->tuned.zprec == p.zprec)
+        return c->tuned.cfg;
+    return heuristic_cfg(c, p);
+}
+
+mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, cudaStream_t st, Prepared& out) {
     Model& m = c->model;
     if (!c->have_sky || !c->have_ant || !c->have_beam)
         return fail(MV_ERR_STATE, "simulate needs init_sky, set_antennas and a beam first");
@@ -265,14 +355,16 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
         return fail(MV_ERR_UNSUPPORTED, "tensor-map encoding unavailable in this driver");
     for (int b : c->h_bidx)
         if (b >= m.n_beam) return fail(MV_ERR_ARG, "antenna beam index %d >= n_beam %d", b, m.n_beam);
-    const int n_times = (int)P.lst.size(), n_chan = (int)P.nu.size();
-    const int n_inst = (int)P.inst.size();
-    c->launches = 0;
-    if (n_inst == 0) return MV_OK;
+    Prepared& p = out;
+    p.n_times = (int)P.lst.size();
+    p.n_chan = (int)P.nu.size();
+    p.n_inst = (int)P.inst.size();
+    p.zprec = prec == MV_PREC_FP32 ? 0 : (prec == MV_PREC_BF16X3 ? 1 : 2);
+    if (p.n_inst == 0) return MV_OK;
 
     // channel table
-    std::vector<Chan> chan(n_chan);
-    for (int i = 0; i < n_chan; ++i) {
+    std::vector<Chan> chan(p.n_chan);
+    for (int i = 0; i < p.n_chan; ++i) {
         const double nu = P.nu[i];
         if (!(std::isfinite(nu) && nu > 0)) return fail(MV_ERR_ARG, "frequency %d is not positive and finite", i);
         chan[i].kappa = nu / kCLight;
@@ -294,9 +386,9 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
         }
     }
     // R(t): eq. "rotation" with hour angle H = -LST; rows East, North, Up
-    std::vector<double> R(9 * (size_t)n_times);
+    std::vector<double> R(9 * (size_t)p.n_times);
     const double sl = std::sin(c->lat), cl = std::cos(c->lat);
-    for (int t = 0; t < n_times; ++t) {
+    for (int t = 0; t < p.n_times; ++t) {
         if (!std::isfinite(P.lst[t])) return fail(MV_ERR_ARG, "LST %d is not finite", t);
         const double H = -P.lst[t];
         const double sH = std::sin(H), cH = std::cos(H);
@@ -307,48 +399,54 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     }
 
     // sizes
-    const int N = m.n_feed * m.n_ant;
-    const int rows = 2 * N;
-    const long long pitch = round_up(m.n_src, kKPad);
-    const long long k_pitch = round_up((long long)m.n_ax * m.n_src, kKPad);
-    const int bpt = (int)((m.n_src + 255) / 256);
-    const int ncomp = m.n_beam * m.n_feed * m.n_ax;
-    int max_slots = 0;
-    for (auto& b : P.batches) max_slots = std::max(max_slots, b.n);
+    p.N = m.n_feed * m.n_ant;
+    p.rows = 2 * p.N;
+    p.pitch = round_up(m.n_src, kKPad);
+    p.k_pitch = round_up((long long)m.n_ax * m.n_src, kKPad);
+    p.bpt = (int)((m.n_src + 255) / 256);
+    p.ncomp = m.n_beam * m.n_feed * m.n_ax;
+    p.max_slots = 0;
+    for (auto& b : P.batches) p.max_slots = std::max(p.max_slots, b.n);
+    const int n_times = p.n_times, max_slots = p.max_slots;
+    const long long pitch = p.pitch;
 
     mv_status s;
     if ((s = upload(c, c->R, R.data(), R.size() * sizeof(double), st))) return s;
     if ((s = upload(c, c->chan, chan.data(), chan.size() * sizeof(Chan), st))) return s;
     if ((s = upload(c, c->inst, P.inst.data(), P.inst.size() * sizeof(Inst), st))) return s;
     if ((s = upload(c, c->groups, P.groups.data(), P.groups.size() * sizeof(ZGroup), st))) return s;
-    if ((s = ensure(c, c->counts, sizeof(int) * (size_t)bpt * n_times))) return s;
-    if ((s = ensure(c, c->offsets, sizeof(int) * (size_t)bpt * n_times))) return s;
+    if ((s = ensure(c, c->counts, sizeof(int) * (size_t)p.bpt * n_times))) return s;
+    if ((s = ensure(c, c->offsets, sizeof(int) * (size_t)p.bpt * n_times))) return s;
     if ((s = ensure(c, c->le, sizeof(double) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->ln, sizeof(double) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lu, sizeof(double) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lidx, sizeof(int) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lazza, sizeof(float2) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
-    if ((s = ensure(c, c->wa, sizeof(float2) * (size_t)max_slots * ncomp * pitch))) return s;
+    if ((s = ensure(c, c->wa, sizeof(float2) * (size_t)max_slots * p.ncomp * pitch))) return s;
     if ((s = ensure(c, c->amax, sizeof(float) * (size_t)max_slots))) return s;
-    const size_t plane_elems = (size_t)rows * k_pitch * max_slots;
-    if (prec == MV_PREC_FP32) {
+    if ((s = ensure(c, c->sched, sizeof(int) * (size_t)(max_slots + 8)))) return s;
+    const size_t plane_elems = (size_t)p.rows * p.k_pitch * max_slots;
+    if (p.zprec == 0) {
         if ((s = ensure(c, c->u, sizeof(float) * plane_elems))) return s;
     } else {
         if ((s = ensure(c, c->u, 2 * plane_elems))) return s;
         if ((s = ensure(c, c->ulo, 2 * plane_elems))) return s;
+        // partial tiles for the largest split any configuration may use
+        const HerkCfg h = chosen_cfg(c, p);
+        const size_t need = sizeof(float) * 128 * h.bn * (size_t)herk_tc_units(p.rows, max_slots, h.split, h.bn);
+        if (h.split > 1 && (s = ensure(c, c->partial, need))) return s;
     }
     if (m.beam_kind == 2 &&
-        (s = ensure(c, c->planes, sizeof(float2) * (size_t)n_chan * ncomp * m.n_za * m.n_az)))
+        (s = ensure(c, c->planes, sizeof(float2) * (size_t)p.n_chan * p.ncomp * m.n_za * m.n_az)))
         return s;
-    float2* Vout = static_cast<float2*>(V);
-    const size_t v_bytes = sizeof(float2) * (size_t)n_inst * N * N;
+    p.Vout = static_cast<float2*>(V);
+    p.v_bytes = sizeof(float2) * (size_t)p.n_inst * p.N * p.N;
     if (!V_on_device) {
-        if ((s = ensure(c, c->vdev, v_bytes))) return s;
-        Vout = static_cast<float2*>(c->vdev.p);
+        if ((s = ensure(c, c->vdev, p.v_bytes))) return s;
+        p.Vout = static_cast<float2*>(c->vdev.p);
     }
-
-    LiveTables lt;
+    LiveTables& lt = p.lt;
     lt.e = (double*)c->le.p;
     lt.n = (double*)c->ln.p;
     lt.u = (double*)c->lu.p;
@@ -356,53 +454,128 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     lt.azza = (float2*)c->lazza.p;
     lt.n_live = (int*)c->nlive.p;
     lt.pitch = pitch;
+    return MV_OK;
+}
 
-    long long L = 0;
+// HERK of one batch with configuration h.
+cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, const HerkCfg& h, cudaStream_t st,
+                         long long* L) {
+    const Inst* d_inst = (const Inst*)c->inst.p;
+    if (p.zprec == 0)
+        return launch_herk_fp32(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const float*)c->u.p, p.rows, p.k_pitch,
+                                p.Vout, p.N, 256, st, L);
+    return launch_herk_tc(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const __nv_bfloat16*)c->u.p,
+                          (const __nv_bfloat16*)c->ulo.p, p.rows, p.k_pitch, p.max_slots, p.zprec == 2 ? 1 : 0,
+                          (const float*)c->amax.p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
+                          (float*)c->partial.p, (int*)c->err.p, st, L);
+}
+
+// Beam evaluation and Z build of one batch.
+mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, cudaStream_t st, long long* L) {
+    mv_status s;
+    const Model& m = c->model;
+    const Inst* d_inst = (const Inst*)c->inst.p;
+    if ((s = cuda_check(cudaMemsetAsync(c->amax.p, 0, sizeof(float) * b.n, st), "amax reset"))) return s;
+    Timed tw(c, MV_KERNEL_BEAM, st);
+    cudaError_t e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, p.lt,
+                              (float2*)c->wa.p, p.pitch, (float*)c->amax.p, st, L);
+    tw.end();
+    if ((s = launched(e, "beam evaluation", st))) return s;
+    Timed tz(c, MV_KERNEL_ZBUILD, st);
+    e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, p.lt,
+                      (const float2*)c->wa.p, p.pitch, (const float*)c->amax.p, c->u.p, c->ulo.p, p.zprec, p.rows,
+                      p.k_pitch, st, L);
+    tz.end();
+    return launched(e, "Z build", st);
+}
+
+// The whole launch sequence of a call: cull, beam planes, then per batch
+// beam evaluation, Z build and HERK.
+mv_status enqueue_all(mv_ctx* c, Plan& P, const Prepared& p, const HerkCfg& h, cudaStream_t st, long long* L) {
+    mv_status s;
+    const Model& m = c->model;
     Timed tc0(c, MV_KERNEL_CULL, st);
-    cudaError_t e = launch_cull(m, (const double*)c->R.p, n_times, lt, (int*)c->counts.p, (int*)c->offsets.p, bpt,
-                                st, &L);
+    cudaError_t e = launch_cull(m, (const double*)c->R.p, p.n_times, p.lt, (int*)c->counts.p, (int*)c->offsets.p,
+                                p.bpt, st, L);
     tc0.end();
     if ((s = launched(e, "cull", st))) return s;
     if (m.beam_kind == 2) {
         Timed tb(c, MV_KERNEL_BEAM, st);
-        e = launch_beam_planes(m, (const float2*)c->grid.p, (const Chan*)c->chan.p, n_chan, (float2*)c->planes.p, st,
-                               &L);
+        e = launch_beam_planes(m, (const float2*)c->grid.p, (const Chan*)c->chan.p, p.n_chan, (float2*)c->planes.p,
+                               st, L);
         tb.end();
         if ((s = launched(e, "beam planes", st))) return s;
     }
-    const Inst* d_inst = (const Inst*)c->inst.p;
-    const int zprec = prec == MV_PREC_FP32 ? 0 : (prec == MV_PREC_BF16X3 ? 1 : 2);
     for (const auto& b : P.batches) {
-        if ((s = cuda_check(cudaMemsetAsync(c->amax.p, 0, sizeof(float) * b.n, st), "amax reset"))) return s;
-        Timed tw(c, MV_KERNEL_BEAM, st);
-        e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, lt,
-                      (float2*)c->wa.p, pitch, (float*)c->amax.p, st, &L);
-        tw.end();
-        if ((s = launched(e, "beam evaluation", st))) return s;
-        Timed tz(c, MV_KERNEL_ZBUILD, st);
-        e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, lt,
-                          (const float2*)c->wa.p, pitch, (const float*)c->amax.p, c->u.p, c->ulo.p, zprec, rows,
-                          k_pitch, st, &L);
-        tz.end();
-        if ((s = launched(e, "Z build", st))) return s;
+        if ((s = enqueue_zside(c, p, b, st, L))) return s;
         Timed th(c, MV_KERNEL_HERK, st);
-        if (prec == MV_PREC_FP32) {
-            e = launch_herk_fp32(d_inst, b.inst0, b.n, lt, m.n_ax, (const float*)c->u.p, rows, k_pitch, Vout, N, 256,
-                                 st, &L);
-        } else {
-            const int flush = c->opt.herk_flush_kblocks > 0 ? c->opt.herk_flush_kblocks : 4;
-            e = launch_herk_tc(d_inst, b.inst0, b.n, lt, m.n_ax, (const __nv_bfloat16*)c->u.p,
-                               (const __nv_bfloat16*)c->ulo.p, rows, k_pitch, max_slots, zprec == 2 ? 1 : 0,
-                               (const float*)c->amax.p, Vout, N, flush, (int*)c->err.p, st, &L);
-        }
+        e = enqueue_herk(c, p, b, h, st, L);
         th.end();
-        if ((s = launched(e, zprec == 0 ? "HERK fp32" : "HERK tc", st))) return s;
+        if ((s = launched(e, p.zprec == 0 ? "HERK fp32" : "HERK tc", st))) return s;
+    }
+    return MV_OK;
+}
+
+// Key of a captured launch sequence: every value its kernel arguments depend on.
+std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, const HerkCfg& h) {
+    std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch,
+                                h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout, c->model_version};
+    const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
+                         &c->lidx, &c->lazza, &c->nlive, &c->wa, &c->amax, &c->sched, &c->u, &c->ulo, &c->partial,
+                         &c->planes, &c->grid, &c->err};
+    for (const Buf* b : bufs) k.push_back((long long)(uintptr_t)b->p);
+    for (const auto& b : P.batches) {
+        k.push_back(b.inst0);
+        k.push_back(b.n);
+        k.push_back(b.g0);
+        k.push_back(b.ng);
+    }
+    return k;
+}
+
+mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, cudaStream_t st) {
+    c->launches = 0;
+    Prepared p;
+    mv_status s = prepare(c, P, prec, V, V_on_device, st, p);
+    if (s || p.n_inst == 0) return s;
+    const HerkCfg h = chosen_cfg(c, p);
+    long long L = 0;
+    // CUDA graph: the launch sequence is captured once per key (on the
+    // context's own stream) and replayed on the caller's stream.  Kernel
+    // timing records events around single launches, so it runs uncaptured.
+    if (c->opt.use_graph && !c->profiling && !debug_sync()) {
+        std::vector<long long> key = graph_key(c, P, p, h);
+        if (!c->graph_exec || key != c->graph_key) {
+            if (c->graph_exec) {
+                cudaGraphExecDestroy(c->graph_exec);
+                c->graph_exec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            if ((s = cuda_check(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture")))
+                return s;
+            mv_status se = enqueue_all(c, P, p, h, c->stream, &L);
+            cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+            if (se) {
+                if (g) cudaGraphDestroy(g);
+                return se;
+            }
+            if ((s = cuda_check(ee, "end capture"))) return s;
+            ee = cudaGraphInstantiate(&c->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if ((s = cuda_check(ee, "graph instantiate"))) return s;
+            c->graph_key = key;
+            c->graph_launches = L;
+        }
+        if ((s = cuda_check(cudaGraphLaunch(c->graph_exec, st), "graph launch"))) return s;
+        L = c->graph_launches;
+    } else {
+        if ((s = enqueue_all(c, P, p, h, st, &L))) return s;
     }
     c->launches = L;
     c->last_inst_t.clear();
     for (auto& in : P.inst) c->last_inst_t.push_back(in.t);
     if (!V_on_device) {
-        if ((s = cuda_check(cudaMemcpyAsync(V, Vout, v_bytes, cudaMemcpyDeviceToHost, st), "copy V to host")))
+        if ((s = cuda_check(cudaMemcpyAsync(V, p.Vout, p.v_bytes, cudaMemcpyDeviceToHost, st), "copy V to host")))
             return s;
         if ((s = cuda_check(cudaStreamSynchronize(st), "synchronize"))) return s;
         int herr = 0;
@@ -416,6 +589,83 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     return MV_OK;
 }
 
+// Autotuner: run the first batch of the call once, then time the HERK of that
+// batch under each candidate (tile width, split, flush) with CUDA events and
+// keep the fastest for calls of the same shape.
+mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tuning* out) {
+    if (prec == MV_PREC_FP32) return fail(MV_ERR_ARG, "the autotuner tunes the tensor-core HERK");
+    c->tuned.valid = false;
+    Prepared p;
+    mv_status s;
+    if ((s = ensure(c, c->vdev, sizeof(float2)))) return s;
+    // V for the trial runs: the context's staging buffer
+    if ((s = prepare(c, P, prec, c->vdev.p, 0, st, p))) return s;
+    if (p.n_inst == 0) return MV_OK;
+    const Plan::Batch b0 = P.batches[0];
+    std::vector<HerkCfg> cands;
+    const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
+    for (int bn : {128, 256})
+        for (int split : {1, 2, 4, 8, 16, 32, 64})
+            for (int flush : {4, 8}) {
+                if (split > 1 && est_kb / split < 8) continue;
+                HerkCfg h;
+                h.bn = bn;
+                h.split = split;
+                h.flush = flush;
+                cands.push_back(h);
+            }
+    size_t need = 0;
+    for (auto& h : cands)
+        need = std::max(need, sizeof(float) * 128 * h.bn * (size_t)herk_tc_units(p.rows, p.max_slots, h.split, h.bn));
+    if ((s = ensure(c, c->partial, need))) return s;
+    long long L = 0;
+    const Model& m = c->model;
+    cudaError_t e = launch_cull(m, (const double*)c->R.p, p.n_times, p.lt, (int*)c->counts.p, (int*)c->offsets.p,
+                                p.bpt, st, &L);
+    if ((s = cuda_check(e, "cull"))) return s;
+    if (m.beam_kind == 2) {
+        e = launch_beam_planes(m, (const float2*)c->grid.p, (const Chan*)c->chan.p, p.n_chan, (float2*)c->planes.p,
+                               st, &L);
+        if ((s = cuda_check(e, "beam planes"))) return s;
+    }
+    if ((s = enqueue_zside(c, p, b0, st, &L))) return s;
+    cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
+    HerkCfg best;
+    double best_ms = 1e300;
+    for (const auto& h : cands) {
+        if ((s = cuda_check(enqueue_herk(c, p, b0, h, st, &L), "trial HERK"))) return s;  // warm-up
+        cudaEventRecord(e0, st);
+        const int reps = 2;
+        for (int r = 0; r < reps; ++r)
+            if ((s = cuda_check(enqueue_herk(c, p, b0, h, st, &L), "trial HERK"))) return s;
+        cudaEventRecord(e1, st);
+        if ((s = cuda_check(cudaEventSynchronize(e1), "trial timing"))) return s;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / reps < best_ms) {
+            best_ms = ms / reps;
+            best = h;
+        }
+    }
+    c->pool.push_back(e0);
+    c->pool.push_back(e1);
+    if ((s = mv_check_device_status(c, st))) return s;
+    c->tuned.valid = true;
+    c->tuned.rows = p.rows;
+    c->tuned.slots = p.max_slots;
+    c->tuned.zprec = p.zprec;
+    c->tuned.cfg = best;
+    c->tuned.ms = best_ms;
+    if (out) {
+        out->tile_n = best.bn;
+        out->split = best.split;
+        out->flush_kblocks = best.flush;
+        out->herk_ms = best_ms;
+        out->candidates = (int)cands.size();
+    }
+    return MV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -424,6 +674,7 @@ void mv_default_options(mv_options* opt) {
     if (!opt) return;
     std::memset(opt, 0, sizeof(*opt));
     opt->interp = MV_INTERP_CUBIC;
+    opt->use_graph = 1;
 }
 
 const char* mv_last_error(void) { return g_err.c_str(); }
@@ -445,6 +696,12 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
     DeviceGuard g(device);
     mv_ctx* c = new mv_ctx();
     c->device = device;
+    c->n_sms = pr.multiProcessorCount;
+    if (herk_tc_init() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(MV_ERR_CUDA, "kernel attribute set-up failed");
+    }
     mv_default_options(&c->opt);
     if (opt) c->opt = *opt;
     if (c->opt.interp != MV_INTERP_CUBIC && c->opt.interp != MV_INTERP_BILINEAR) {
@@ -471,10 +728,12 @@ void mv_destroy(mv_ctx* c) {
     cudaDeviceSynchronize();
     Buf* all[] = {&c->xeq, &c->sqrt_flux, &c->half_alpha, &c->ant_e, &c->ant_n, &c->ant_u, &c->bidx, &c->grid,
                   &c->R, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu, &c->lidx, &c->lazza, &c->nlive,
-                  &c->chan, &c->inst, &c->groups, &c->planes, &c->wa, &c->amax, &c->u, &c->ulo, &c->vdev, &c->err};
+                  &c->chan, &c->inst, &c->groups, &c->planes, &c->wa, &c->amax, &c->u, &c->ulo, &c->vdev, &c->err,
+                  &c->partial, &c->sched};
     for (Buf* b : all) buf_free(c, *b);
     harvest(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -514,6 +773,7 @@ mv_status mv_init_sky(mv_ctx* c, int64_t n_src, const double* ra, const double* 
     c->model.half_alpha = (const float*)c->half_alpha.p;
     c->nu_ref = nu_ref;
     c->have_sky = true;
+    ++c->model_version;
     return MV_OK;
 }
 
@@ -525,6 +785,7 @@ mv_status mv_set_beam_gaussian(mv_ctx* c, double fwhm) {
     c->model.gauss_c = (float)(4.0 * std::log(2.0) / (fwhm * fwhm));
     c->model.n_beam = c->model.n_feed = c->model.n_ax = 1;
     c->have_beam = true;
+    ++c->model_version;
     return MV_OK;
 }
 
@@ -562,6 +823,7 @@ mv_status mv_set_beam_grid(mv_ctx* c, int n_beam, int n_feed, int n_ax, int n_nu
     c->grid_nu0 = nu0;
     c->grid_dnu = dnu;
     c->have_beam = true;
+    ++c->model_version;
     return MV_OK;
 }
 
@@ -598,6 +860,7 @@ mv_status mv_set_antennas(mv_ctx* c, int n_ant, const double* enu, const int32_t
     c->h_bidx = b;
     c->lat = lat;
     c->have_ant = true;
+    ++c->model_version;
     return MV_OK;
 }
 
@@ -608,21 +871,7 @@ mv_status mv_simulate(mv_ctx* c, int n_t, const double* lst, int n_nu, const dou
     if (n_t < 0 || n_nu < 0 || (n_t > 0 && !lst) || (n_nu > 0 && !nu)) return fail(MV_ERR_ARG, "bad time/frequency lists");
     DeviceGuard g(c->device);
     Plan P;
-    P.lst.assign(lst, lst + n_t);
-    P.nu.assign(nu, nu + n_nu);
-    const long long N = (long long)c->model.n_feed * c->model.n_ant;
-    for (int t = 0; t < n_t; ++t)
-        for (int f = 0; f < n_nu; ++f) P.inst.push_back(Inst{t, f, ((long long)t * n_nu + f) * N * N});
-    const long long slot_bytes = 4ll * 2 * N * round_up((long long)c->model.n_ax * std::max<long long>(c->model.n_src, 1), kKPad);
-    const int B = auto_batch(c, slot_bytes);
-    for (int t = 0; t < n_t; ++t)
-        for (int f0 = 0; f0 < n_nu; f0 += B) {
-            const int n = std::min(B, n_nu - f0);
-            const int i0 = t * n_nu + f0;
-            Plan::Batch b{i0, n, (int)P.groups.size(), 1};
-            P.groups.push_back(make_group(P, i0, n, 0));
-            P.batches.push_back(b);
-        }
+    plan_grid(c, n_t, lst, n_nu, nu, P);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     return run(c, P, prec, V, V_on_device, st);
 }
@@ -634,20 +883,22 @@ mv_status mv_simulate_pairs(mv_ctx* c, int n_pairs, const double* lst, const dou
     if (n_pairs < 0 || (n_pairs > 0 && (!lst || !nu))) return fail(MV_ERR_ARG, "bad pair lists");
     DeviceGuard g(c->device);
     Plan P;
-    P.lst.assign(lst, lst + n_pairs);
-    P.nu.assign(nu, nu + n_pairs);
-    const long long N = (long long)c->model.n_feed * c->model.n_ant;
-    for (int i = 0; i < n_pairs; ++i) P.inst.push_back(Inst{i, i, (long long)i * N * N});
-    const long long slot_bytes = 4ll * 2 * N * round_up((long long)c->model.n_ax * std::max<long long>(c->model.n_src, 1), kKPad);
-    const int B = auto_batch(c, slot_bytes);
-    for (int i0 = 0; i0 < n_pairs; i0 += B) {
-        const int n = std::min(B, n_pairs - i0);
-        Plan::Batch b{i0, n, (int)P.groups.size(), n};
-        for (int j = 0; j < n; ++j) P.groups.push_back(make_group(P, i0 + j, 1, j));
-        P.batches.push_back(b);
-    }
+    plan_pairs(c, n_pairs, lst, nu, P);
     cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
     return run(c, P, prec, V, V_on_device, st);
+}
+
+mv_status mv_autotune(mv_ctx* c, int n_t, const double* lst, int n_nu, const double* nu, mv_precision prec,
+                      int pairs, mv_tuning* out) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (n_t < 1 || n_nu < 1 || !lst || !nu || (pairs && n_t != n_nu))
+        return fail(MV_ERR_ARG, "bad time/frequency lists");
+    DeviceGuard g(c->device);
+    Plan P;
+    if (pairs) plan_pairs(c, n_t, lst, nu, P);
+    else plan_grid(c, n_t, lst, n_nu, nu, P);
+    return autotune(c, P, prec, c->stream, out);
 }
 
 mv_status mv_check_device_status(mv_ctx* c, void* stream) {

@@ -98,10 +98,21 @@ cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan
 cudaError_t launch_herk_fp32(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                              const float* d_u, int rows, long long k_pitch, float2* d_v, int N,
                              int flush_k, cudaStream_t st, long long* launches);
+// Persistent tensor-core HERK over n_inst instance slots: tiles 128 x bn
+// (bn = 128 or 256), the source axis split `split` ways (split > 1 writes
+// 128 x bn FP32 partial tiles, summed by a finalize kernel), TMEM flushed into
+// FP32 register sums every flush_kblocks k-blocks.  d_sched holds n_inst + 1
+// ints (instance order and the work counter).
 cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                            const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows,
                            long long k_pitch, int n_slots, int fp16, const float* d_amax, float2* d_v,
-                           int N, int flush_kblocks, int* d_err, cudaStream_t st, long long* launches);
+                           int N, int flush_kblocks, int split, int bn, int n_ctas, int* d_sched,
+                           float* d_partial, int* d_err, cudaStream_t st, long long* launches);
+// Set kernel attributes of the tensor-core HERK (once per process, outside
+// any stream capture).
+cudaError_t herk_tc_init();
+// Work units of that HERK (each needs 128 x bn x 4 bytes of partials when split > 1).
+int herk_tc_units(int rows, int n_slots, int split, int bn);
 bool herk_tc_available();
 
 // Set the message mv_last_error() returns on this thread.

@@ -21,27 +21,15 @@
 // records MV device timeout in the status word, stops, lets in-flight
 // copies and MMAs land, frees TMEM and returns.
 #include <cuda.h>
+
+#include <algorithm>
 #include "common.cuh"
 
 namespace mv {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
-constexpr int STAGES = 2;
-constexpr int A_BYTES = BM * BK * 2;                       // 16 KB
-constexpr int B_BYTES = BN * BK * 2;                       // 32 KB
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;     // 96 KB
-constexpr int NUM_THREADS = 320;
-constexpr int TMEM_COLS = 512;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int BM = 128, BK = 64;  // tile rows, k-block (64 sources = 128 B of BF16/FP16)
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
-
-// kind::f16 instruction descriptor: D = F32, A = B = BF16 (format 1) or FP16
-// (format 0), both K-major, N = 256, M = 128.
-constexpr uint32_t idesc_for(bool fp16) {
-    return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
-}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -137,49 +125,134 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
         : "memory");
 }
 
-// lower-triangle tiles: row tile ti (128 rows), column tile tj (256 rows of U), tj <= ti / 2
-__device__ __forceinline__ void tile_of(int idx, int& ti, int& tj) {
+// ------------------------------------------------------------------ tiling
+// Lower-triangle tiles of G: row tile ti (BM rows), column tile tj (BN rows of
+// U) with tj <= ti BM / BN; tile index runs over (ti, tj) in row order.
+template <int BN>
+__host__ __device__ __forceinline__ int tiles_in_row(int ti) { return ti * BM / BN + 1; }
+
+template <int BN>
+__host__ __device__ __forceinline__ void tile_of(int idx, int& ti, int& tj) {
     int i = 0;
-    while (idx >= i / 2 + 1) { idx -= i / 2 + 1; ++i; }
+    while (idx >= tiles_in_row<BN>(i)) { idx -= tiles_in_row<BN>(i); ++i; }
     ti = i;
     tj = idx;
 }
 
-__global__ void __launch_bounds__(NUM_THREADS, 1)
+template <int BN>
+int n_tiles_for(int rows) {
+    const int T = (rows + BM - 1) / BM;
+    int n = 0;
+    for (int i = 0; i < T; ++i) n += tiles_in_row<BN>(i);
+    return n;
+}
+
+// Kernel-wide configuration for a tile width BN (128 or 256 columns).
+template <int BN>
+struct Cfg {
+    static constexpr int A_BYTES = BM * BK * 2;                    // 16 KB per plane
+    static constexpr int B_BYTES = BN * BK * 2;                    // 16 or 32 KB per plane
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 64 or 96 KB
+    static constexpr int STAGES = BN == 256 ? 2 : 3;               // 192 KB of ring either way
+    static constexpr int TMEM_COLS = BN == 256 ? 512 : 256;        // two accumulator buffers
+    static constexpr int EPI_WARPS = BN / 32;                      // 128 columns per epilogue warp
+    static constexpr int THREADS = (2 + EPI_WARPS) * 32;
+    static constexpr int QDEPTH = 4;                               // unit-id queue depth
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
+};
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16 (format 1) or FP16
+// (format 0), both K-major, N = BN, M = 128.
+constexpr uint32_t idesc_for(bool fp16, int bn) {
+    return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) | ((uint32_t)(bn >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+// One unit of work: instance slot, tile (ti, tj) and the k-block range
+// [kb0, kb1) of split ks of S (balanced integer split of the instance's K).
+// Unit u = (r S + ks) n_tiles + tile, where r ranks the batch's instances by
+// decreasing live count (order[r] = slot): the longest instances are fetched
+// first, and the CTAs running at one time share k-ranges of one instance, so
+// each 64-column block of U is read from HBM about once and reused via L2.
+struct Unit {
+    int slot, ti, tj, kb0, kb1;
+    int part;  // index of the unit's partial tile: (slot n_tiles + tile) S + ks
+};
+
+template <int BN>
+__device__ __forceinline__ Unit decode_unit(int u, int n_tiles, int S, const int* __restrict__ order,
+                                            const Inst* __restrict__ inst, int inst0, const LiveTables& lt,
+                                            int n_ax) {
+    Unit w;
+    const int tile = u % n_tiles;
+    const int rest = u / n_tiles;
+    const int ks = rest % S;
+    w.slot = order[rest / S];
+    w.part = (w.slot * n_tiles + tile) * S + ks;
+    tile_of<BN>(tile, w.ti, w.tj);
+    const long long K = (long long)lt.n_live[inst[inst0 + w.slot].t] * n_ax;
+    const long long KB = ((K + kKPad - 1) / kKPad * kKPad) / BK;
+    w.kb0 = (int)(KB * ks / S);
+    w.kb1 = (int)(KB * (ks + 1) / S);
+    return w;
+}
+
+// order[r] = the slot with the r-th largest live count (ties by slot).
+__global__ void k_slot_order(const Inst* __restrict__ inst, int inst0, int n_slots, LiveTables lt,
+                             int* __restrict__ order) {
+    for (int i = threadIdx.x; i < n_slots; i += blockDim.x) {
+        const int ki = lt.n_live[inst[inst0 + i].t];
+        int rank = 0;
+        for (int j = 0; j < n_slots; ++j) {
+            const int kj = lt.n_live[inst[inst0 + j].t];
+            rank += (kj > ki) || (kj == ki && j < i);
+        }
+        order[rank] = i;
+    }
+}
+
+// Persistent HERK.  Warp 0 fetches units dynamically (one atomic counter per
+// launch), streams their U blocks with TMA and broadcasts each unit id to the
+// MMA warp and the epilogue warps through a shared-memory queue; the ring
+// and the two TMEM buffers carry across units, so the MMA warp starts the
+// next unit while the epilogue writes out the last one.
+template <int BN>
+__global__ void __launch_bounds__(Cfg<BN>::THREADS, 1)
 k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           const Inst* __restrict__ inst, int inst0, LiveTables lt, int n_ax, uint32_t idesc, int fp16,
-          const float* __restrict__ amax, float2* __restrict__ V, int N, int flush, int* __restrict__ err) {
+          const float* __restrict__ amax, float2* __restrict__ V, int N, int n_tiles, int n_units, int S,
+          int flush, const int* __restrict__ order, int* __restrict__ counter, float* __restrict__ partial,
+          int* __restrict__ err) {
+    using C = Cfg<BN>;
+    constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+    constexpr int QD = C::QDEPTH;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // barriers: full[STAGES], empty[STAGES], tfull[2], tempty[2], qfull[QD], qempty[QD]
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+    int* qslot = reinterpret_cast<int*>(bars + 2 * STAGES + 4 + 2 * QD);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(qslot + QD);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = blockIdx.y;
-    const Inst in = inst[inst0 + slot];
-    int ti, tj;
-    tile_of(blockIdx.x, ti, tj);
-    const long long K = (long long)lt.n_live[in.t] * n_ax;
-    const int KB = (int)(((K + kKPad - 1) / kKPad * kKPad) / BK);
-    const int n_chunks = (KB + flush - 1) / flush;
-
     auto full = [&](int s) { return smem_u32(&bars[s]); };
     auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
     auto tfull = [&](int b) { return smem_u32(&bars[2 * STAGES + b]); };
     auto tempty = [&](int b) { return smem_u32(&bars[2 * STAGES + 2 + b]); };
+    auto qfull = [&](int q) { return smem_u32(&bars[2 * STAGES + 4 + q]); };
+    auto qempty = [&](int q) { return smem_u32(&bars[2 * STAGES + 4 + QD + q]); };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(full(s), 1); mbar_init(empty(s), 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(tfull(b), 1); mbar_init(tempty(b), 8); }
+        for (int b = 0; b < 2; ++b) { mbar_init(tfull(b), 1); mbar_init(tempty(b), C::EPI_WARPS); }
+        for (int q = 0; q < QD; ++q) { mbar_init(qfull(q), 1); mbar_init(qempty(q), 1 + C::EPI_WARPS); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS));
+                     "r"(C::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         tc_fence_before();
     }
@@ -190,88 +263,130 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int it = 0; it < KB; ++it) {
-                const int s = it % STAGES;
-                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                if (!wait_bounded(empty(s), ph ^ 1u, abort_flag, err)) break;
-                mbar_expect_tx(full(s), STAGE_BYTES);
-                const uint32_t st = sbase + s * STAGE_BYTES;
-                const int x = it * BK;
-                tma_load_3d(st, &map_hi, x, ti * BM, slot, full(s));
-                tma_load_3d(st + A_BYTES, &map_lo, x, ti * BM, slot, full(s));
-                tma_load_3d(st + 2 * A_BYTES, &map_hi, x, tj * BN, slot, full(s));
-                tma_load_3d(st + 2 * A_BYTES + B_BYTES / 2, &map_hi, x, tj * BN + BN / 2, slot, full(s));
-                tma_load_3d(st + 2 * A_BYTES + B_BYTES, &map_lo, x, tj * BN, slot, full(s));
-                tma_load_3d(st + 2 * A_BYTES + B_BYTES + B_BYTES / 2, &map_lo, x, tj * BN + BN / 2, slot, full(s));
+            int it = 0;  // k-blocks loaded so far (ring position)
+            for (int n = 0;; ++n) {
+                int u = atomicAdd(counter, 1);
+                if (u >= n_units) u = -1;
+                const int q = n % QD;
+                if (!wait_bounded(qempty(q), ((uint32_t)(n / QD) & 1u) ^ 1u, abort_flag, err)) break;
+                qslot[q] = u;
+                mbar_arrive(qfull(q));
+                if (u < 0) break;
+                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+                bool ok = true;
+                for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!wait_bounded(empty(s), ph ^ 1u, abort_flag, err)) { ok = false; break; }
+                    mbar_expect_tx(full(s), STAGE_BYTES);
+                    const uint32_t st = sbase + s * STAGE_BYTES;
+                    const int x = kb * BK;
+                    tma_load_3d(st, &map_hi, x, w.ti * BM, w.slot, full(s));
+                    tma_load_3d(st + A_BYTES, &map_lo, x, w.ti * BM, w.slot, full(s));
+#pragma unroll
+                    for (int h = 0; h < BN / 128; ++h) {
+                        tma_load_3d(st + 2 * A_BYTES + h * 16384, &map_hi, x, w.tj * BN + h * 128, w.slot, full(s));
+                        tma_load_3d(st + 2 * A_BYTES + B_BYTES + h * 16384, &map_lo, x, w.tj * BN + h * 128, w.slot,
+                                    full(s));
+                    }
+                }
+                if (!ok) break;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            int it = 0;
-            bool ok = true;
-            for (int c = 0; c < n_chunks && ok; ++c) {
-                const int buf = c & 1;
-                const uint32_t ph = (uint32_t)(c >> 1) & 1u;
-                if (!wait_bounded(tempty(buf), ph ^ 1u, abort_flag, err)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(buf * BN);
-                const int kb_end = min(KB, (c + 1) * flush);
-                uint32_t acc = 0;
-                for (; it < kb_end; ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t sph = (uint32_t)(it / STAGES) & 1u;
-                    if (!wait_bounded(full(s), sph, abort_flag, err)) { ok = false; break; }
+            int it = 0, cg = 0;  // ring position, TMEM chunks issued so far
+            for (int n = 0;; ++n) {
+                const int q = n % QD;
+                if (!wait_bounded(qfull(q), (uint32_t)(n / QD) & 1u, abort_flag, err)) break;
+                const int u = qslot[q];
+                mbar_arrive(qempty(q));
+                if (u < 0) break;
+                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+                bool ok = true;
+                for (int kc = w.kb0; kc < w.kb1 && ok; kc += flush, ++cg) {
+                    const int buf = cg & 1;
+                    const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
+                    if (!wait_bounded(tempty(buf), ph ^ 1u, abort_flag, err)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t st = sbase + s * STAGE_BYTES;
+                    const uint32_t d = tmem_base + (uint32_t)(buf * BN);
+                    const int kc_end = min(w.kb1, kc + flush);
+                    uint32_t acc = 0;
+                    for (int kb = kc; kb < kc_end; ++kb, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t sph = (uint32_t)(it / STAGES) & 1u;
+                        if (!wait_bounded(full(s), sph, abort_flag, err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t st = sbase + s * STAGE_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint64_t a_hi = sdesc(st + kk * 32);
-                        const uint64_t a_lo = sdesc(st + A_BYTES + kk * 32);
-                        const uint64_t b_hi = sdesc(st + 2 * A_BYTES + kk * 32);
-                        const uint64_t b_lo = sdesc(st + 2 * A_BYTES + B_BYTES + kk * 32);
-                        tc_mma(d, a_hi, b_hi, idesc, acc);
-                        acc = 1;
-                        tc_mma(d, a_hi, b_lo, idesc, 1);
-                        tc_mma(d, a_lo, b_hi, idesc, 1);
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint64_t a_hi = sdesc(st + kk * 32);
+                            const uint64_t a_lo = sdesc(st + A_BYTES + kk * 32);
+                            const uint64_t b_hi = sdesc(st + 2 * A_BYTES + kk * 32);
+                            const uint64_t b_lo = sdesc(st + 2 * A_BYTES + B_BYTES + kk * 32);
+                            tc_mma(d, a_hi, b_hi, idesc, acc);
+                            acc = 1;
+                            tc_mma(d, a_hi, b_lo, idesc, 1);
+                            tc_mma(d, a_lo, b_hi, idesc, 1);
+                        }
+                        tc_commit(empty(s));
                     }
-                    tc_commit(empty(s));
+                    tc_commit(tfull(buf));
                 }
-                tc_commit(tfull(buf));
+                if (!ok) break;
             }
         }
     } else {
-        // epilogue: warps 2..9; TMEM lane quadrant q, column half h
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        float run[128];
-#pragma unroll
-        for (int i = 0; i < 128; ++i) run[i] = 0.f;
-        bool ok = true;
-        for (int c = 0; c < n_chunks; ++c) {
-            const int buf = c & 1;
-            const uint32_t ph = (uint32_t)(c >> 1) & 1u;
-            if (!wait_bounded(tfull(buf), ph, abort_flag, err)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * 128);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                uint32_t r[32];
-                tmem_ld32(ta + g * 32, r);
-                tmem_wait_ld(r);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) run[g * 32 + i] += __uint_as_float(r[i]);
-            }
-            tc_fence_before();
+        // epilogue warps: TMEM lane quadrant q4, 128-column group h
+        const int ew = warp - 2;
+        const int q4 = warp & 3, h = ew >> 2;
+        int cg = 0;
+        for (int n = 0;; ++n) {
+            const int qi = n % QD;
+            if (!wait_bounded(qfull(qi), (uint32_t)(n / QD) & 1u, abort_flag, err)) break;
+            const int u = qslot[qi];
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty(buf));
-        }
-        if (ok && !*abort_flag) {
-            const int r = ti * BM + q * 32 + lane;
+            if (lane == 0) mbar_arrive(qempty(qi));
+            if (u < 0) break;
+            const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+            float run[128];
+#pragma unroll
+            for (int i = 0; i < 128; ++i) run[i] = 0.f;
+            bool ok = true;
+            for (int kc = w.kb0; kc < w.kb1; kc += flush, ++cg) {
+                const int buf = cg & 1;
+                const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
+                if (!wait_bounded(tfull(buf), ph, abort_flag, err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t ta = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * BN + h * 128);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t r[32];
+                    tmem_ld32(ta + g * 32, r);
+                    tmem_wait_ld(r);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) run[g * 32 + i] += __uint_as_float(r[i]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty(buf));
+            }
+            if (!ok || *abort_flag) break;
+            const int rl = q4 * 32 + lane;  // row of the tile held by this thread
+            if (S > 1) {
+                // raw partial tile, column-major [BN][128] (coalesced along rows)
+                float* p = partial + (long long)w.part * (BN * BM) + (long long)h * 128 * BM + rl;
+#pragma unroll
+                for (int j = 0; j < 128; ++j) p[j * BM] = run[j];
+                continue;
+            }
+            const int r = w.ti * BM + rl;
             const int a = r >> 1;
             const bool even = (lane & 1) == 0;
-            float2* Vb = V + in.v_off;
-            const int c0 = tj * BN + h * 128;
+            float2* Vb = V + inst[inst0 + w.slot].v_off;
+            const int c0 = w.tj * BN + h * 128;
             // undo the FP16 scaling 2^e of both operands: two exact power-of-two steps
-            const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[slot])) : 1.f;
+            const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[w.slot])) : 1.f;
 #pragma unroll
             for (int jj = 0; jj < 64; ++jj) {
                 const float x0 = run[2 * jj], x1 = run[2 * jj + 1];
@@ -299,8 +414,41 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(C::TMEM_COLS));
     }
+}
+
+// Sum the S partial tiles of every (slot, tile) in a fixed order and fold the
+// 2 x 2 blocks of G into V (lower triangle + conjugate mirror).
+template <int BN>
+__global__ void __launch_bounds__(256)
+k_herk_finalize(const Inst* __restrict__ inst, int inst0, int fp16, const float* __restrict__ amax,
+                const float* __restrict__ partial, float2* __restrict__ V, int N, int n_tiles, int S) {
+    const int st = blockIdx.x;
+    const int slot = st / n_tiles, tile = st % n_tiles;
+    int ti, tj;
+    tile_of<BN>(tile, ti, tj);
+    const int q = blockIdx.y * 256 + threadIdx.x;  // 2 x 2 block index within the tile
+    const int rp = q % (BM / 2), cp = q / (BM / 2);
+    const int r = 2 * rp, c = 2 * cp;
+    const int a = (ti * BM + r) >> 1, b = (tj * BN + c) >> 1;
+    if (a >= N || b >= N || a < b) return;
+    float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
+    for (int ks = 0; ks < S; ++ks) {
+        const float* p = partial + ((long long)st * S + ks) * (BN * BM);
+        const float2 v0 = *reinterpret_cast<const float2*>(p + (long long)c * BM + r);
+        const float2 v1 = *reinterpret_cast<const float2*>(p + (long long)(c + 1) * BM + r);
+        g00 += v0.x;
+        g10 += v0.y;
+        g01 += v1.x;
+        g11 += v1.y;
+    }
+    const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[slot])) : 1.f;
+    const float re = ((g00 + g11) * unscale) * unscale;
+    const float im = a == b ? 0.f : ((g10 - g01) * unscale) * unscale;
+    float2* Vb = V + inst[inst0 + slot].v_off;
+    Vb[(long long)a * N + b] = make_float2(re, im);
+    if (a != b) Vb[(long long)b * N + a] = make_float2(re, -im);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -329,38 +477,72 @@ bool make_map(CUtensorMap* map, const void* base, long long k_pitch, int rows, i
     cuuint64_t strides[2] = {(cuuint64_t)k_pitch * 2, (cuuint64_t)k_pitch * 2 * rows};
     cuuint32_t box[3] = {BK, BM, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* d_inst, int inst0, int n_inst,
+                      LiveTables lt, int n_ax, int fp16, const float* d_amax, float2* d_v, int N, int rows,
+                      int flush, int split, int n_ctas, int* d_sched, float* d_partial, int* d_err,
+                      cudaStream_t st, long long* launches) {
+    using C = Cfg<BN>;
+    const int n_tiles = n_tiles_for<BN>(rows);
+    const int n_units = n_tiles * n_inst * split;
+    int* order = d_sched;            // [n_inst]
+    int* counter = d_sched + n_inst;  // one int
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_slot_order<<<1, 256, 0, st>>>(d_inst, inst0, n_inst, lt, order);
+    const int grid = std::max(1, std::min(n_ctas, n_units));
+    k_herk_tc<BN><<<grid, C::THREADS, C::SMEM, st>>>(mh, ml, d_inst, inst0, lt, n_ax, idesc_for(fp16 != 0, BN), fp16,
+                                                     d_amax, d_v, N, n_tiles, n_units, split, flush, order, counter,
+                                                     d_partial, d_err);
+    *launches += 2;
+    if (split > 1) {
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dim3 g2(n_tiles * n_inst, (BM / 2) * (BN / 2) / 256);
+        k_herk_finalize<BN><<<g2, 256, 0, st>>>(d_inst, inst0, fp16, d_amax, d_partial, d_v, N, n_tiles, split);
+        *launches += 1;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool herk_tc_available() { return get_encode() != nullptr; }
 
+cudaError_t herk_tc_init() {
+    cudaError_t e = cudaFuncSetAttribute(k_herk_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<256>::SMEM);
+    return e;
+}
+
+int herk_tc_units(int rows, int n_slots, int split, int bn) {
+    return (bn == 128 ? n_tiles_for<128>(rows) : n_tiles_for<256>(rows)) * n_slots * split;
+}
+
 cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                            const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows, long long k_pitch,
-                           int n_slots, int fp16, const float* d_amax, float2* d_v, int N, int flush, int* d_err,
-                           cudaStream_t st, long long* launches) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_herk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+                           int n_slots, int fp16, const float* d_amax, float2* d_v, int N, int flush, int split,
+                           int bn, int n_ctas, int* d_sched, float* d_partial, int* d_err, cudaStream_t st,
+                           long long* launches) {
     CUtensorMap mh, ml;
     if (!make_map(&mh, d_hi, k_pitch, rows, n_slots, fp16) || !make_map(&ml, d_lo, k_pitch, rows, n_slots, fp16))
         return cudaErrorInvalidValue;
-    const int T = (rows + BM - 1) / BM;
-    int n_tiles = 0;
-    for (int i = 0; i < T; ++i) n_tiles += i / 2 + 1;
     if (flush < 1) flush = 4;
-    dim3 grid(n_tiles, n_inst);
-    k_herk_tc<<<grid, NUM_THREADS, SMEM_BYTES, st>>>(mh, ml, d_inst, inst0, lt, n_ax, idesc_for(fp16 != 0), fp16,
-                                                     d_amax, d_v, N, flush, d_err);
-    *launches += 1;
-    return cudaGetLastError();
+    if (split < 1) split = 1;
+    if ((split > 1 && !d_partial) || !d_sched || n_inst > 4096) return cudaErrorInvalidValue;
+    if (bn == 128)
+        return launch_bn<128>(mh, ml, d_inst, inst0, n_inst, lt, n_ax, fp16, d_amax, d_v, N, rows, flush, split, n_ctas,
+                              d_sched, d_partial, d_err, st, launches);
+    return launch_bn<256>(mh, ml, d_inst, inst0, n_inst, lt, n_ax, fp16, d_amax, d_v, N, rows, flush, split, n_ctas,
+                          d_sched, d_partial, d_err, st, launches);
 }
 
 }  // namespace mv

@@ -8,7 +8,7 @@
 // The phase argument (nu/c) x_a . s_hat is formed in FP64 and reduced
 // exactly modulo one turn into 64-bit fixed point (bit operations on the
 // FP64 significand); only the reduced fraction is rounded to FP32 for
-// sincospi.  For the channels of one time that are equally spaced in nu,
+// the sine and cosine.  For the channels of one time that are equally spaced in nu,
 // (x_a . s_hat) kappa_0 and (x_a . s_hat) dkappa are formed in FP64 once per
 // (antenna, source) and the channel phases are stepped by exact 64-bit
 // integer addition of their fractions.
@@ -32,92 +32,138 @@ __device__ __forceinline__ unsigned long long frac64(double p) {
     return b < 0 ? (0ull - f) : f;
 }
 
-// Fixed-point turns in [-1/2, 1/2) as FP32 (top 32 bits, two's complement).
-__device__ __forceinline__ float turns(unsigned long long f) {
-    return (float)(int)(f >> 32) * 2.3283064365386962890625e-10f;  // 2^-32
+// cos(2 pi r), sin(2 pi r) for the fixed-point turn F (r = frac(F / 2^64)):
+// the nearest quarter turn q comes from the top bits, the remainder
+// x in [-1/8, 1/8) turns goes through polynomials fitted to sin(2 pi x) / x and
+// cos(2 pi x) in x^2 (least squares on Chebyshev nodes, |error| < 2e-9 before
+// FP32 rounding), and the result is rotated by q quarter turns.
+__device__ __forceinline__ void cos_sin_turns(unsigned long long F, float& c, float& s) {
+    const unsigned X = (unsigned)(F >> 32);
+    const unsigned q = (X + 0x20000000u) >> 30;
+    const int t = (int)(X - (q << 30));
+    const float x = (float)t * 2.3283064365386962890625e-10f;  // 2^-32
+    const float x2 = x * x;
+    const float sp = fmaf(fmaf(fmaf(-75.24006652832031f, x2, 81.58812713623047f), x2, -41.34162902832031f), x2,
+                          6.283185005187988f) * x;
+    const float cp = fmaf(fmaf(fmaf(fmaf(59.22040557861328f, x2, -85.44285583496094f), x2, 64.93931579589844f), x2,
+                               -19.739208221435547f), x2, 1.0f);
+    const bool swap = (q & 1u) != 0u;
+    const float a = swap ? sp : cp, b = swap ? cp : sp;
+    c = __int_as_float(__float_as_int(a) ^ (int)((((q + 1u) & 2u)) << 30));
+    s = __int_as_float(__float_as_int(b) ^ (int)(((q & 2u)) << 30));
 }
 
-// Store one real entry of U: FP32 (PREC 0), or split into hi + lo halves,
-// BF16 (PREC 1) or FP16 after the instance's power-of-two scale (PREC 2).
-template <int PREC>
-__device__ __forceinline__ void put(void* u, void* ulo, long long o, float v, float scale) {
+// Store 2 n_ax consecutive entries of one row of U (two sources).
+template <int PREC, int NAX>
+__device__ __forceinline__ void put_row(void* u, void* ulo, long long o, const float* v, float scale) {
     if (PREC == 0) {
-        static_cast<float*>(u)[o] = v;
-    } else if (PREC == 1) {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        static_cast<__nv_bfloat16*>(u)[o] = hi;
-        static_cast<__nv_bfloat16*>(ulo)[o] = lo;
+        float* p = static_cast<float*>(u) + o;
+        if (NAX == 1) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        else *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+    uint32_t hi[NAX], lo[NAX];
+#pragma unroll
+    for (int i = 0; i < NAX; ++i) {
+        const float x0 = PREC == 2 ? v[2 * i] * scale : v[2 * i];
+        const float x1 = PREC == 2 ? v[2 * i + 1] * scale : v[2 * i + 1];
+        if (PREC == 1) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+            hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+            lo[i] = *reinterpret_cast<const uint32_t*>(&l);
+        } else {
+            const __half2 h = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+            hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+            lo[i] = *reinterpret_cast<const uint32_t*>(&l);
+        }
+    }
+    uint16_t* ph = static_cast<uint16_t*>(u) + o;
+    uint16_t* pl = static_cast<uint16_t*>(ulo) + o;
+    if (NAX == 1) {
+        *reinterpret_cast<uint32_t*>(ph) = hi[0];
+        *reinterpret_cast<uint32_t*>(pl) = lo[0];
     } else {
-        const float x = v * scale;
-        const __half hi = __float2half_rn(x);
-        const __half lo = __float2half_rn(x - __half2float(hi));
-        static_cast<__half*>(u)[o] = hi;
-        static_cast<__half*>(ulo)[o] = lo;
+        *reinterpret_cast<uint2*>(ph) = make_uint2(hi[0], hi[1]);
+        *reinterpret_cast<uint2*>(pl) = make_uint2(lo[0], lo[1]);
     }
 }
 
-template <int PREC>
+// One thread builds two adjacent sources (columns 2 n_ax wide) for a range of
+// antennas and every instance of its group.  Sources past the live count
+// (up to the k padding) are written as zeros.
+template <int PREC, int NAX>
 __global__ void __launch_bounds__(128)
 k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
          const ZGroup* __restrict__ groups, int g_first, LiveTables lt, const float2* __restrict__ wa,
          long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo, int rows, long long k_pitch,
          int ant_per_block) {
     const ZGroup g = groups[g_first + blockIdx.z];
-    const int slot0 = g.slot0;
     const int t = inst[g.inst0].t;
     const int nl = lt.n_live[t];
-    const long long kpad = ((long long)nl * m.n_ax + kKPad - 1) / kKPad * kKPad;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if ((long long)s * m.n_ax >= kpad) return;
+    const long long kpad = ((long long)nl * NAX + kKPad - 1) / kKPad * kKPad;
+    const int s0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if ((long long)s0 * NAX >= kpad) return;
     const int a_begin = blockIdx.y * ant_per_block;
     const int a_end = min(m.n_ant, a_begin + ant_per_block);
     const long long slot_stride = (long long)rows * k_pitch;
-    const int ncomp = m.n_beam * m.n_feed * m.n_ax;
-    if (s >= nl) {  // zero padding of the source axis up to the k granularity
-        for (int j = 0; j < g.n; ++j) {
-            const long long base = (long long)(slot0 + j) * slot_stride;
-            for (int a = a_begin; a < a_end; ++a)
-                for (int p = 0; p < m.n_feed; ++p)
-                    for (int k = 0; k < m.n_ax; ++k) {
-                        const long long r = 2ll * (a * m.n_feed + p);
-                        const long long col = (long long)s * m.n_ax + k;
-                        put<PREC>(u, ulo, base + r * k_pitch + col, 0.f, 1.f);
-                        put<PREC>(u, ulo, base + (r + 1) * k_pitch + col, 0.f, 1.f);
-                    }
-        }
-        return;
-    }
-    const long long lo = (long long)t * lt.pitch + s;
-    const double se = lt.e[lo], sn = lt.n[lo], su = lt.u[lo];
+    const int nfd = m.n_feed;
+    const int ncomp = m.n_beam * nfd * NAX;
+    const bool live0 = s0 < nl, live1 = s0 + 1 < nl;
+    double e0 = 0, n0 = 0, u0 = 0, e1 = 0, n1 = 0, u1 = 0;
+    const long long lo = (long long)t * lt.pitch + s0;
+    if (live0) { e0 = lt.e[lo]; n0 = lt.n[lo]; u0 = lt.u[lo]; }
+    if (live1) { e1 = lt.e[lo + 1]; n1 = lt.n[lo + 1]; u1 = lt.u[lo + 1]; }
+    const long long col = (long long)s0 * NAX;
     for (int a = a_begin; a < a_end; ++a) {
-        // path length x_a . s_hat in metres (FP64)
-        const double d = fma(m.ant_e[a], se, fma(m.ant_n[a], sn, m.ant_u[a] * su));
+        // path lengths x_a . s_hat in metres (FP64)
+        const double ae = m.ant_e[a], an = m.ant_n[a], au = m.ant_u[a];
+        const double d0 = fma(ae, e0, fma(an, n0, au * u0));
+        const double d1 = fma(ae, e1, fma(an, n1, au * u1));
         const int beta = m.beam_idx[a];
-        unsigned long long F = 0ull, FQ = 0ull;
+        unsigned long long F0 = 0ull, F1 = 0ull, Q0 = 0ull, Q1 = 0ull;
         if (g.uniform) {
-            F = frac64(d * g.kappa0);
-            FQ = frac64(d * g.dkappa);
+            F0 = frac64(d0 * g.kappa0);
+            F1 = frac64(d1 * g.kappa0);
+            Q0 = frac64(d0 * g.dkappa);
+            Q1 = frac64(d1 * g.dkappa);
         }
         for (int j = 0; j < g.n; ++j) {
-            if (!g.uniform) F = frac64(d * chan[inst[g.inst0 + j].c].kappa);
-            float sv, cv;
-            sincospif(2.f * turns(F), &sv, &cv);  // exp(-2 pi i p) = cv - i sv
-            const int slot = slot0 + j;
+            if (!g.uniform) {
+                const double kap = chan[inst[g.inst0 + j].c].kappa;
+                F0 = frac64(d0 * kap);
+                F1 = frac64(d1 * kap);
+            }
+            float c0, sn0, c1, sn1;
+            cos_sin_turns(F0, c0, sn0);
+            cos_sin_turns(F1, c1, sn1);
+            const int slot = g.slot0 + j;
             const long long base = (long long)slot * slot_stride;
             const float scale = PREC == 2 ? ldexpf(1.f, fp16_scale_exp(amax[slot])) : 1.f;
-            const float2* w = wa + ((long long)slot * ncomp + (long long)beta * m.n_feed * m.n_ax) * wa_pitch + s;
-            for (int p = 0; p < m.n_feed; ++p)
-                for (int k = 0; k < m.n_ax; ++k) {
-                    const float2 A = w[(long long)(p * m.n_ax + k) * wa_pitch];
-                    const float re = fmaf(A.x, cv, A.y * sv);
-                    const float im = fmaf(A.y, cv, -A.x * sv);
-                    const long long r = 2ll * (a * m.n_feed + p);
-                    const long long col = (long long)s * m.n_ax + k;
-                    put<PREC>(u, ulo, base + r * k_pitch + col, re, scale);
-                    put<PREC>(u, ulo, base + (r + 1) * k_pitch + col, im, scale);
+            const float2* w = wa + ((long long)slot * ncomp + (long long)beta * nfd * NAX) * wa_pitch + s0;
+            for (int p = 0; p < nfd; ++p) {
+                float re[2 * NAX], im[2 * NAX];
+#pragma unroll
+                for (int k = 0; k < NAX; ++k) {
+                    // WA of the two sources: one 16-byte load (s0 is even)
+                    float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (live0) A = *reinterpret_cast<const float4*>(w + (long long)(p * NAX + k) * wa_pitch);
+                    if (!live1) { A.z = 0.f; A.w = 0.f; }
+                    // Z = WA * exp(-2 pi i phase) = WA * (c - i s)
+                    re[k] = fmaf(A.x, c0, A.y * sn0);
+                    im[k] = fmaf(A.y, c0, -A.x * sn0);
+                    re[NAX + k] = fmaf(A.z, c1, A.w * sn1);
+                    im[NAX + k] = fmaf(A.w, c1, -A.z * sn1);
                 }
-            F += FQ;
+                const long long r = 2ll * (a * nfd + p);
+                put_row<PREC, NAX>(u, ulo, base + r * k_pitch + col, re, scale);
+                put_row<PREC, NAX>(u, ulo, base + (r + 1) * k_pitch + col, im, scale);
+            }
+            F0 += Q0;
+            F1 += Q1;
         }
     }
 }
@@ -129,16 +175,16 @@ cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan
                           const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows, long long k_pitch,
                           cudaStream_t st, long long* launches) {
     const int apb = 32;
-    dim3 grid((unsigned)((lt.pitch + 127) / 128), (m.n_ant + apb - 1) / apb, n_groups);
-    if (prec == 0)
-        k_zbuild<0><<<grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u,
-                                          nullptr, rows, k_pitch, apb);
-    else if (prec == 1)
-        k_zbuild<1><<<grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u,
-                                          d_u_lo, rows, k_pitch, apb);
-    else
-        k_zbuild<2><<<grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u,
-                                          d_u_lo, rows, k_pitch, apb);
+    dim3 grid((unsigned)((lt.pitch / 2 + 127) / 128), (m.n_ant + apb - 1) / apb, n_groups);
+#define MV_ZB(P, A) \
+    k_zbuild<P, A><<<grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u, d_u_lo, \
+                                         rows, k_pitch, apb)
+    if (m.n_ax == 1) {
+        if (prec == 0) MV_ZB(0, 1); else if (prec == 1) MV_ZB(1, 1); else MV_ZB(2, 1);
+    } else {
+        if (prec == 0) MV_ZB(0, 2); else if (prec == 1) MV_ZB(1, 2); else MV_ZB(2, 2);
+    }
+#undef MV_ZB
     *launches += 1;
     return cudaGetLastError();
 }

@@ -80,6 +80,22 @@ def uniform_sphere(n: int, g: np.random.Generator):
     return ra, dec
 
 
+def vmf_cluster(n: int, kappa: float, ra0: float, dec0: float, g: np.random.Generator):
+    """(ra, dec) drawn from a von Mises-Fisher distribution on the sphere about
+    (ra0, dec0) with concentration kappa (Wood 1994: the cosine of the angle
+    to the mean direction by inverse CDF, the azimuth about it uniform)."""
+    mu = np.array([np.cos(ra0) * np.cos(dec0), np.sin(ra0) * np.cos(dec0), np.sin(dec0)])
+    u = g.uniform(0.0, 1.0, n)
+    w = 1.0 + np.log(u + (1.0 - u) * np.exp(-2.0 * kappa)) / kappa
+    phi = g.uniform(0.0, 2.0 * np.pi, n)
+    a = np.cross(mu, [0.0, 0.0, 1.0])
+    a /= np.linalg.norm(a)
+    b = np.cross(mu, a)
+    s = np.sqrt(np.maximum(0.0, 1.0 - w * w))
+    v = w[:, None] * mu + s[:, None] * (np.cos(phi)[:, None] * a + np.sin(phi)[:, None] * b)
+    return np.mod(np.arctan2(v[:, 1], v[:, 0]), 2 * np.pi), np.arcsin(np.clip(v[:, 2], -1.0, 1.0))
+
+
 def powerlaw_flux(n: int, smin: float, smax: float, gamma: float, g: np.random.Generator) -> np.ndarray:
     """Fluxes with dN/dS ~ S^-gamma on [smin, smax] (inverse CDF)."""
     a, b = smin ** (1.0 - gamma), smax ** (1.0 - gamma)
@@ -176,4 +192,30 @@ def hera_like(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times:
     grid = gaussian_ripple_grid(nu_grid, n_za, n_az, 10.0 * DEG, 150e6, 0.05, rng(1, "beam_ripple"))
     beam = ("grid", grid, 98e6, 1e6, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
     return Workload(f"hera_like: {n_ant} ant x {n_src} src x {n_chan} ch x {n_times} t, bicubic grid beam",
+                    ra, dec, flux, alpha, 150e6, enu, HERA_LAT, beam, lsts, freqs)
+
+
+def batched_uneven(n_pairs: int = 256, n_ant: int = 350, n_src: int = 100_000, n_za: int = 91,
+                   n_az: int = 360) -> Workload:
+    """Workload 3: n_pairs (LST, frequency) pairs, LST ~ U[0, 24 h) and
+    nu ~ U[50, 250] MHz, for the HERA-like array; the sky is 40 % uniform and
+    60 % von Mises-Fisher clustered (kappa = 20) about RA 6 h, Dec = latitude,
+    so the horizon cut leaves about 20k-80k live sources depending on LST;
+    fluxes and spectra as workload 1; the beam of workload 1 on 48-252 MHz.
+    `lsts` and `freqs` hold the pairs (equal length)."""
+    enu = hex_array(n_ant, 14.6)
+    n_uni = int(round(0.4 * n_src))
+    ra1, dec1 = uniform_sphere(n_uni, rng(3, "positions_uniform"))
+    ra2, dec2 = vmf_cluster(n_src - n_uni, 20.0, np.pi / 2, HERA_LAT, rng(3, "positions_cluster"))
+    ra, dec = np.concatenate([ra1, ra2]), np.concatenate([dec1, dec2])
+    flux = powerlaw_flux(n_src, 0.01, 100.0, 1.6, rng(3, "flux"))
+    alpha = rng(3, "spectral_index").normal(-0.8, 0.2, size=n_src)
+    gp = rng(3, "pairs")
+    lsts = gp.uniform(0.0, 2 * np.pi, n_pairs)
+    freqs = gp.uniform(50e6, 250e6, n_pairs)
+    nu_grid = 48e6 + np.arange(205) * 1e6
+    grid = gaussian_ripple_grid(nu_grid, n_za, n_az, 10.0 * DEG, 150e6, 0.05, rng(3, "beam_ripple"))
+    beam = ("grid", grid, 48e6, 1e6, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
+    return Workload(f"batched_uneven: {n_pairs} (LST, nu) pairs, {n_ant} ant x {n_src} src (40% uniform + "
+                    "60% clustered), bicubic grid beam 48-252 MHz",
                     ra, dec, flux, alpha, 150e6, enu, HERA_LAT, beam, lsts, freqs)

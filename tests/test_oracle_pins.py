@@ -337,3 +337,14 @@ def test_per_antenna_beam_index():
     V = oracle.vis(p, lst, 150e6)
     gains = np.array([g0, g1])[bidx]
     assert np.abs(V - 1.5 * np.outer(gains, gains.conj())).max() < 1e-12
+
+
+def test_batched_uneven_generator_live_range():
+    w = synth.batched_uneven(n_pairs=64, n_src=20_000, n_za=31, n_az=60)
+    assert w.lsts.size == w.freqs.size == 64
+    assert np.all((w.freqs >= 50e6) & (w.freqs <= 250e6))
+    lat = w.lat
+    up = [np.sum(np.sin(lat) * np.sin(w.dec) + np.cos(lat) * np.cos(w.dec) * np.cos(t - w.ra) > 0)
+          for t in np.linspace(0, 2 * np.pi, 25)]
+    # 40 % uniform + 60 % clustered: about 20 % to 80 % of the catalogue above the horizon
+    assert 0.15 * 20_000 < min(up) < 0.30 * 20_000 and 0.75 * 20_000 < max(up) <= 0.85 * 20_000
