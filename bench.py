@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
     return ap.parse_args()
 
 
@@ -203,7 +204,7 @@ def main():
     d = Dist(world)
     torch.cuda.set_device(local)
     w = workload(args.small)
-    sim = Simulator(local)
+    sim = Simulator(local, overlap_batches=args.overlap)
     sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
     sim.set_beam(w.beam)
     sim.set_antennas(w.enu, None, w.lat)

@@ -86,6 +86,9 @@ typedef struct {
     int herk_tile_n;            /* tensor-core HERK tile width: 128 or 256 columns (0 = auto) */
     int use_graph;              /* capture each call shape's launch sequence in a CUDA graph and
                                    replay it (default 1; calls with kernel timing run uncaptured) */
+    int overlap_batches;        /* 1: with two or more batches, build the Z matrices of one batch
+                                   on a second stream while the HERK of the previous one runs (two
+                                   workspace sets); 0 (default): one set, strictly in order */
 } mv_options;
 
 /* A tensor-core HERK configuration chosen by mv_autotune. */

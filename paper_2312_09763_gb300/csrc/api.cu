@@ -59,8 +59,12 @@ struct mv_ctx {
     // model buffers
     Buf xeq, sqrt_flux, half_alpha, ant_e, ant_n, ant_u, bidx, grid;
     // workspace
-    Buf R, counts, offsets, le, ln, lu, lidx, lazza, nlive, chan, inst, groups, planes, wa, amax, u, ulo, vdev, err,
-        partial, sched;
+    Buf R, counts, offsets, le, ln, lu, lidx, lazza, nlive, chan, inst, groups, planes, vdev, err, partial, sched;
+    // per-batch workspace, double-buffered so that the beam evaluation and Z
+    // build of one batch (on zstream) overlap the HERK of the previous one
+    Buf wa[2], amax[2], u[2], ulo[2];
+    cudaStream_t zstream = nullptr;
+    cudaEvent_t ev_prep = nullptr, ev_zdone[2] = {nullptr, nullptr}, ev_hdone[2] = {nullptr, nullptr};
     int n_sms = 148;
     long long model_version = 0;  // bumped by every set-up call (kernel arguments embed the model)
     // autotuned HERK configuration, valid for calls of the same shape
@@ -317,6 +321,7 @@ void plan_pairs(mv_ctx* c, int n_pairs, const double* lst, const double* nu, Pla
 struct Prepared {
     int n_times = 0, n_chan = 0, n_inst = 0;
     int N = 0, rows = 0, bpt = 0, ncomp = 0, max_slots = 0, zprec = 0;
+    int nbuf = 1;  // workspace sets in use (2: Z side and HERK overlap)
     long long pitch = 0, k_pitch = 0;
     LiveTables lt{};
     float2* Vout = nullptr;
@@ -423,15 +428,22 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if ((s = ensure(c, c->lidx, sizeof(int) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lazza, sizeof(float2) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
-    if ((s = ensure(c, c->wa, sizeof(float2) * (size_t)max_slots * p.ncomp * pitch))) return s;
-    if ((s = ensure(c, c->amax, sizeof(float) * (size_t)max_slots))) return s;
+    p.nbuf = (P.batches.size() > 1 && c->opt.overlap_batches) ? 2 : 1;
+    for (int k = 0; k < p.nbuf; ++k) {
+        if ((s = ensure(c, c->wa[k], sizeof(float2) * (size_t)max_slots * p.ncomp * pitch))) return s;
+        if ((s = ensure(c, c->amax[k], sizeof(float) * (size_t)max_slots))) return s;
+    }
     if ((s = ensure(c, c->sched, sizeof(int) * (size_t)(max_slots + 8)))) return s;
     const size_t plane_elems = (size_t)p.rows * p.k_pitch * max_slots;
-    if (p.zprec == 0) {
-        if ((s = ensure(c, c->u, sizeof(float) * plane_elems))) return s;
-    } else {
-        if ((s = ensure(c, c->u, 2 * plane_elems))) return s;
-        if ((s = ensure(c, c->ulo, 2 * plane_elems))) return s;
+    for (int k = 0; k < p.nbuf; ++k) {
+        if (p.zprec == 0) {
+            if ((s = ensure(c, c->u[k], sizeof(float) * plane_elems))) return s;
+        } else {
+            if ((s = ensure(c, c->u[k], 2 * plane_elems))) return s;
+            if ((s = ensure(c, c->ulo[k], 2 * plane_elems))) return s;
+        }
+    }
+    if (p.zprec != 0) {
         // partial tiles for the largest split any configuration may use
         const HerkCfg h = chosen_cfg(c, p);
         const size_t need = sizeof(float) * 128 * h.bn * (size_t)herk_tc_units(p.rows, max_slots, h.split, h.bn);
@@ -458,33 +470,33 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
 }
 
 // HERK of one batch with configuration h.
-cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, const HerkCfg& h, cudaStream_t st,
-                         long long* L) {
+cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, const HerkCfg& h, int k,
+                         cudaStream_t st, long long* L) {
     const Inst* d_inst = (const Inst*)c->inst.p;
     if (p.zprec == 0)
-        return launch_herk_fp32(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const float*)c->u.p, p.rows, p.k_pitch,
-                                p.Vout, p.N, 256, st, L);
-    return launch_herk_tc(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const __nv_bfloat16*)c->u.p,
-                          (const __nv_bfloat16*)c->ulo.p, p.rows, p.k_pitch, p.max_slots, p.zprec == 2 ? 1 : 0,
-                          (const float*)c->amax.p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
+        return launch_herk_fp32(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const float*)c->u[k].p, p.rows,
+                                p.k_pitch, p.Vout, p.N, 256, st, L);
+    return launch_herk_tc(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const __nv_bfloat16*)c->u[k].p,
+                          (const __nv_bfloat16*)c->ulo[k].p, p.rows, p.k_pitch, p.max_slots, p.zprec == 2 ? 1 : 0,
+                          (const float*)c->amax[k].p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
                           (float*)c->partial.p, (int*)c->err.p, st, L);
 }
 
 // Beam evaluation and Z build of one batch.
-mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, cudaStream_t st, long long* L) {
+mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, cudaStream_t st, long long* L) {
     mv_status s;
     const Model& m = c->model;
     const Inst* d_inst = (const Inst*)c->inst.p;
-    if ((s = cuda_check(cudaMemsetAsync(c->amax.p, 0, sizeof(float) * b.n, st), "amax reset"))) return s;
+    if ((s = cuda_check(cudaMemsetAsync(c->amax[k].p, 0, sizeof(float) * b.n, st), "amax reset"))) return s;
     Timed tw(c, MV_KERNEL_BEAM, st);
     cudaError_t e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, p.lt,
-                              (float2*)c->wa.p, p.pitch, (float*)c->amax.p, st, L);
+                              (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
     tw.end();
     if ((s = launched(e, "beam evaluation", st))) return s;
     Timed tz(c, MV_KERNEL_ZBUILD, st);
     e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, p.lt,
-                      (const float2*)c->wa.p, p.pitch, (const float*)c->amax.p, c->u.p, c->ulo.p, p.zprec, p.rows,
-                      p.k_pitch, st, L);
+                      (const float2*)c->wa[k].p, p.pitch, (const float*)c->amax[k].p, c->u[k].p, c->ulo[k].p,
+                      p.zprec, p.rows, p.k_pitch, p.nbuf == 2 ? 4 * c->n_sms : 0, st, L);
     tz.end();
     return launched(e, "Z build", st);
 }
@@ -506,23 +518,46 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, const Prepared& p, const HerkCfg& h, c
         tb.end();
         if ((s = launched(e, "beam planes", st))) return s;
     }
-    for (const auto& b : P.batches) {
-        if ((s = enqueue_zside(c, p, b, st, L))) return s;
+    if (p.nbuf == 1) {
+        for (const auto& b : P.batches) {
+            if ((s = enqueue_zside(c, p, b, 0, st, L))) return s;
+            Timed th(c, MV_KERNEL_HERK, st);
+            e = enqueue_herk(c, p, b, h, 0, st, L);
+            th.end();
+            if ((s = launched(e, p.zprec == 0 ? "HERK fp32" : "HERK tc", st))) return s;
+        }
+        return MV_OK;
+    }
+    // Two workspace sets: batch b builds Z into set b % 2 on zstream while the
+    // HERK of batch b - 1 reads the other set on st.  zstream first waits for
+    // everything already queued on st (earlier calls included); before reusing
+    // a set it waits for the HERK that read it.
+    cudaStream_t zs = c->zstream;
+    if ((s = cuda_check(cudaEventRecord(c->ev_prep, st), "event"))) return s;
+    if ((s = cuda_check(cudaStreamWaitEvent(zs, c->ev_prep, 0), "event wait"))) return s;
+    for (size_t i = 0; i < P.batches.size(); ++i) {
+        const auto& b = P.batches[i];
+        const int k = (int)(i & 1);
+        if (i >= 2 && (s = cuda_check(cudaStreamWaitEvent(zs, c->ev_hdone[k], 0), "event wait"))) return s;
+        if ((s = enqueue_zside(c, p, b, k, zs, L))) return s;
+        if ((s = cuda_check(cudaEventRecord(c->ev_zdone[k], zs), "event"))) return s;
+        if ((s = cuda_check(cudaStreamWaitEvent(st, c->ev_zdone[k], 0), "event wait"))) return s;
         Timed th(c, MV_KERNEL_HERK, st);
-        e = enqueue_herk(c, p, b, h, st, L);
+        e = enqueue_herk(c, p, b, h, k, st, L);
         th.end();
         if ((s = launched(e, p.zprec == 0 ? "HERK fp32" : "HERK tc", st))) return s;
+        if ((s = cuda_check(cudaEventRecord(c->ev_hdone[k], st), "event"))) return s;
     }
     return MV_OK;
 }
 
 // Key of a captured launch sequence: every value its kernel arguments depend on.
 std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, const HerkCfg& h) {
-    std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch,
+    std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch, p.nbuf,
                                 h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout, c->model_version};
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
-                         &c->lidx, &c->lazza, &c->nlive, &c->wa, &c->amax, &c->sched, &c->u, &c->ulo, &c->partial,
-                         &c->planes, &c->grid, &c->err};
+                         &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
+                         &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err};
     for (const Buf* b : bufs) k.push_back((long long)(uintptr_t)b->p);
     for (const auto& b : P.batches) {
         k.push_back(b.inst0);
@@ -628,16 +663,16 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
                                st, &L);
         if ((s = cuda_check(e, "beam planes"))) return s;
     }
-    if ((s = enqueue_zside(c, p, b0, st, &L))) return s;
+    if ((s = enqueue_zside(c, p, b0, 0, st, &L))) return s;
     cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
     HerkCfg best;
     double best_ms = 1e300;
     for (const auto& h : cands) {
-        if ((s = cuda_check(enqueue_herk(c, p, b0, h, st, &L), "trial HERK"))) return s;  // warm-up
+        if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L), "trial HERK"))) return s;  // warm-up
         cudaEventRecord(e0, st);
         const int reps = 2;
         for (int r = 0; r < reps; ++r)
-            if ((s = cuda_check(enqueue_herk(c, p, b0, h, st, &L), "trial HERK"))) return s;
+            if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L), "trial HERK"))) return s;
         cudaEventRecord(e1, st);
         if ((s = cuda_check(cudaEventSynchronize(e1), "trial timing"))) return s;
         float ms = 0.f;
@@ -708,9 +743,16 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
         delete c;
         return fail(MV_ERR_ARG, "unknown interpolation %d", c->opt.interp);
     }
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-        delete c;
-        return fail(MV_ERR_CUDA, "stream creation failed");
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->zstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_zdone[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_zdone[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_hdone[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_hdone[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        mv_destroy(c);
+        return fail(MV_ERR_CUDA, "stream or event creation failed");
     }
     mv_status s = ensure(c, c->err, sizeof(int));
     if (s == MV_OK) s = cuda_check(cudaMemset(c->err.p, 0, sizeof(int)), "status word");
@@ -728,12 +770,16 @@ void mv_destroy(mv_ctx* c) {
     cudaDeviceSynchronize();
     Buf* all[] = {&c->xeq, &c->sqrt_flux, &c->half_alpha, &c->ant_e, &c->ant_n, &c->ant_u, &c->bidx, &c->grid,
                   &c->R, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu, &c->lidx, &c->lazza, &c->nlive,
-                  &c->chan, &c->inst, &c->groups, &c->planes, &c->wa, &c->amax, &c->u, &c->ulo, &c->vdev, &c->err,
+                  &c->chan, &c->inst, &c->groups, &c->planes, &c->wa[0], &c->amax[0], &c->u[0], &c->ulo[0],
+                  &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->vdev, &c->err,
                   &c->partial, &c->sched};
     for (Buf* b : all) buf_free(c, *b);
     harvest(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (cudaEvent_t e : {c->ev_prep, c->ev_zdone[0], c->ev_zdone[1], c->ev_hdone[0], c->ev_hdone[1]})
+        if (e) cudaEventDestroy(e);
+    if (c->zstream) cudaStreamDestroy(c->zstream);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -94,7 +94,7 @@ struct ZGroup {
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
                           int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
                           const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows,
-                          long long k_pitch, cudaStream_t st, long long* launches);
+                          long long k_pitch, int max_blocks, cudaStream_t st, long long* launches);
 cudaError_t launch_herk_fp32(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                              const float* d_u, int rows, long long k_pitch, float2* d_v, int N,
                              int flush_k, cudaStream_t st, long long* launches);

@@ -13,6 +13,8 @@
 // (antenna, source) and the channel phases are stepped by exact 64-bit
 // integer addition of their fractions.
 #include <cuda_fp16.h>
+
+#include <algorithm>
 #include "common.cuh"
 
 namespace mv {
@@ -92,22 +94,23 @@ __device__ __forceinline__ void put_row(void* u, void* ulo, long long o, const f
     }
 }
 
-// One thread builds two adjacent sources (columns 2 n_ax wide) for a range of
-// antennas and every instance of its group.  Sources past the live count
-// (up to the k padding) are written as zeros.
+// One work item (bx, by, bz): thread t builds the two adjacent sources
+// 2 (bx 128 + t) and +1 (columns 2 n_ax wide) for antennas
+// [by ant_per_block, +ant_per_block) and every instance of group bz.
+// Sources past the live count (up to the k padding) are written as zeros.
 template <int PREC, int NAX>
-__global__ void __launch_bounds__(128)
-k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
-         const ZGroup* __restrict__ groups, int g_first, LiveTables lt, const float2* __restrict__ wa,
-         long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo, int rows, long long k_pitch,
-         int ant_per_block) {
-    const ZGroup g = groups[g_first + blockIdx.z];
+__device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restrict__ inst,
+                                            const Chan* __restrict__ chan, const ZGroup* __restrict__ groups,
+                                            int g_first, const LiveTables& lt, const float2* __restrict__ wa,
+                                            long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo,
+                                            int rows, long long k_pitch, int ant_per_block, int bx, int by, int bz) {
+    const ZGroup g = groups[g_first + bz];
     const int t = inst[g.inst0].t;
     const int nl = lt.n_live[t];
     const long long kpad = ((long long)nl * NAX + kKPad - 1) / kKPad * kKPad;
-    const int s0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int s0 = 2 * (bx * blockDim.x + threadIdx.x);
     if ((long long)s0 * NAX >= kpad) return;
-    const int a_begin = blockIdx.y * ant_per_block;
+    const int a_begin = by * ant_per_block;
     const int a_end = min(m.n_ant, a_begin + ant_per_block);
     const long long slot_stride = (long long)rows * k_pitch;
     const int nfd = m.n_feed;
@@ -168,17 +171,35 @@ k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
     }
 }
 
+// Grid-stride over the work items, so that the launch can be held to a fixed
+// number of resident blocks per SM (room left for a concurrent HERK).
+template <int PREC, int NAX>
+__global__ void __launch_bounds__(128, 8)
+k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
+         const ZGroup* __restrict__ groups, int g_first, LiveTables lt, const float2* __restrict__ wa,
+         long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo, int rows, long long k_pitch,
+         int ant_per_block, int nx, int ny, long long n_items) {
+    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int bx = (int)(item % nx);
+        const long long rest = item / nx;
+        zbuild_item<PREC, NAX>(m, inst, chan, groups, g_first, lt, wa, wa_pitch, amax, u, ulo, rows, k_pitch,
+                               ant_per_block, bx, (int)(rest % ny), (int)(rest / ny));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
                           int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
                           const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows, long long k_pitch,
-                          cudaStream_t st, long long* launches) {
+                          int max_blocks, cudaStream_t st, long long* launches) {
     const int apb = 32;
-    dim3 grid((unsigned)((lt.pitch / 2 + 127) / 128), (m.n_ant + apb - 1) / apb, n_groups);
+    const int nx = (int)((lt.pitch / 2 + 127) / 128), ny = (m.n_ant + apb - 1) / apb;
+    const long long n_items = (long long)nx * ny * n_groups;
+    const long long grid = max_blocks > 0 ? std::min<long long>(n_items, max_blocks) : n_items;
 #define MV_ZB(P, A) \
-    k_zbuild<P, A><<<grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u, d_u_lo, \
-                                         rows, k_pitch, apb)
+    k_zbuild<P, A><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, \
+                                                   d_u, d_u_lo, rows, k_pitch, apb, nx, ny, n_items)
     if (m.n_ax == 1) {
         if (prec == 0) MV_ZB(0, 1); else if (prec == 1) MV_ZB(1, 1); else MV_ZB(2, 1);
     } else {

@@ -55,7 +55,20 @@ def test_graph_replay_matches_uncaptured_run():
     assert sim.last_launch_count() > 0
 
 
-@pytest.mark.parametrize("tile_n,split,flush", [(128, 1, 4), (128, 8, 1), (256, 1, 8), (256, 5, 2), (256, 64, 4)])
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+def test_overlapped_batches_match_serial(prec):
+    # batches of 2 channels: the Z side of batch b+1 overlaps the HERK of batch b
+    w = synth.hera_like(n_ant=90, n_src=12_000, n_chan=6, n_times=2, n_za=46, n_az=120)
+    a = simulator(w, max_batch=2).simulate(w.lsts, w.freqs, prec).cpu().numpy()
+    for use_graph in (False, True):
+        sim = simulator(w, max_batch=2, use_graph=use_graph, overlap_batches=True)
+        for _ in range(2):
+            assert np.array_equal(sim.simulate(w.lsts, w.freqs, prec).cpu().numpy(), a)
+    P = oracle_problem(w)
+    assert rel_err(a[1, 4], oracle.vis(P, w.lsts[1], w.freqs[4])) <= TOL[prec]
+
+
+@pytest.mark.parametrize("tile_n,split,flush",[(128, 1, 4), (128, 8, 1), (256, 1, 8), (256, 5, 2), (256, 64, 4)])
 def test_herk_configurations(tile_n, split, flush):
     # multi-tile, ragged rows (2 x 150 = 300) and ragged splits of the source axis
     w = synth.hera_like(n_ant=150, n_src=9_000, n_chan=3, n_times=2, n_za=46, n_az=120)
