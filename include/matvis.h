@@ -223,6 +223,68 @@ mv_status mv_horizon_cull_static(int64_t n_src, const double *xeq_dev, double ls
                                  int32_t *live_idx_dev, double *enu_dev, float *azza_dev,
                                  int32_t *n_live_dev, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Learned beam.  The paper interpolates gridded beams (Sec. 2.4) and notes
+ * that per-antenna beams make that step expensive (Sec. 3.1); here a
+ * Fourier-feature MLP stands in for a set of gridded beams:
+ *   x = (az / 2 pi, za / (pi/2), (nu - nu_mid) / nu_half), nu_mid and nu_half
+ *       the centre and half-width of the grid's frequency range;
+ *   f = [sin(2 pi B x), cos(2 pi B x), e_beta]  (B: n_freq x 3 fixed, az column
+ *       integer so az stays periodic; e_beta the learned embedding of beam beta);
+ *   h_l = relu(W_l h_{l-1} + b_l) for depth hidden layers of `width` units;
+ *   y = W_out h + b_out: 2 n_feed n_ax real outputs (re, im of each component
+ *       in (feed, axis) order).
+ * It is trained on the GPU (BF16 tensor-core products, FP32 master weights,
+ * Adam, MSE) on samples (beta, az, za, nu) drawn uniformly and labelled by the
+ * Keys interpolation of the gridded beam set with mv_set_beam_grid, one
+ * embedding per gridded beam. */
+typedef struct {
+    int n_freq;                          /* Fourier frequencies (default 64) */
+    int emb_dim;                         /* embedding size (16) */
+    int width;                           /* hidden width (256) */
+    int depth;                           /* hidden layers (4) */
+    float sigma_az, sigma_za, sigma_nu;  /* scales of B's columns (2, 3, 1) */
+    uint64_t seed;                       /* initial weights and B */
+} mv_mlp_config;
+
+void mv_default_mlp_config(mv_mlp_config *cfg);
+
+/* Create (or replace) the surrogate for the current gridded beams.  cfg may be
+ * NULL (defaults).  MV_ERR_STATE without a gridded beam. */
+mv_status mv_surrogate_create(mv_ctx *ctx, const mv_mlp_config *cfg);
+
+/* Train for `steps` Adam steps of `batch` samples (batch a multiple of 8), the
+ * learning rate following a cosine from lr0 to lr1; sample draws use `seed`.
+ * loss_first / loss_last (may be NULL) receive the MSE of the first and last
+ * step.  Synchronises. */
+mv_status mv_surrogate_train(mv_ctx *ctx, int steps, int batch, float lr0, float lr1, uint64_t seed,
+                             double *loss_first, double *loss_last);
+
+/* Parameters: *n_params receives the count; if host != NULL the FP32 master
+ * vector is copied there; if fourier != NULL, B ([n_freq][3]); if layout !=
+ * NULL, 2 (depth + 1) + 2 offsets: W_l, b_l for l = 0..depth (W_depth is the
+ * output layer, stored [8][width]; W_0 is [width][d0p] with d0p = 2 n_freq +
+ * emb_dim rounded up to 32), then the embedding offset and d0p. */
+mv_status mv_surrogate_params(mv_ctx *ctx, int64_t *n_params, float *host, float *fourier, int64_t *layout);
+mv_status mv_surrogate_set_params(mv_ctx *ctx, const float *host);
+
+/* Evaluate at n points (host arrays): out [n][2 n_feed n_ax] host. */
+mv_status mv_surrogate_eval(mv_ctx *ctx, int n, const int32_t *beam, const double *az, const double *za,
+                            const double *nu, float *out);
+
+/* Loss and gradient of all parameters for n given samples and targets
+ * ([n][2 n_feed n_ax]); grads [n_params] host, no update.  n a multiple of 8. */
+mv_status mv_surrogate_grad(mv_ctx *ctx, int n, const int32_t *beam, const double *az, const double *za,
+                            const double *nu, const float *target, float *grads, double *loss);
+
+/* Save / load the surrogate (configuration, B and parameters) to a file. */
+mv_status mv_surrogate_save(mv_ctx *ctx, const char *path);
+mv_status mv_surrogate_load(mv_ctx *ctx, const char *path);
+
+/* enable != 0: mv_simulate evaluates the beams with the surrogate (antenna a
+ * uses embedding beam_idx[a]) instead of interpolating the grid. */
+mv_status mv_set_beam_surrogate(mv_ctx *ctx, int enable);
+
 /* enable != 0 switches timing on and clears the counters; 0 switches it off. */
 mv_status mv_profile_enable(mv_ctx *ctx, int enable);
 

@@ -156,6 +156,14 @@ class Problem:
             p.grid = _ptr(g)
             p.nu0, p.dnu, p.dza, p.daz = float(nu0), float(dnu), float(dza), float(daz)
             p.interp = {"cubic": 0, "bilinear": 1}[interp]
+        elif kind == "table":
+            # caller-evaluated beams at the live sources: complex [beam][feed][ax][n_live]
+            g = np.ascontiguousarray(np.asarray(self.beam[1], dtype=np.complex128))
+            assert g.ndim == 4
+            keep.append(g)
+            p.beam_kind = 3
+            p.n_beam, p.n_feed, p.n_ax = g.shape[:3]
+            p.grid = _ptr(g)
         else:
             raise ValueError(kind)
         self._keep = keep
@@ -249,3 +257,20 @@ def vis_outer(prob: Problem, lst: float, nu: float) -> np.ndarray:
     if rc:
         raise ValueError("frequency outside the beam grid")
     return out
+
+
+def live_directions(prob: Problem, lst: float):
+    """(az, za) of the live sources (Up > 0), in catalogue order."""
+    enu = to_topo(rotation(lst, prob.lat), xeq(prob.ra, prob.dec))
+    live = enu[:, 2] > 0
+    return azza(enu[live])
+
+
+def vis_with_beam_fn(prob: Problem, lst: float, nu: float, beam_fn, pairs=None, threads=None) -> np.ndarray:
+    """Direct per-baseline sum with the beams given by a caller's model:
+    beam_fn(az, za, nu) -> complex [beam][feed][ax][n] at the live sources."""
+    az, za = live_directions(prob, lst)
+    table = np.asarray(beam_fn(az, za, nu), dtype=np.complex128)
+    q = Problem(ra=prob.ra, dec=prob.dec, flux_ref=prob.flux_ref, enu=prob.enu, lat=prob.lat,
+                beam=("table", table), spec_idx=prob.spec_idx, nu_ref=prob.nu_ref, beam_idx=prob.beam_idx)
+    return vis(q, lst, nu, pairs=pairs, threads=threads)

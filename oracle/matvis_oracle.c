@@ -64,7 +64,7 @@ typedef struct {
     const int32_t *beam_idx;     /* may be NULL (all zero) */
     double lat;                  /* radians */
     /* beam */
-    int32_t beam_kind;           /* 0 uniform, 1 gaussian, 2 grid */
+    int32_t beam_kind;           /* 0 uniform, 1 gaussian, 2 grid, 3 tabulated (see inst_prepare) */
     double fwhm;                 /* radians (gaussian) */
     int32_t n_beam, n_feed, n_ax;
     int32_t n_nu, n_za, n_az;
@@ -214,7 +214,7 @@ static int beam_eval(const orc_problem *P, int b, int p, int k,
 int orc_beam_eval_many(const orc_problem *P, int64_t n, const double *az,
                        const double *za, double nu, double *out)
 {
-    int nb = P->beam_kind == 2 ? P->n_beam : 1;
+    int nb = P->beam_kind >= 2 ? P->n_beam : 1;
     for (int b = 0; b < nb; ++b)
         for (int p = 0; p < P->n_feed; ++p)
             for (int k = 0; k < P->n_ax; ++k)
@@ -257,7 +257,7 @@ static int inst_prepare(const orc_problem *P, double lst, double nu, orc_inst *I
     int64_t m = 0;
     for (int64_t s = 0; s < n; ++s)
         if (enu[3 * s + 2] > 0.0) ++m;
-    int nb = P->beam_kind == 2 ? P->n_beam : 1;
+    int nb = P->beam_kind >= 2 ? P->n_beam : 1;
     int64_t mm = m > 0 ? m : 1;
     I->n_live = m;
     I->enu = malloc(sizeof(double) * 3 * mm);
@@ -275,7 +275,14 @@ static int inst_prepare(const orc_problem *P, double lst, double nu, orc_inst *I
         ++j;
     }
     orc_azza(m, I->enu, az, za);
-    int rc = orc_beam_eval_many(P, m, az, za, nu, I->A);
+    int rc = 0;
+    if (P->beam_kind == 3) {
+        /* tabulated: P->grid holds complex128 [beam][feed][ax][m] for the live
+         * sources in catalogue order (a caller-evaluated beam model) */
+        memcpy(I->A, P->grid, sizeof(double) * 2 * (size_t)nb * P->n_feed * P->n_ax * (size_t)m);
+    } else {
+        rc = orc_beam_eval_many(P, m, az, za, nu, I->A);
+    }
     free(az); free(za); free(xyz); free(enu);
     if (rc) inst_free(I);
     return rc;
@@ -321,8 +328,8 @@ int orc_vis(const orc_problem *P, double lst, double nu, int64_t n_pairs,
         if (n_pairs < 0) { a = (int)(q / na); b = (int)(q % na); }
         else { a = pa[q]; b = pb[q]; }
         if (a < 0 || a >= na || b < 0 || b >= na) { bad = 1; continue; }
-        int ba = P->beam_kind == 2 && P->beam_idx ? P->beam_idx[a] : 0;
-        int bb = P->beam_kind == 2 && P->beam_idx ? P->beam_idx[b] : 0;
+        int ba = P->beam_kind >= 2 && P->beam_idx ? P->beam_idx[a] : 0;
+        int bb = P->beam_kind >= 2 && P->beam_idx ? P->beam_idx[b] : 0;
         double bx = P->enu[3 * a] - P->enu[3 * b];
         double by = P->enu[3 * a + 1] - P->enu[3 * b + 1];
         double bz = P->enu[3 * a + 2] - P->enu[3 * b + 2];
@@ -376,7 +383,7 @@ int orc_vis_outer(const orc_problem *P, double lst, double nu, double *out)
     const double kappa = nu / ORC_C_LIGHT;
     double *Z = malloc(sizeof(double) * 2 * (size_t)(N > 0 ? N : 1) * (M > 0 ? M : 1));
     for (int a = 0; a < na; ++a) {
-        int ba = P->beam_kind == 2 && P->beam_idx ? P->beam_idx[a] : 0;
+        int ba = P->beam_kind >= 2 && P->beam_idx ? P->beam_idx[a] : 0;
         for (int64_t s = 0; s < K; ++s) {
             const double *x = &I.enu[3 * s];
             double tau = (P->enu[3 * a] * x[0] + P->enu[3 * a + 1] * x[1]) + P->enu[3 * a + 2] * x[2];

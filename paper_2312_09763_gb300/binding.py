@@ -26,7 +26,10 @@ INTERP = {"cubic": 0, "bilinear": 1}
 EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv_init_sky",
            "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas", "mv_simulate",
            "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts", "mv_last_launch_count",
-           "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static", "mv_autotune"]
+           "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static", "mv_autotune",
+           "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
+           "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
+           "mv_surrogate_load", "mv_set_beam_surrogate"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -48,6 +51,12 @@ class _Options(ctypes.Structure):
     _fields_ = [("interp", ctypes.c_int), ("max_batch", ctypes.c_int), ("herk_flush_kblocks", ctypes.c_int),
                 ("herk_split", ctypes.c_int), ("allocator", _Allocator), ("herk_tile_n", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("overlap_batches", ctypes.c_int)]
+
+
+class _MlpConfig(ctypes.Structure):
+    _fields_ = [("n_freq", ctypes.c_int), ("emb_dim", ctypes.c_int), ("width", ctypes.c_int), ("depth", ctypes.c_int),
+                ("sigma_az", ctypes.c_float), ("sigma_za", ctypes.c_float), ("sigma_nu", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
 
 
 class _Tuning(ctypes.Structure):
@@ -91,6 +100,21 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_horizon_cull_static.restype = i32
     lib.mv_autotune.argtypes = [vp, i32, vp, i32, vp, i32, i32, vp]
     lib.mv_autotune.restype = i32
+    lib.mv_default_mlp_config.argtypes = [ctypes.POINTER(_MlpConfig)]
+    lib.mv_default_mlp_config.restype = None
+    lib.mv_surrogate_create.argtypes = [vp, ctypes.POINTER(_MlpConfig)]
+    lib.mv_surrogate_train.argtypes = [vp, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    lib.mv_surrogate_params.argtypes = [vp, vp, vp, vp, vp]
+    lib.mv_surrogate_set_params.argtypes = [vp, vp]
+    lib.mv_surrogate_eval.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.mv_surrogate_grad.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.mv_surrogate_save.argtypes = [vp, ctypes.c_char_p]
+    lib.mv_surrogate_load.argtypes = [vp, ctypes.c_char_p]
+    lib.mv_set_beam_surrogate.argtypes = [vp, i32]
+    for name in ("mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params", "mv_surrogate_set_params",
+                 "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save", "mv_surrogate_load",
+                 "mv_set_beam_surrogate"):
+        getattr(lib, name).restype = i32
     for name in ("mv_create", "mv_init_sky", "mv_set_beam_gaussian", "mv_set_beam_grid", "mv_set_antennas",
                  "mv_simulate", "mv_simulate_pairs", "mv_check_device_status", "mv_last_live_counts",
                  "mv_profile_enable", "mv_profile_read"):
@@ -179,6 +203,7 @@ class Simulator:
         self._check(self._lib.mv_set_beam_grid(self._h, nb, nf, na, nn, nz, naz, _p(v), float(nu0), float(dnu),
                                                float(dza), float(daz)))
         self.n_feed = nf
+        self.n_ax = na
 
     def set_beam(self, beam: tuple):
         """beam = ("gaussian", fwhm) or ("grid", values, nu0, dnu, dza, daz[, interp])."""
@@ -261,6 +286,69 @@ class Simulator:
                                           1 if pairs else 0, ctypes.byref(t)))
         return {"tile_n": t.tile_n, "split": t.split, "flush_kblocks": t.flush_kblocks,
                 "candidates": t.candidates, "herk_ms": t.herk_ms}
+
+    # --------------------------------------------------------- learned beam
+    def surrogate_create(self, n_freq=64, emb_dim=16, width=256, depth=4, sigma_az=2.0, sigma_za=3.0, sigma_nu=1.0,
+                         seed=20231213):
+        """Fourier-feature MLP standing in for the current gridded beams."""
+        c = _MlpConfig(n_freq, emb_dim, width, depth, sigma_az, sigma_za, sigma_nu, seed)
+        self._check(self._lib.mv_surrogate_create(self._h, ctypes.byref(c)))
+        self._mlp = dict(n_freq=n_freq, emb_dim=emb_dim, width=width, depth=depth)
+
+    def surrogate_train(self, steps: int, batch: int, lr0: float = 1e-3, lr1: float = 1e-5, seed: int = 1):
+        """Adam on samples labelled by the gridded beams; returns (first, last) loss."""
+        l0, l1 = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.mv_surrogate_train(self._h, steps, batch, lr0, lr1, seed, ctypes.byref(l0),
+                                                 ctypes.byref(l1)))
+        return l0.value, l1.value
+
+    def surrogate_params(self):
+        """(FP32 parameter vector, Fourier matrix [F][3], layout offsets)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.mv_surrogate_params(self._h, ctypes.byref(n), None, None, None))
+        p = np.empty(n.value, dtype=np.float32)
+        B = np.empty((self._mlp["n_freq"], 3), dtype=np.float32)
+        lay = np.empty(2 * (self._mlp["depth"] + 1) + 2, dtype=np.int64)
+        self._check(self._lib.mv_surrogate_params(self._h, ctypes.byref(n), _p(p), _p(B), _p(lay)))
+        return p, B, lay
+
+    def surrogate_set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.mv_surrogate_set_params(self._h, _p(p)))
+
+    def surrogate_eval(self, beam, az, za, nu):
+        beam = np.ascontiguousarray(beam, dtype=np.int32)
+        az, za, nu = _f64(az), _f64(za), _f64(nu)
+        out = np.empty((beam.size, 2 * self.n_feed * self._n_ax()), dtype=np.float32)
+        self._check(self._lib.mv_surrogate_eval(self._h, beam.size, _p(beam), _p(az), _p(za), _p(nu), _p(out)))
+        return out
+
+    def surrogate_grad(self, beam, az, za, nu, target):
+        """(gradient of every parameter, loss) for given samples; no update."""
+        beam = np.ascontiguousarray(beam, dtype=np.int32)
+        az, za, nu = _f64(az), _f64(za), _f64(nu)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        n = ctypes.c_int64()
+        self._check(self._lib.mv_surrogate_params(self._h, ctypes.byref(n), None, None, None))
+        g = np.empty(n.value, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.mv_surrogate_grad(self._h, beam.size, _p(beam), _p(az), _p(za), _p(nu), _p(t), _p(g),
+                                                ctypes.byref(loss)))
+        return g, loss.value
+
+    def surrogate_save(self, path: str):
+        self._check(self._lib.mv_surrogate_save(self._h, str(path).encode()))
+
+    def surrogate_load(self, path: str, **cfg):
+        self._check(self._lib.mv_surrogate_load(self._h, str(path).encode()))
+        if cfg:
+            self._mlp = dict(cfg)
+
+    def set_beam_surrogate(self, enable: bool = True):
+        self._check(self._lib.mv_set_beam_surrogate(self._h, 1 if enable else 0))
+
+    def _n_ax(self) -> int:
+        return getattr(self, "n_ax", 1)
 
     def profile_enable(self, enable: bool = True):
         """Time every kernel launch with CUDA events (clears the counters)."""

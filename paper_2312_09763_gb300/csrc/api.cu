@@ -80,6 +80,10 @@ struct mv_ctx {
     long long graph_launches = 0;
     long long launches = 0;
     std::vector<int> last_inst_t;
+    // learned beam
+    Surrogate* sur = nullptr;
+    bool use_sur = false;
+    mv_mlp_config sur_cfg{};
     // kernel timing
     bool profiling = false;
     struct Rec { int kind; cudaEvent_t a, b; };
@@ -279,9 +283,13 @@ int auto_batch(mv_ctx* c, long long slot_bytes) {
     return (int)std::max(1ll, std::min(b, 64ll));
 }
 
+// Workspace of one instance slot: the Z planes plus its beam x sqrt(I) table.
 long long slot_bytes_of(mv_ctx* c) {
-    const long long N = (long long)c->model.n_feed * c->model.n_ant;
-    return 4ll * 2 * N * round_up((long long)c->model.n_ax * std::max<long long>(c->model.n_src, 1), kKPad);
+    const Model& m = c->model;
+    const long long N = (long long)m.n_feed * m.n_ant;
+    const long long src = std::max<long long>(m.n_src, 1);
+    const long long ncomp = (long long)std::max(m.n_beam, 1) * std::max(m.n_feed, 1) * std::max(m.n_ax, 1);
+    return 4ll * 2 * N * round_up((long long)m.n_ax * src, kKPad) + 8ll * ncomp * round_up(src, kKPad);
 }
 
 // Every (LST, channel) pair; batches are up to B channels of one LST.
@@ -322,6 +330,8 @@ struct Prepared {
     int n_times = 0, n_chan = 0, n_inst = 0;
     int N = 0, rows = 0, bpt = 0, ncomp = 0, max_slots = 0, zprec = 0;
     int nbuf = 1;  // workspace sets in use (2: Z side and HERK overlap)
+    const Plan* plan = nullptr;
+    std::vector<int> h_nlive;  // live counts on the host (learned-beam calls only)
     long long pitch = 0, k_pitch = 0;
     LiveTables lt{};
     float2* Vout = nullptr;
@@ -489,8 +499,13 @@ mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int 
     const Inst* d_inst = (const Inst*)c->inst.p;
     if ((s = cuda_check(cudaMemsetAsync(c->amax[k].p, 0, sizeof(float) * b.n, st), "amax reset"))) return s;
     Timed tw(c, MV_KERNEL_BEAM, st);
-    cudaError_t e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, p.lt,
-                              (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
+    cudaError_t e;
+    if (c->use_sur)
+        e = surrogate_wa(c->sur, m, p.plan->inst, b.inst0, b.n, p.h_nlive, p.plan->nu, c->nu_ref, p.lt,
+                         (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
+    else
+        e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, p.lt,
+                      (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
     tw.end();
     if ((s = launched(e, "beam evaluation", st))) return s;
     Timed tz(c, MV_KERNEL_ZBUILD, st);
@@ -503,7 +518,7 @@ mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int 
 
 // The whole launch sequence of a call: cull, beam planes, then per batch
 // beam evaluation, Z build and HERK.
-mv_status enqueue_all(mv_ctx* c, Plan& P, const Prepared& p, const HerkCfg& h, cudaStream_t st, long long* L) {
+mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStream_t st, long long* L) {
     mv_status s;
     const Model& m = c->model;
     Timed tc0(c, MV_KERNEL_CULL, st);
@@ -511,7 +526,14 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, const Prepared& p, const HerkCfg& h, c
                                 p.bpt, st, L);
     tc0.end();
     if ((s = launched(e, "cull", st))) return s;
-    if (m.beam_kind == 2) {
+    if (c->use_sur) {
+        // the network's row count per instance is n_beam x live count: read them
+        p.h_nlive.assign(p.n_times, 0);
+        if ((s = cuda_check(cudaMemcpyAsync(p.h_nlive.data(), p.lt.n_live, sizeof(int) * p.n_times,
+                                            cudaMemcpyDeviceToHost, st), "live counts")))
+            return s;
+        if ((s = cuda_check(cudaStreamSynchronize(st), "synchronize"))) return s;
+    } else if (m.beam_kind == 2) {
         Timed tb(c, MV_KERNEL_BEAM, st);
         e = launch_beam_planes(m, (const float2*)c->grid.p, (const Chan*)c->chan.p, p.n_chan, (float2*)c->planes.p,
                                st, L);
@@ -578,7 +600,8 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     // CUDA graph: the launch sequence is captured once per key (on the
     // context's own stream) and replayed on the caller's stream.  Kernel
     // timing records events around single launches, so it runs uncaptured.
-    if (c->opt.use_graph && !c->profiling && !debug_sync()) {
+    p.plan = &P;
+    if (c->opt.use_graph && !c->profiling && !debug_sync() && !c->use_sur) {
         std::vector<long long> key = graph_key(c, P, p, h);
         if (!c->graph_exec || key != c->graph_key) {
             if (c->graph_exec) {
@@ -629,6 +652,7 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
 // keep the fastest for calls of the same shape.
 mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tuning* out) {
     if (prec == MV_PREC_FP32) return fail(MV_ERR_ARG, "the autotuner tunes the tensor-core HERK");
+    if (c->use_sur) return fail(MV_ERR_STATE, "autotune with the gridded beam (mv_set_beam_surrogate(ctx, 0))");
     c->tuned.valid = false;
     Prepared p;
     mv_status s;
@@ -774,6 +798,7 @@ void mv_destroy(mv_ctx* c) {
                   &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->vdev, &c->err,
                   &c->partial, &c->sched};
     for (Buf* b : all) buf_free(c, *b);
+    surrogate_destroy(c->sur);
     harvest(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -1004,6 +1029,209 @@ mv_status mv_profile_read(mv_ctx* c, int kind, int64_t* launches, double* total_
     harvest(c);
     *launches = c->prof_launches[kind];
     *total_ms = c->prof_ms[kind];
+    return MV_OK;
+}
+
+void mv_default_mlp_config(mv_mlp_config* cfg) {
+    if (!cfg) return;
+    cfg->n_freq = 64;
+    cfg->emb_dim = 16;
+    cfg->width = 256;
+    cfg->depth = 4;
+    cfg->sigma_az = 2.f;
+    cfg->sigma_za = 3.f;
+    cfg->sigma_nu = 1.f;
+    cfg->seed = 20231213ull;
+}
+
+mv_status mv_surrogate_create(mv_ctx* c, const mv_mlp_config* cfg) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (c->model.beam_kind != 2) return fail(MV_ERR_STATE, "the surrogate learns a gridded beam: set one first");
+    mv_mlp_config k;
+    mv_default_mlp_config(&k);
+    if (cfg) k = *cfg;
+    if (k.n_freq < 1 || k.n_freq > 512 || k.emb_dim < 1 || k.emb_dim > 256 || k.width < 8 || k.width > 1024 ||
+        k.width % 8 || k.depth < 1 || k.depth > 16)
+        return fail(MV_ERR_ARG, "MLP configuration out of range");
+    DeviceGuard g(c->device);
+    const Model& m = c->model;
+    const double nu_lo = c->grid_nu0, nu_hi = c->grid_nu0 + (m.n_nu - 1) * c->grid_dnu;
+    cudaError_t e = cudaSuccess;
+    Surrogate* S = surrogate_create(k.n_freq, k.emb_dim, k.width, k.depth, 2 * m.n_feed * m.n_ax, m.n_beam,
+                                    k.sigma_az, k.sigma_za, k.sigma_nu, k.seed, 0.5 * (nu_lo + nu_hi),
+                                    0.5 * (nu_hi - nu_lo), &e);
+    if (!S) return fail(MV_ERR_OOM, "surrogate allocation failed: %s", cudaGetErrorString(e));
+    surrogate_destroy(c->sur);
+    c->sur = S;
+    c->sur_cfg = k;
+    ++c->model_version;
+    return MV_OK;
+}
+
+mv_status mv_surrogate_train(mv_ctx* c, int steps, int batch, float lr0, float lr1, uint64_t seed,
+                             double* loss_first, double* loss_last) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (!c->sur) return fail(MV_ERR_STATE, "no surrogate: call mv_surrogate_create");
+    if (steps < 1 || batch < 8 || batch % 8 || batch > (1 << 24) || !(lr0 > 0) || !(lr1 >= 0))
+        return fail(MV_ERR_ARG, "steps >= 1, batch a multiple of 8, lr0 > 0, lr1 >= 0");
+    DeviceGuard g(c->device);
+    double l0 = 0, l1 = 0;
+    long long L = 0;
+    cudaError_t e = surrogate_train(c->sur, c->model, (const float2*)c->grid.p, c->grid_nu0, c->grid_dnu, steps, batch,
+                                    lr0, lr1, seed, c->stream, &l0, &l1, &L);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(MV_ERR_CUDA, "surrogate training: %s", cudaGetErrorString(e));
+    if (loss_first) *loss_first = l0;
+    if (loss_last) *loss_last = l1;
+    c->launches = L;
+    return MV_OK;
+}
+
+mv_status mv_surrogate_params(mv_ctx* c, int64_t* n_params, float* host, float* fourier, int64_t* layout) {
+    g_err.clear();
+    if (!c || !n_params) return fail(MV_ERR_ARG, "NULL argument");
+    if (!c->sur) return fail(MV_ERR_STATE, "no surrogate");
+    DeviceGuard g(c->device);
+    *n_params = surrogate_param_count(c->sur);
+    if (host) {
+        cudaError_t e = surrogate_get_params(c->sur, host);
+        if (e != cudaSuccess) return fail(MV_ERR_CUDA, "parameter copy: %s", cudaGetErrorString(e));
+    }
+    if (fourier) surrogate_fourier(c->sur, fourier);
+    if (layout) {
+        const int D = c->sur_cfg.depth;
+        std::vector<long long> ow(D + 1), ob(D + 1);
+        long long oe = 0;
+        int d0p = 0;
+        surrogate_layout(c->sur, ow.data(), ob.data(), &oe, &d0p);
+        for (int l = 0; l <= D; ++l) {
+            layout[2 * l] = ow[l];
+            layout[2 * l + 1] = ob[l];
+        }
+        layout[2 * (D + 1)] = oe;
+        layout[2 * (D + 1) + 1] = d0p;
+    }
+    return MV_OK;
+}
+
+mv_status mv_surrogate_set_params(mv_ctx* c, const float* host) {
+    g_err.clear();
+    if (!c || !host) return fail(MV_ERR_ARG, "NULL argument");
+    if (!c->sur) return fail(MV_ERR_STATE, "no surrogate");
+    DeviceGuard g(c->device);
+    cudaError_t e = surrogate_set_params(c->sur, host);
+    if (e != cudaSuccess) return fail(MV_ERR_CUDA, "parameter copy: %s", cudaGetErrorString(e));
+    ++c->model_version;
+    return MV_OK;
+}
+
+namespace {
+mv_status points(mv_ctx* c, int n, const int32_t* beam, const double* az, const double* za, const double* nu,
+                 std::vector<float>& faz, std::vector<float>& fza, std::vector<float>& fnu) {
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (!c->sur) return fail(MV_ERR_STATE, "no surrogate");
+    if (n < 1 || !beam || !az || !za || !nu) return fail(MV_ERR_ARG, "bad point arrays");
+    faz.resize(n);
+    fza.resize(n);
+    fnu.resize(n);
+    for (int i = 0; i < n; ++i) {
+        if (beam[i] < 0 || beam[i] >= c->model.n_beam) return fail(MV_ERR_ARG, "beam index %d out of range", beam[i]);
+        if (!std::isfinite(az[i]) || !std::isfinite(za[i]) || !std::isfinite(nu[i]))
+            return fail(MV_ERR_ARG, "point %d not finite", i);
+        faz[i] = (float)az[i];
+        fza[i] = (float)za[i];
+        fnu[i] = (float)nu[i];
+    }
+    return MV_OK;
+}
+}  // namespace
+
+mv_status mv_surrogate_eval(mv_ctx* c, int n, const int32_t* beam, const double* az, const double* za,
+                            const double* nu, float* out) {
+    g_err.clear();
+    std::vector<float> faz, fza, fnu;
+    mv_status s = points(c, n, beam, az, za, nu, faz, fza, fnu);
+    if (s) return s;
+    if (!out) return fail(MV_ERR_ARG, "out is NULL");
+    DeviceGuard g(c->device);
+    cudaError_t e = surrogate_eval(c->sur, n, beam, faz.data(), fza.data(), fnu.data(), out, c->stream);
+    if (e != cudaSuccess) return fail(MV_ERR_CUDA, "surrogate evaluation: %s", cudaGetErrorString(e));
+    return MV_OK;
+}
+
+mv_status mv_surrogate_grad(mv_ctx* c, int n, const int32_t* beam, const double* az, const double* za,
+                            const double* nu, const float* target, float* grads, double* loss) {
+    g_err.clear();
+    std::vector<float> faz, fza, fnu;
+    mv_status s = points(c, n, beam, az, za, nu, faz, fza, fnu);
+    if (s) return s;
+    if (n % 8 || !target || !grads || !loss) return fail(MV_ERR_ARG, "n a multiple of 8; target, grads, loss");
+    DeviceGuard g(c->device);
+    cudaError_t e = surrogate_grad(c->sur, n, beam, faz.data(), fza.data(), fnu.data(), target, grads, loss, c->stream);
+    if (e != cudaSuccess) return fail(MV_ERR_CUDA, "surrogate gradient: %s", cudaGetErrorString(e));
+    return MV_OK;
+}
+
+mv_status mv_surrogate_save(mv_ctx* c, const char* path) {
+    g_err.clear();
+    if (!c || !path) return fail(MV_ERR_ARG, "NULL argument");
+    if (!c->sur) return fail(MV_ERR_STATE, "no surrogate");
+    DeviceGuard g(c->device);
+    const long long n = surrogate_param_count(c->sur);
+    std::vector<float> p(n), B(3 * (size_t)c->sur_cfg.n_freq);
+    if (surrogate_get_params(c->sur, p.data()) != cudaSuccess) return fail(MV_ERR_CUDA, "parameter copy");
+    surrogate_fourier(c->sur, B.data());
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(MV_ERR_ARG, "cannot open %s for writing", path);
+    const char magic[8] = {'M', 'V', 'M', 'L', 'P', '0', '0', '1'};
+    const int32_t hdr[6] = {c->sur_cfg.n_freq, c->sur_cfg.emb_dim, c->sur_cfg.width, c->sur_cfg.depth,
+                            c->model.n_beam, 2 * c->model.n_feed * c->model.n_ax};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+              fwrite(&c->sur_cfg, sizeof(mv_mlp_config), 1, f) == 1 && fwrite(&n, sizeof(n), 1, f) == 1 &&
+              fwrite(B.data(), sizeof(float), B.size(), f) == B.size() &&
+              fwrite(p.data(), sizeof(float), (size_t)n, f) == (size_t)n;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(MV_ERR_ARG, "write to %s failed", path);
+    return MV_OK;
+}
+
+mv_status mv_surrogate_load(mv_ctx* c, const char* path) {
+    g_err.clear();
+    if (!c || !path) return fail(MV_ERR_ARG, "NULL argument");
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(MV_ERR_ARG, "cannot open %s", path);
+    char magic[8];
+    int32_t hdr[6];
+    mv_mlp_config k;
+    long long n = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "MVMLP001", 8) == 0 && fread(hdr, sizeof(hdr), 1, f) == 1 &&
+              fread(&k, sizeof(k), 1, f) == 1 && fread(&n, sizeof(n), 1, f) == 1;
+    std::vector<float> B, p;
+    if (ok) {
+        B.resize(3 * (size_t)std::max(0, hdr[0]));
+        p.resize((size_t)std::max(0ll, n));
+        ok = fread(B.data(), sizeof(float), B.size(), f) == B.size() && fread(p.data(), sizeof(float), p.size(), f) == p.size();
+    }
+    fclose(f);
+    if (!ok) return fail(MV_ERR_ARG, "%s is not a surrogate file", path);
+    if (hdr[4] != c->model.n_beam || hdr[5] != 2 * c->model.n_feed * c->model.n_ax)
+        return fail(MV_ERR_ARG, "surrogate in %s was made for another beam set", path);
+    mv_status s = mv_surrogate_create(c, &k);  // same seed: the same B
+    if (s) return s;
+    std::vector<float> B2(B.size());
+    surrogate_fourier(c->sur, B2.data());
+    if (B2 != B || surrogate_param_count(c->sur) != n) return fail(MV_ERR_ARG, "surrogate file layout mismatch");
+    return mv_surrogate_set_params(c, p.data());
+}
+
+mv_status mv_set_beam_surrogate(mv_ctx* c, int enable) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (enable && !c->sur) return fail(MV_ERR_STATE, "no surrogate");
+    c->use_sur = enable != 0;
+    ++c->model_version;
     return MV_OK;
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace mv {
 
 constexpr double kCLight = 299792458.0;   // m/s
@@ -117,6 +119,27 @@ bool herk_tc_available();
 
 // Set the message mv_last_error() returns on this thread.
 void set_last_error(const char* msg);
+
+// ------------------------------------------------------ learned beam (mlp.cu)
+struct Surrogate;
+Surrogate* surrogate_create(int F, int E, int H, int depth, int n_out, int n_ant, float s_az, float s_za, float s_nu,
+                            unsigned long long seed, double nu_mid, double nu_half, cudaError_t* err);
+void surrogate_destroy(Surrogate* S);
+long long surrogate_param_count(const Surrogate* S);
+int surrogate_fourier(const Surrogate* S, float* out);
+void surrogate_layout(const Surrogate* S, long long* off_w, long long* off_b, long long* off_emb, int* d0p);
+cudaError_t surrogate_get_params(const Surrogate* S, float* host);
+cudaError_t surrogate_set_params(Surrogate* S, const float* host);
+cudaError_t surrogate_grad(Surrogate* S, int n, const int* ant, const float* az, const float* za, const float* nu,
+                           const float* T, float* grads_host, double* loss, cudaStream_t st);
+cudaError_t surrogate_eval(Surrogate* S, int n, const int* ant, const float* az, const float* za, const float* nu,
+                           float* out_host, cudaStream_t st);
+cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, double nu0, double dnu, int steps,
+                            int batch, float lr0, float lr1, unsigned long long seed, cudaStream_t st,
+                            double* loss_first, double* loss_last, long long* L);
+cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& h_inst, int inst0, int n_inst,
+                         const std::vector<int>& h_nlive, const std::vector<double>& h_nu, double nu_ref,
+                         LiveTables lt, float2* wa, long long wa_pitch, float* amax, cudaStream_t st, long long* L);
 
 // Exponent e of the exact power-of-two scale 2^e that brings max |Z| of an
 // instance into [2^13, 2^14) before the FP16 hi/lo split (the HERK epilogue

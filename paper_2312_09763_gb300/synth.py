@@ -219,3 +219,44 @@ def batched_uneven(n_pairs: int = 256, n_ant: int = 350, n_src: int = 100_000, n
     return Workload(f"batched_uneven: {n_pairs} (LST, nu) pairs, {n_ant} ant x {n_src} src (40% uniform + "
                     "60% clustered), bicubic grid beam 48-252 MHz",
                     ra, dec, flux, alpha, 150e6, enu, HERA_LAT, beam, lsts, freqs)
+
+
+def dipole_feed_offset_grids(n_ant: int, nu_grid: np.ndarray, n_za: int, n_az: int, g: np.random.Generator,
+                             offset_m: float = 0.02, fwhm_ref: float = 30.0 * DEG, nu_ref: float = 150e6) -> np.ndarray:
+    """Per-antenna Jones beams, complex64 [n_ant][2][2][nu][za][az]: a short
+    dipole pair (X along East, Y along North) projected on the (theta, phi)
+    basis, times a Gaussian envelope with FWHM fwhm_ref nu_ref / nu, times the
+    phase exp(-2 pi i (nu / c) delta_a . s_hat) of a seeded feed displacement
+    delta_a ~ U[-offset_m, offset_m] per axis."""
+    za = np.arange(n_za) * (np.pi / 2 / (n_za - 1))
+    az = np.arange(n_az) * (2 * np.pi / n_az)
+    NU, ZA, AZ = np.meshgrid(nu_grid, za, az, indexing="ij")
+    env = np.exp(-4.0 * np.log(2.0) * ZA ** 2 / (fwhm_ref * nu_ref / NU) ** 2)
+    s = np.stack([np.sin(ZA) * np.sin(AZ), np.sin(ZA) * np.cos(AZ), np.cos(ZA)], -1)
+    base = np.zeros((2, 2) + NU.shape)
+    base[0, 0] = np.cos(ZA) * np.sin(AZ)
+    base[0, 1] = np.cos(AZ)
+    base[1, 0] = np.cos(ZA) * np.cos(AZ)
+    base[1, 1] = -np.sin(AZ)
+    delta = g.uniform(-offset_m, offset_m, size=(n_ant, 3))
+    out = np.empty((n_ant, 2, 2) + NU.shape, dtype=np.complex64)
+    for a in range(n_ant):
+        ph = np.exp(-2j * np.pi * (NU / 299792458.0) * (s @ delta[a]))
+        out[a] = (base * (env * ph)[None, None]).astype(np.complex64)
+    return out
+
+
+def learned_beam(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times: int = 60, n_za: int = 91,
+                 n_az: int = 360, dnu: float = 1e6) -> Workload:
+    """Workload 4: the HERA-like array and sky of workload 1 with one beam per
+    antenna (dipole_feed_offset_grids on a 1 deg x 1 deg x 1 MHz grid over
+    98-202 MHz), the setting where a learned surrogate replaces n_ant grids."""
+    w = hera_like(n_ant=n_ant, n_src=n_src, n_chan=n_chan, n_times=n_times, n_za=31, n_az=60)
+    n_nu = int(round(104e6 / dnu)) + 1
+    nu_grid = 98e6 + np.arange(n_nu) * dnu
+    grids = dipole_feed_offset_grids(n_ant, nu_grid, n_za, n_az, rng(4, "feed_offsets"))
+    w.beam = ("grid", grids, 98e6, dnu, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
+    w.beam_idx = np.arange(n_ant, dtype=np.int32)
+    w.name = (f"learned_beam: {n_ant} ant (one Jones beam each) x {n_src} src x {n_chan} ch x {n_times} t, "
+              f"Fourier-feature MLP beam")
+    return w

@@ -59,3 +59,48 @@ def dipole_jones_grid(nu_grid, n_za, n_az, fwhm_ref, nu_ref, g: np.random.Genera
     J[0, 1, 1] = -np.sin(AZ)
     J = J * env * np.exp(1j * ph) * (1 + 0.05 * np.cos(3 * ZA + 0.2 * (NU / nu_ref)))
     return J.astype(np.complex64)
+
+
+def oracle_net(sim, nu0: float, dnu: float, n_nu: int):
+    """The FP64 oracle MLP holding the GPU surrogate's current parameters."""
+    from oracle import mlp
+    p, B, lay = sim.surrogate_params()
+    cfg = sim._mlp
+    F, E, H, D = cfg["n_freq"], cfg["emb_dim"], cfg["width"], cfg["depth"]
+    d0, d0p, off_emb = 2 * F + E, int(lay[-1]), int(lay[-2])
+    n_out = 2 * sim.n_feed * sim._n_ax()
+    W, b = [], []
+    for l in range(D + 1):
+        ow, ob = int(lay[2 * l]), int(lay[2 * l + 1])
+        kin, nout = (d0p if l == 0 else H), (8 if l == D else H)
+        Wl = p[ow:ow + nout * kin].reshape(nout, kin).astype(np.float64)
+        bl = p[ob:ob + nout].astype(np.float64)
+        if l == 0:
+            Wl = Wl[:, :d0]
+        if l == D:
+            Wl, bl = Wl[:n_out], bl[:n_out]
+        W.append(Wl)
+        b.append(bl)
+    n_beam = (p.size - off_emb) // E
+    emb = p[off_emb:off_emb + n_beam * E].reshape(n_beam, E).astype(np.float64)
+    lo, hi = nu0, nu0 + (n_nu - 1) * dnu
+    return mlp.MLP(B=B.astype(np.float64), emb=emb, W=W, b=b, nu_mid=0.5 * (lo + hi), nu_half=0.5 * (hi - lo))
+
+
+def flat_grads(sim, g: dict) -> np.ndarray:
+    """Oracle gradients laid out like the GPU parameter vector (padding zero)."""
+    p, B, lay = sim.surrogate_params()
+    cfg = sim._mlp
+    F, E, H, D = cfg["n_freq"], cfg["emb_dim"], cfg["width"], cfg["depth"]
+    d0, d0p, off_emb = 2 * F + E, int(lay[-1]), int(lay[-2])
+    out = np.zeros(p.size)
+    for l in range(D + 1):
+        ow, ob = int(lay[2 * l]), int(lay[2 * l + 1])
+        kin, nout = (d0p if l == 0 else H), (8 if l == D else H)
+        Wg = np.zeros((nout, kin))
+        gw = g[f"W{l}"]
+        Wg[:gw.shape[0], :gw.shape[1]] = gw
+        out[ow:ow + nout * kin] = Wg.ravel()
+        out[ob:ob + g[f"b{l}"].size] = g[f"b{l}"]
+    out[off_emb:off_emb + g["emb"].size] = g["emb"].ravel()
+    return out
