@@ -7,7 +7,12 @@ already resident on the device.  vis = N_ant (N_ant + 1) / 2 baselines
 (autocorrelations included) x channels x times.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp16x3|fp32]
-                    [--impl ours|reference]
+                    [--impl ours|reference] [--workload hera|diffuse|uneven]
+
+--workload diffuse times the polarised HEALPix sky (350 antennas, 196,608
+pixels, 32 channels x 120 LSTs, 2 x 2 Jones beam) and --workload uneven the
+256 random (LST, nu) pairs through mv_simulate_pairs; the default is the
+HERA-like point-source workload above.
 
 Under torchrun each rank simulates the full workload on its own GPU (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -41,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    ap.add_argument("--workload", default="hera", choices=["hera", "diffuse", "uneven"],
+                    help="hera: 350 ant x 1e5 src x 64 ch x 60 t (default); diffuse: 350 ant x 196,608 HEALPix "
+                         "pixels x 32 ch x 120 t, 2x2 Jones beam; uneven: 256 (LST, nu) pairs, one call")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
     return ap.parse_args()
@@ -81,15 +89,24 @@ class Dist:
             self.dist.destroy_process_group()
 
 
-def workload(small: bool):
+def workload(args):
     from paper_2312_09763_gb300 import synth
-    if small:  # profiling captures: 64 channels of 1 LST, 1.5e4 sources (~2.7 GB of Z planes)
+    if args.workload == "diffuse":
+        return synth.polarised_diffuse()
+    if args.workload == "uneven":
+        return synth.batched_uneven()
+    if args.small:  # profiling captures: 64 channels of 1 LST, 1.5e4 sources (~2.7 GB of Z planes)
         return synth.hera_like(n_ant=350, n_src=15_000, n_chan=64, n_times=1)
     return synth.hera_like()
 
 
-def n_vis(w) -> int:
-    return w.n_ant * (w.n_ant + 1) // 2 * len(w.freqs) * len(w.lsts)
+def n_instances(w, pairs: bool) -> int:
+    return len(w.lsts) if pairs else len(w.lsts) * len(w.freqs)
+
+
+def n_vis(w, pairs: bool = False) -> int:
+    """Baselines (a >= b) x instances; a Jones beam's 2 x 2 feed products count once."""
+    return w.n_ant * (w.n_ant + 1) // 2 * n_instances(w, pairs)
 
 
 class Clocks:
@@ -172,7 +189,7 @@ def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
     if rank != 0:
         return
-    w = workload(args.small)
+    w = workload(args)
     per_step = 2048
     for _ in range(args.warmup):
         cpu_baseline(w, budget_pairs=256)
@@ -203,21 +220,25 @@ def main():
     from paper_2312_09763_gb300 import Simulator
     d = Dist(world)
     torch.cuda.set_device(local)
-    w = workload(args.small)
+    w = workload(args)
+    pairs = args.workload == "uneven"
     sim = Simulator(local, overlap_batches=args.overlap)
     sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
     sim.set_beam(w.beam)
     sim.set_antennas(w.enu, None, w.lat)
     N = w.n_ant
-    V = torch.empty((len(w.lsts), len(w.freqs), N, N), dtype=torch.complex64, device=f"cuda:{local}")
+    nf, nax = sim.n_feed, sim._n_ax()
+    shape = (len(w.lsts), N * nf, N * nf) if pairs else (len(w.lsts), len(w.freqs), N * nf, N * nf)
+    V = torch.empty(shape, dtype=torch.complex64, device=f"cuda:{local}")
+    run = sim.simulate_pairs if pairs else sim.simulate
     stream = torch.cuda.current_stream()
     tuning = None
     if args.precision != "fp32" and not args.no_autotune:
-        tuning = sim.autotune(w.lsts, w.freqs, args.precision)
+        tuning = sim.autotune(w.lsts, w.freqs, args.precision, pairs=pairs)
     for _ in range(args.warmup):
-        sim.simulate(w.lsts, w.freqs, args.precision, out=V)
+        run(w.lsts, w.freqs, args.precision, out=V)
     torch.cuda.synchronize()
-    live = sim.last_live_counts(len(w.lsts) * len(w.freqs))
+    live = sim.last_live_counts(n_instances(w, pairs))
     sim.profile_enable(True)
     clocks = Clocks(local)
     clocks.start()
@@ -227,7 +248,7 @@ def main():
     e0.record(stream)
     launches = 0
     for _ in range(args.steps):
-        sim.simulate(w.lsts, w.freqs, args.precision, out=V)
+        run(w.lsts, w.freqs, args.precision, out=V)
         launches += sim.last_launch_count()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -238,14 +259,14 @@ def main():
     sim.profile_enable(False)
     sim.check_device_status()
     ms_max = d.max(ms)
-    vis_step = n_vis(w)
+    vis_step = n_vis(w, pairs)
     value = world * vis_step * args.steps / (ms_max / 1e3)
 
     # roofline of the dominant kernel (the HERK)
     burst, sustained, hbm, src = peaks()
     n_h, ms_h = prof["herk"]
-    rows = 2 * N
-    K = live.astype(np.float64)  # n_ax = 1
+    rows = 2 * N * nf
+    K = live.astype(np.float64) * nax
     if args.precision == "fp32":
         roof = None
     else:
@@ -260,8 +281,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": w.name, "instances_per_step": len(w.lsts) * len(w.freqs),
-                       "live_sources_mean": float(K.mean()), "precision": args.precision,
+            "config": {"workload": w.name, "instances_per_step": n_instances(w, pairs),
+                       "live_sources_mean": float(live.mean()), "precision": args.precision,
                        "l2": "inputs larger than L2: Z planes of one batch ~4.5 GB, re-streamed each step",
                        "parallelism": f"{world} replica(s), instances simulated independently"},
             "gpu_launches": launches, "roofline": roof, "clocks": clk, "herk_tuning": tuning,
@@ -280,7 +301,7 @@ def main():
             sim.init_sky(ra.numpy(), dec.numpy(), fl.numpy(), w.spec_idx, w.nu_ref)
             sim.set_beam(w.beam)
             sim.set_antennas(w.enu, None, w.lat)
-            sim.simulate(w.lsts, w.freqs, args.precision, out=Vh, host=True)
+            run(w.lsts, w.freqs, args.precision, out=Vh, host=True)
         dt = time.perf_counter() - t0
         line["e2e"] = {"value": vis_step * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}

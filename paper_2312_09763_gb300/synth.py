@@ -260,3 +260,121 @@ def learned_beam(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_tim
     w.name = (f"learned_beam: {n_ant} ant (one Jones beam each) x {n_src} src x {n_chan} ch x {n_times} t, "
               f"Fourier-feature MLP beam")
     return w
+
+
+# ----------------------------------------------------------- diffuse sky
+
+def healpix_ring_pix2ang(nside: int):
+    """(theta, phi) of every HEALPix pixel centre in RING order (Gorski et al.
+    2005, ApJ 622, 759: polar caps, equatorial belt, south cap)."""
+    npix = 12 * nside * nside
+    ncap = 2 * nside * (nside - 1)
+    p = np.arange(npix, dtype=np.int64)
+    z = np.empty(npix)
+    phi = np.empty(npix)
+    north = p < ncap
+    south = p >= npix - ncap
+    belt = ~(north | south)
+    # north cap: ring i has 4 i pixels
+    pn = p[north]
+    i = np.floor(np.sqrt((pn + 1) / 2.0 - np.sqrt(np.floor((pn + 1) / 2.0)))).astype(np.int64) + 1
+    j = pn + 1 - 2 * i * (i - 1)
+    z[north] = 1.0 - i * i / (3.0 * nside * nside)
+    phi[north] = np.pi / (2.0 * i) * (j - 0.5)
+    # equatorial belt: rings nside .. 3 nside, 4 nside pixels each
+    pe = p[belt] - ncap
+    i = pe // (4 * nside) + nside
+    j = pe % (4 * nside) + 1
+    s = (i - nside + 1) % 2
+    z[belt] = 4.0 / 3.0 - 2.0 * i / (3.0 * nside)
+    phi[belt] = np.pi / (2.0 * nside) * (j - s / 2.0)
+    # south cap (mirror of the north cap)
+    ps = npix - p[south]
+    i = np.floor(np.sqrt(ps / 2.0 - np.sqrt(np.floor(ps / 2.0)))).astype(np.int64) + 1
+    j = 4 * i + 1 - (ps - 2 * i * (i - 1))
+    z[south] = -1.0 + i * i / (3.0 * nside * nside)
+    phi[south] = np.pi / (2.0 * i) * (j - 0.5)
+    return np.arccos(np.clip(z, -1, 1)), phi
+
+
+def gaussian_random_field(theta: np.ndarray, phi: np.ndarray, lmax: int, cl: np.ndarray,
+                          g: np.random.Generator) -> np.ndarray:
+    """Real Gaussian random field sum_lm a_lm Y_lm at the given points, with
+    a_lm ~ N(0, C_l) (complex for m > 0), evaluated ring by ring: the
+    normalised associated Legendre functions come from the standard three-term
+    recurrence in l at fixed m, and each ring's azimuthal sum is one matrix
+    product over m."""
+    a = np.zeros((lmax + 1, lmax + 1), dtype=np.complex128)
+    for l in range(lmax + 1):
+        sd = np.sqrt(cl[l])
+        a[l, 0] = sd * g.normal()
+        if l > 0:
+            a[l, 1:l + 1] = sd * (g.normal(size=l) + 1j * g.normal(size=l)) / np.sqrt(2.0)
+    zs, inv = np.unique(np.round(np.cos(theta), 12), return_inverse=True)
+    st = np.sqrt(np.maximum(0.0, 1.0 - zs * zs))
+    # fm[r, m] = sum_l a_lm lam_lm(z_r), lam_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!) P_l^m,
+    # the recursion in l vectorised over the rings
+    fm = np.zeros((zs.size, lmax + 1), dtype=np.complex128)
+    pmm = np.full(zs.size, 1.0 / np.sqrt(4 * np.pi))
+    for m in range(lmax + 1):
+        if m > 0:
+            pmm = -np.sqrt((2 * m + 1) / (2.0 * m)) * st * pmm
+        l2, l1 = None, pmm
+        fm[:, m] += a[m, m] * pmm
+        if m + 1 <= lmax:
+            l2, l1 = pmm, zs * np.sqrt(2 * m + 3) * pmm
+            fm[:, m] += a[m + 1, m] * l1
+        for l in range(m + 2, lmax + 1):
+            al = np.sqrt((4.0 * l * l - 1) / (l * l - m * m))
+            bl = np.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1) ** 2 - 1))
+            l2, l1 = l1, al * (zs * l1 - bl * l2)
+            fm[:, m] += a[l, m] * l1
+    out = np.empty(theta.size)
+    for r in range(zs.size):
+        sel = np.nonzero(inv == r)[0]
+        e = np.exp(1j * np.outer(np.arange(1, lmax + 1), phi[sel]))
+        out[sel] = fm[r, 0].real + 2.0 * np.real(fm[r, 1:, None] * e).sum(axis=0)
+    return out
+
+
+def polarised_diffuse(n_ant: int = 350, nside: int = 128, n_chan: int = 32, n_times: int = 120,
+                      n_za: int = 91, n_az: int = 360, lmax: int = None) -> Workload:
+    """Workload 2: the HERA-like array, a diffuse sky of 12 nside^2 HEALPix
+    pixel centres whose intensities are a log-normal Gaussian random field
+    (C_l ~ l^-2.5 for l >= 1, C_0 = 0, field normalised to unit variance)
+    turned into fluxes (intensity x pixel area, about 1e3 Jy in total, spectral
+    index -2.5), 32 channels centred in 140-160 MHz, 120 LSTs 30 s apart, and
+    a 2 feed x 2 axis dipole-like Jones beam on a 1 deg x 1 deg x 1 MHz grid
+    (138-162 MHz) with a 5 % ripple and a smooth phase of at most 0.1 rad."""
+    lmax = 3 * nside - 1 if lmax is None else lmax
+    theta, phi = healpix_ring_pix2ang(nside)
+    ell = np.arange(lmax + 1, dtype=float)
+    cl = np.where(ell >= 1, np.maximum(ell, 1.0) ** -2.5, 0.0)
+    f = gaussian_random_field(theta, phi, lmax, cl, rng(2, "grf"))
+    f = (f - f.mean()) / f.std()
+    inten = np.exp(f - 0.5)
+    npix = theta.size
+    flux = inten * (4 * np.pi / npix)
+    flux *= 1e3 / flux.sum()
+    ra, dec = phi, np.pi / 2 - theta
+    enu = hex_array(n_ant, 14.6)
+    freqs = 140e6 + (np.arange(n_chan) + 0.5) * (20e6 / n_chan)
+    lsts = np.arange(n_times) * (0.5 * SIDEREAL_MINUTE)
+    nu_grid = 138e6 + np.arange(25) * 1e6
+    gb = rng(2, "beam")
+    za = np.arange(n_za) * (np.pi / 2 / (n_za - 1))
+    az = np.arange(n_az) * (2 * np.pi / n_az)
+    NU, ZA, AZ = np.meshgrid(nu_grid, za, az, indexing="ij")
+    env = np.exp(-4 * np.log(2) * ZA ** 2 / (30 * DEG * 150e6 / NU) ** 2)
+    rip = 1.0 + 0.05 * ripple_field(AZ, ZA, (NU - 150e6) / 150e6, gb)
+    pha = 0.1 * ripple_field(AZ, ZA, (NU - 150e6) / 150e6, gb)
+    J = np.zeros((1, 2, 2) + NU.shape, dtype=np.complex128)
+    J[0, 0, 0] = np.cos(ZA) * np.sin(AZ)
+    J[0, 0, 1] = np.cos(AZ)
+    J[0, 1, 0] = np.cos(ZA) * np.cos(AZ)
+    J[0, 1, 1] = -np.sin(AZ)
+    J = (J * (env * rip * np.exp(1j * pha))[None, None, None]).astype(np.complex64)
+    beam = ("grid", J, 138e6, 1e6, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
+    return Workload(f"polarised_diffuse: {n_ant} ant x {npix} HEALPix pixels (nside {nside}) x {n_chan} ch x "
+                    f"{n_times} t, 2x2 Jones beam", ra, dec, flux, np.full(npix, -2.5), 150e6, enu, HERA_LAT,
+                    beam, lsts, freqs)
