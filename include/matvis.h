@@ -121,6 +121,20 @@ const char *mv_last_error(void);
 mv_status mv_init_sky(mv_ctx *ctx, int64_t n_src, const double *ra, const double *dec,
                       const double *flux_ref, const double *spec_idx, double nu_ref);
 
+/* Fully polarised sky (Sec. 2.1 coherency, Sec. 2.2 eq. "fullz"): Stokes Q,
+ * U, V of every source of the last mv_init_sky, in Jy at nu_ref, host
+ * arrays of n_src (copied).  The coherency in the beam's (theta, phi)
+ * component basis is C = [[I + Q, U + iV], [U - iV, I - Q]], static in
+ * celestial coordinates as in the paper, and all four Stokes follow the
+ * source's power law.  Z becomes sum_k A^{pk} F M_{kk''} with M the
+ * lower-triangular Cholesky factor of C (formed in FP64 on the host), so V
+ * stays Z Z^dagger.  Needs Q^2 + U^2 + V^2 <= I^2 (1 + 1e-6) per source
+ * (MV_ERR_ARG otherwise) and, at simulate time, a two-axis gridded beam or a
+ * surrogate of one (MV_ERR_STATE otherwise).  q = u = v = NULL returns to an
+ * unpolarised sky; a later mv_init_sky also does. */
+mv_status mv_set_sky_polarisation(mv_ctx *ctx, int64_t n_src, const double *stokes_q,
+                                  const double *stokes_u, const double *stokes_v);
+
 /* Analytic unpolarised Gaussian E-field beam, the same for every antenna:
  * A(za) = exp(-4 ln2 za^2 / fwhm^2) (Sec. 2.4 analytic beams).  fwhm > 0. */
 mv_status mv_set_beam_gaussian(mv_ctx *ctx, double fwhm_rad);

@@ -68,6 +68,7 @@ class _Problem(ctypes.Structure):
         ("nu0", ctypes.c_double), ("dnu", ctypes.c_double),
         ("dza", ctypes.c_double), ("daz", ctypes.c_double),
         ("interp", ctypes.c_int32),
+        ("stokes_quv", ctypes.c_void_p),
     ]
 
 
@@ -95,6 +96,8 @@ def _load() -> ctypes.CDLL:
         lib.orc_vis.restype = ctypes.c_int
         lib.orc_vis_outer.argtypes = [P, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_vis_outer.restype = ctypes.c_int
+        lib.orc_coherency_sqrt.argtypes = [ctypes.c_double] * 4 + [dp]
+        lib.orc_coherency_sqrt.restype = None
         _lib = lib
     return _lib
 
@@ -124,6 +127,7 @@ class Problem:
     spec_idx: Optional[np.ndarray] = None
     nu_ref: float = 150e6
     beam_idx: Optional[np.ndarray] = None
+    stokes_quv: Optional[np.ndarray] = None   # [3][n_src] Q, U, V (Jy at nu_ref); needs a two-axis beam
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Problem:
@@ -131,8 +135,10 @@ class Problem:
         si = None if self.spec_idx is None else _f64(self.spec_idx)
         enu = _f64(self.enu).reshape(-1, 3)
         bi = None if self.beam_idx is None else np.ascontiguousarray(self.beam_idx, dtype=np.int32)
-        keep = [ra, dec, fl, si, enu, bi]
+        quv = None if self.stokes_quv is None else _f64(self.stokes_quv).reshape(3, -1)
+        keep = [ra, dec, fl, si, enu, bi, quv]
         p = _Problem()
+        p.stokes_quv = _ptr(quv)
         p.n_src = ra.size
         p.ra, p.dec, p.flux_ref, p.spec_idx = _ptr(ra), _ptr(dec), _ptr(fl), _ptr(si)
         p.nu_ref = float(self.nu_ref)
@@ -241,11 +247,19 @@ def vis(prob: Problem, lst: float, nu: float, pairs=None, threads: Optional[int]
         pb = np.ascontiguousarray(pairs[1], dtype=np.int32)
         out = np.empty((pa.size, nfd, nfd), dtype=np.complex128)
         rc = _load().orc_vis(ctypes.byref(p), float(lst), float(nu), pa.size, _ptr(pa), _ptr(pb), _ptr(out), nt)
+    _raise(rc)
+    return out
+
+
+def _raise(rc: int):
     if rc == -1:
         raise ValueError("frequency outside the beam grid")
-    if rc:
+    if rc == -2:
         raise ValueError("bad antenna index")
-    return out
+    if rc == -3:
+        raise ValueError("a polarised sky needs a two-axis beam")
+    if rc:
+        raise ValueError(f"oracle error {rc}")
 
 
 def vis_outer(prob: Problem, lst: float, nu: float) -> np.ndarray:
@@ -254,9 +268,15 @@ def vis_outer(prob: Problem, lst: float, nu: float) -> np.ndarray:
     N = p.n_feed * p.n_ant
     out = np.empty((N, N), dtype=np.complex128)
     rc = _load().orc_vis_outer(ctypes.byref(p), float(lst), float(nu), _ptr(out))
-    if rc:
-        raise ValueError("frequency outside the beam grid")
+    _raise(rc)
     return out
+
+
+def coherency_sqrt(I, Q, U, V) -> np.ndarray:
+    """M with M M^dagger = C = [[I+Q, U+iV], [U-iV, I-Q]] (lower-triangular), complex [2][2]."""
+    m = np.empty(4)
+    _load().orc_coherency_sqrt(float(I), float(Q), float(U), float(V), _ptr(m))
+    return np.array([[m[0], 0.0], [m[1] + 1j * m[2], m[3]]])
 
 
 def live_directions(prob: Problem, lst: float):
@@ -272,5 +292,6 @@ def vis_with_beam_fn(prob: Problem, lst: float, nu: float, beam_fn, pairs=None, 
     az, za = live_directions(prob, lst)
     table = np.asarray(beam_fn(az, za, nu), dtype=np.complex128)
     q = Problem(ra=prob.ra, dec=prob.dec, flux_ref=prob.flux_ref, enu=prob.enu, lat=prob.lat,
-                beam=("table", table), spec_idx=prob.spec_idx, nu_ref=prob.nu_ref, beam_idx=prob.beam_idx)
+                beam=("table", table), spec_idx=prob.spec_idx, nu_ref=prob.nu_ref, beam_idx=prob.beam_idx,
+                stokes_quv=prob.stokes_quv)
     return vis(q, lst, nu, pairs=pairs, threads=threads)

@@ -16,7 +16,11 @@
  *
  * which is the discrete RIME of Sec. 2.1 (eq. "matvisrime") with the delay of
  * eq. "matvisdelay" and an unpolarised coherency C = I * identity (Sec. 2.2,
- * the case that leads to eq. "littlez").  Source directions follow eq. "xeq"
+ * the case that leads to eq. "littlez").  With Stokes Q, U, V given, the
+ * source term I_s sum_k A^{pk} conj(A^{qk}) becomes the full
+ * sum_{k,k'} A^{pk} C_{kk'} conj(A^{qk'}) with the coherency of Sec. 2.1,
+ * C = [[I + Q, U + iV], [U - iV, I - Q]] in the beam's (theta, phi) component
+ * basis (eq. "matvistensorprod"), all four Stokes scaled by (nu/nu_ref)^alpha.  Source directions follow eq. "xeq"
  * and eq. "rotation" (Sec. 2.3); beams follow Sec. 2.4.  Every floating-point
  * step is IEEE double.  Compile with -ffp-contract=off so that no product is
  * fused into an add behind our back (the horizon test Up > 0 must be taken on
@@ -71,6 +75,9 @@ typedef struct {
     const double *grid;          /* complex128 [beam][feed][ax][nu][za][az] */
     double nu0, dnu, dza, daz;   /* grid axes: nu_m = nu0 + m dnu, za_i = i dza, az_j = j daz */
     int32_t interp;              /* 0 cubic (Keys), 1 bilinear in az/za */
+    /* polarised sky (needs n_ax = 2): [3][n_src] Stokes Q, U, V in Jy at
+     * nu_ref, or NULL for an unpolarised sky */
+    const double *stokes_quv;
 } orc_problem;
 
 /* ---------------------------------------------------------------- coords */
@@ -234,11 +241,12 @@ typedef struct {
     double *flux;   /* [n_live] I_s(nu) */
     double *A;      /* complex128 [n_beam][feed][ax][n_live] */
     int64_t *idx;   /* [n_live] catalogue index */
+    double *quv;    /* [n_live][3] Q, U, V at nu, or NULL */
 } orc_inst;
 
 static void inst_free(orc_inst *I)
 {
-    free(I->enu); free(I->flux); free(I->A); free(I->idx);
+    free(I->enu); free(I->flux); free(I->A); free(I->idx); free(I->quv);
     memset(I, 0, sizeof(*I));
 }
 
@@ -264,13 +272,17 @@ static int inst_prepare(const orc_problem *P, double lst, double nu, orc_inst *I
     I->flux = malloc(sizeof(double) * mm);
     I->idx = malloc(sizeof(int64_t) * mm);
     I->A = malloc(sizeof(double) * 2 * (size_t)nb * P->n_feed * P->n_ax * mm);
+    if (P->stokes_quv) I->quv = malloc(sizeof(double) * 3 * mm);
     double *az = malloc(sizeof(double) * mm), *za = malloc(sizeof(double) * mm);
     int64_t j = 0;
     for (int64_t s = 0; s < n; ++s) {
         if (!(enu[3 * s + 2] > 0.0)) continue;
         memcpy(&I->enu[3 * j], &enu[3 * s], 3 * sizeof(double));
         double alpha = P->spec_idx ? P->spec_idx[s] : 0.0;
-        I->flux[j] = P->flux_ref[s] * pow(nu / P->nu_ref, alpha);
+        double g = pow(nu / P->nu_ref, alpha);
+        I->flux[j] = P->flux_ref[s] * g;
+        if (I->quv)
+            for (int c = 0; c < 3; ++c) I->quv[3 * j + c] = P->stokes_quv[(int64_t)c * n + s] * g;
         I->idx[j] = s;
         ++j;
     }
@@ -308,10 +320,12 @@ int64_t orc_count_live(const orc_problem *P, double lst)
  * pairs: n_pairs (a, b) antenna pairs (pa[i], pb[i]); out complex128
  * [n_pairs][n_feed][n_feed].  If n_pairs < 0 all N x N entries are computed
  * into out[(a n_feed + p)][(b n_feed + q)] with N = n_feed n_ant.
- * Returns 0, -1 (frequency outside the beam grid) or -2 (bad index). */
+ * Returns 0, -1 (frequency outside the beam grid), -2 (bad index) or -3 (a
+ * polarised sky with a single-axis beam). */
 int orc_vis(const orc_problem *P, double lst, double nu, int64_t n_pairs,
             const int32_t *pa, const int32_t *pb, double *out, int n_threads)
 {
+    if (P->stokes_quv && P->n_ax != 2) return -3;
     orc_inst I;
     int rc = inst_prepare(P, lst, nu, &I);
     if (rc) return rc;
@@ -342,15 +356,32 @@ int orc_vis(const orc_problem *P, double lst, double nu, int64_t n_pairs,
             double c = cos(phase), sn = sin(phase);
             for (int p = 0; p < nfd; ++p)
                 for (int r = 0; r < nfd; ++r) {
-                    double tr = 0.0, ti = 0.0;
-                    for (int k = 0; k < nax; ++k) {
-                        const double *u = &I.A[2 * ((((int64_t)ba * nfd + p) * nax + k) * K + s)];
-                        const double *v = &I.A[2 * ((((int64_t)bb * nfd + r) * nax + k) * K + s)];
-                        /* u * conj(v) */
-                        tr += u[0] * v[0] + u[1] * v[1];
-                        ti += u[1] * v[0] - u[0] * v[1];
+                    double tr = 0.0, ti = 0.0, f = I.flux[s];
+                    if (I.quv) {
+                        /* sum_{k,k'} u_k C_kk' conj(v_k'), C from (I, Q, U, V) */
+                        const double *q3 = &I.quv[3 * s];
+                        double Cr[2][2] = {{f + q3[0], q3[1]}, {q3[1], f - q3[0]}};
+                        double Ci[2][2] = {{0.0, q3[2]}, {-q3[2], 0.0}};
+                        for (int k = 0; k < 2; ++k)
+                            for (int k2 = 0; k2 < 2; ++k2) {
+                                const double *u = &I.A[2 * ((((int64_t)ba * nfd + p) * nax + k) * K + s)];
+                                const double *v = &I.A[2 * ((((int64_t)bb * nfd + r) * nax + k2) * K + s)];
+                                /* w = u * C_kk' */
+                                double wr = u[0] * Cr[k][k2] - u[1] * Ci[k][k2];
+                                double wi = u[0] * Ci[k][k2] + u[1] * Cr[k][k2];
+                                tr += wr * v[0] + wi * v[1];
+                                ti += wi * v[0] - wr * v[1];
+                            }
+                        f = 1.0;
+                    } else {
+                        for (int k = 0; k < nax; ++k) {
+                            const double *u = &I.A[2 * ((((int64_t)ba * nfd + p) * nax + k) * K + s)];
+                            const double *v = &I.A[2 * ((((int64_t)bb * nfd + r) * nax + k) * K + s)];
+                            /* u * conj(v) */
+                            tr += u[0] * v[0] + u[1] * v[1];
+                            ti += u[1] * v[0] - u[0] * v[1];
+                        }
                     }
-                    double f = I.flux[s];
                     acc[p * nfd + r][0] += f * (tr * c - ti * sn);
                     acc[p * nfd + r][1] += f * (tr * sn + ti * c);
                 }
@@ -368,13 +399,37 @@ int orc_vis(const orc_problem *P, double lst, double nu, int64_t n_pairs,
     return bad ? -2 : 0;
 }
 
+/* A square root M of the coherency, M M^dagger = C (Sec. 2.2, "second
+ * trick"): the lower-triangular Cholesky factor
+ *   M = [[m00, 0], [m10, m11]],  m00 = sqrt(I + Q),  m10 = (U - iV) / m00,
+ *   m11 = sqrt(I - Q - |m10|^2),
+ * with m10 = 0 and m11 = sqrt(I - Q) when I + Q = 0 (then U = V = 0 for a
+ * physical source).  Writes m00, m10 (re, im), m11. */
+void orc_coherency_sqrt(double I, double Q, double U, double V, double *m)
+{
+    double a = I + Q;
+    m[0] = a > 0.0 ? sqrt(a) : 0.0;
+    if (m[0] > 0.0) {
+        m[1] = U / m[0];
+        m[2] = -V / m[0];
+    } else {
+        m[1] = 0.0;
+        m[2] = 0.0;
+    }
+    double d = I - Q - (m[1] * m[1] + m[2] * m[2]);
+    m[3] = d > 0.0 ? sqrt(d) : 0.0;
+}
+
 /* Outer-product form (Algorithm 2 steps iii-v): builds
  * Z[(a,p)][(s,k)] = sqrt(I_s) A_{beta(a)}^{pk}(s) exp(-2 pi i (nu/c) x_a . X_hrz,s)
- * (eq. "littlez") in FP64 and forms V = Z Z^dagger (eq. "zz") with a plain
- * triple loop.  A cross-check of the direct sum on small problems only.
- * out complex128 [N][N]. */
+ * (eq. "littlez"), or for a polarised sky
+ * Z[(a,p)][(s,k'')] = sum_k A^{pk}(s) F_as M_{kk''}(s) (eq. "fullz") with M from
+ * orc_coherency_sqrt, in FP64 and forms V = Z Z^dagger (eq. "zz") with a
+ * plain triple loop.  A cross-check of the direct sum on small problems
+ * only.  out complex128 [N][N]. */
 int orc_vis_outer(const orc_problem *P, double lst, double nu, double *out)
 {
+    if (P->stokes_quv && P->n_ax != 2) return -3;
     orc_inst I;
     int rc = inst_prepare(P, lst, nu, &I);
     if (rc) return rc;
@@ -389,13 +444,30 @@ int orc_vis_outer(const orc_problem *P, double lst, double nu, double *out)
             double tau = (P->enu[3 * a] * x[0] + P->enu[3 * a + 1] * x[1]) + P->enu[3 * a + 2] * x[2];
             double phase = -2.0 * ORC_PI * kappa * tau;
             double c = cos(phase), sn = sin(phase), w = sqrt(I.flux[s]);
-            for (int p = 0; p < nfd; ++p)
+            double m[4];
+            if (I.quv) orc_coherency_sqrt(I.flux[s], I.quv[3 * s], I.quv[3 * s + 1], I.quv[3 * s + 2], m);
+            for (int p = 0; p < nfd; ++p) {
+                /* A^{pk} F for both axes */
+                double af[2][2];
                 for (int k = 0; k < nax; ++k) {
                     const double *u = &I.A[2 * ((((int64_t)ba * nfd + p) * nax + k) * K + s)];
-                    int64_t o = ((int64_t)a * nfd + p) * M + s * nax + k;
-                    Z[2 * o] = w * (u[0] * c - u[1] * sn);
-                    Z[2 * o + 1] = w * (u[0] * sn + u[1] * c);
+                    af[k][0] = u[0] * c - u[1] * sn;
+                    af[k][1] = u[0] * sn + u[1] * c;
                 }
+                for (int k = 0; k < nax; ++k) {
+                    int64_t o = ((int64_t)a * nfd + p) * M + s * nax + k;
+                    if (!I.quv) {
+                        Z[2 * o] = w * af[k][0];
+                        Z[2 * o + 1] = w * af[k][1];
+                    } else if (k == 0) {  /* A0 M00 + A1 M10 */
+                        Z[2 * o] = af[0][0] * m[0] + (af[1][0] * m[1] - af[1][1] * m[2]);
+                        Z[2 * o + 1] = af[0][1] * m[0] + (af[1][0] * m[2] + af[1][1] * m[1]);
+                    } else {              /* A1 M11 */
+                        Z[2 * o] = af[1][0] * m[3];
+                        Z[2 * o + 1] = af[1][1] * m[3];
+                    }
+                }
+            }
         }
     }
     for (int64_t i = 0; i < N; ++i)

@@ -29,7 +29,7 @@ EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv
            "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static", "mv_autotune",
            "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
            "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
-           "mv_surrogate_load", "mv_set_beam_surrogate"]
+           "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_last_error.restype = ctypes.c_char_p
     lib.mv_last_error.argtypes = []
     lib.mv_init_sky.argtypes = [vp, i64, vp, vp, vp, vp, dp]
+    lib.mv_set_sky_polarisation.argtypes = [vp, i64, vp, vp, vp]
     lib.mv_set_beam_gaussian.argtypes = [vp, dp]
     lib.mv_set_beam_grid.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, dp, dp, dp, dp]
     lib.mv_set_antennas.argtypes = [vp, i32, vp, vp, dp]
@@ -190,6 +191,14 @@ class Simulator:
         ra, dec, fl = _f64(ra), _f64(dec), _f64(flux_ref)
         si = None if spec_idx is None else _f64(spec_idx)
         self._check(self._lib.mv_init_sky(self._h, ra.size, _p(ra), _p(dec), _p(fl), _p(si), float(nu_ref)))
+
+    def set_sky_polarisation(self, stokes_quv=None):
+        """Stokes Q, U, V ([3][n_src], Jy at nu_ref) of the current sky; None = unpolarised."""
+        if stokes_quv is None:
+            self._check(self._lib.mv_set_sky_polarisation(self._h, 0, None, None, None))
+            return
+        q = _f64(stokes_quv).reshape(3, -1)
+        self._check(self._lib.mv_set_sky_polarisation(self._h, q.shape[1], _p(q[0]), _p(q[1]), _p(q[2])))
 
     def set_beam_gaussian(self, fwhm: float):
         self._check(self._lib.mv_set_beam_gaussian(self._h, float(fwhm)))

@@ -57,7 +57,8 @@ struct mv_ctx {
     std::vector<int> h_bidx;
     double grid_nu0 = 0, grid_dnu = 0;
     // model buffers
-    Buf xeq, sqrt_flux, half_alpha, ant_e, ant_n, ant_u, bidx, grid;
+    std::vector<double> h_flux;  // I at nu_ref (host copy, for the polarised sky's coherency)
+    Buf xeq, sqrt_flux, half_alpha, pol_m, ant_e, ant_n, ant_u, bidx, grid;
     // workspace
     Buf R, counts, offsets, le, ln, lu, lidx, lazza, nlive, chan, inst, groups, planes, vdev, err, partial, sched;
     // per-batch workspace, double-buffered so that the beam evaluation and Z
@@ -363,6 +364,7 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     Model& m = c->model;
     if (!c->have_sky || !c->have_ant || !c->have_beam)
         return fail(MV_ERR_STATE, "simulate needs init_sky, set_antennas and a beam first");
+    if (m.pol_m && m.n_ax != 2) return fail(MV_ERR_STATE, "a polarised sky needs a two-axis beam");
     if (prec != MV_PREC_FP32 && prec != MV_PREC_BF16X3 && prec != MV_PREC_FP16X3)
         return fail(MV_ERR_ARG, "unknown precision %d", (int)prec);
     if (!V) return fail(MV_ERR_ARG, "V is NULL");
@@ -842,8 +844,47 @@ mv_status mv_init_sky(mv_ctx* c, int64_t n_src, const double* ra, const double* 
     c->model.xeq = (const double*)c->xeq.p;
     c->model.sqrt_flux = (const float*)c->sqrt_flux.p;
     c->model.half_alpha = (const float*)c->half_alpha.p;
+    c->model.pol_m = nullptr;
+    c->h_flux.assign(flux_ref, flux_ref + n_src);
     c->nu_ref = nu_ref;
     c->have_sky = true;
+    ++c->model_version;
+    return MV_OK;
+}
+
+mv_status mv_set_sky_polarisation(mv_ctx* c, int64_t n_src, const double* q, const double* u, const double* v) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (!c->have_sky) return fail(MV_ERR_STATE, "call mv_init_sky first");
+    if (!q && !u && !v) {
+        c->model.pol_m = nullptr;
+        ++c->model_version;
+        return MV_OK;
+    }
+    if (!q || !u || !v) return fail(MV_ERR_ARG, "stokes_q, stokes_u and stokes_v go together");
+    if (n_src != c->model.n_src) return fail(MV_ERR_ARG, "n_src %lld != the sky's %lld", (long long)n_src,
+                                             (long long)c->model.n_src);
+    DeviceGuard g(c->device);
+    mv_status s;
+    const std::vector<double>& fl = c->h_flux;
+    // C = [[I + Q, U + iV], [U - iV, I - Q]] = M M^dagger with M lower triangular
+    std::vector<float4> M(n_src);
+    for (int64_t i = 0; i < n_src; ++i) {
+        const double I = fl[i], Q = q[i], U = u[i], V = v[i];
+        if (!(std::isfinite(Q) && std::isfinite(U) && std::isfinite(V)))
+            return fail(MV_ERR_ARG, "Stokes of source %lld not finite", (long long)i);
+        if (Q * Q + U * U + V * V > I * I * (1.0 + 1e-6))
+            return fail(MV_ERR_ARG, "source %lld: Q^2 + U^2 + V^2 > I^2", (long long)i);
+        const double a = I + Q;
+        const double m00 = a > 0.0 ? std::sqrt(a) : 0.0;
+        const double m10r = m00 > 0.0 ? U / m00 : 0.0, m10i = m00 > 0.0 ? -V / m00 : 0.0;
+        const double d = I - Q - (m10r * m10r + m10i * m10i);
+        const double m11 = d > 0.0 ? std::sqrt(d) : 0.0;
+        M[i] = make_float4((float)m00, (float)m10r, (float)m10i, (float)m11);
+    }
+    if ((s = upload(c, c->pol_m, M.data(), M.size() * sizeof(float4), c->stream))) return s;
+    if ((s = cuda_check(cudaStreamSynchronize(c->stream), "set_sky_polarisation"))) return s;
+    c->model.pol_m = (const float4*)c->pol_m.p;
     ++c->model_version;
     return MV_OK;
 }

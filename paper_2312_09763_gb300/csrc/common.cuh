@@ -55,6 +55,7 @@ struct Model {
     const double* xeq;       // [3][n_src] SoA: x, y, z (eq. "xeq")
     const float* sqrt_flux;  // [n_src] sqrt(flux at nu_ref)
     const float* half_alpha; // [n_src] spectral index / 2
+    const float4* pol_m;     // [n_src] (m00, Re m10, Im m10, m11) of C = M M^dagger at nu_ref, or NULL
     // array
     int n_ant;
     const double* ant_e;     // [n_ant]
@@ -77,6 +78,16 @@ cudaError_t launch_cull(const Model& m, const double* d_R, int n_times, LiveTabl
                         long long* launches);
 cudaError_t launch_beam_planes(const Model& m, const float2* d_grid, const Chan* d_chan, int n_chan,
                                float2* d_planes, cudaStream_t st, long long* launches);
+// Z-side source factor of a polarised sky (eq. "fullz"): the two axis
+// components a0, a1 of one (beam, feed) times M = [[m00, 0], [m10, m11]] and
+// the spectral factor w: z0 = w (a0 m00 + a1 m10), z1 = w a1 m11.
+__device__ __forceinline__ void apply_sky_sqrt(float2 a0, float2 a1, float4 M, float w, float2& z0, float2& z1) {
+    z0.x = w * (a0.x * M.x + (a1.x * M.y - a1.y * M.z));
+    z0.y = w * (a0.y * M.x + (a1.x * M.z + a1.y * M.y));
+    z1.x = w * (a1.x * M.w);
+    z1.y = w * (a1.y * M.w);
+}
+
 // WA[slot] = sqrt(I_s) A(s) for the live sources; amax[slot] (zeroed by the
 // caller) receives max |WA| over the slot's components, as float bits.
 cudaError_t launch_wa(const Model& m, const float2* d_planes, const Chan* d_chan, const Inst* d_inst,

@@ -383,11 +383,24 @@ __global__ void k_wa_rows(Model m, int K, long long r0, int R, int t, float ln_r
         const long long r = r0 + i;
         const int b = (int)(r / K), s = (int)(r % K);
         const int src = lt.idx[(long long)t * lt.pitch + s];
-        const float w = m.sqrt_flux[src] * expf(m.half_alpha[src] * ln_ratio);
-        for (int c = 0; c < ncomp; ++c) {
-            const float2 v = make_float2(w * Y[(long long)i * 8 + 2 * c], w * Y[(long long)i * 8 + 2 * c + 1]);
-            wa_slot[((long long)b * ncomp + c) * wa_pitch + s] = v;
-            mx = fmaxf(mx, hypotf(v.x, v.y));
+        const float spec = expf(m.half_alpha[src] * ln_ratio);
+        if (!m.pol_m) {
+            const float w = m.sqrt_flux[src] * spec;
+            for (int c = 0; c < ncomp; ++c) {
+                const float2 v = make_float2(w * Y[(long long)i * 8 + 2 * c], w * Y[(long long)i * 8 + 2 * c + 1]);
+                wa_slot[((long long)b * ncomp + c) * wa_pitch + s] = v;
+                mx = fmaxf(mx, hypotf(v.x, v.y));
+            }
+        } else {  // two axes per feed: z = A M (eq. "fullz")
+            const float4 M = m.pol_m[src];
+            for (int c = 0; c + 1 < ncomp; c += 2) {
+                const float* y = Y + (long long)i * 8 + 2 * c;
+                float2 z0, z1;
+                apply_sky_sqrt(make_float2(y[0], y[1]), make_float2(y[2], y[3]), M, spec, z0, z1);
+                wa_slot[((long long)b * ncomp + c) * wa_pitch + s] = z0;
+                wa_slot[((long long)b * ncomp + c + 1) * wa_pitch + s] = z1;
+                mx = fmaxf(mx, fmaxf(hypotf(z0.x, z0.y), hypotf(z1.x, z1.y)));
+            }
         }
     }
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));

@@ -170,7 +170,9 @@ __device__ float wa_eval(const Model& m, const float2* __restrict__ planes, cons
     const long long o = (long long)in.t * lt.pitch + s;
     const int src = lt.idx[o];
     const float2 azza = lt.azza[o];
-    const float w = m.sqrt_flux[src] * expf(m.half_alpha[src] * ch.ln_ratio);
+    const float spec = expf(m.half_alpha[src] * ch.ln_ratio);
+    const float w = m.pol_m ? spec : m.sqrt_flux[src] * spec;
+    const float4 M = m.pol_m ? m.pol_m[src] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int ncomp = m.n_beam * m.n_feed * m.n_ax;
     if (m.beam_kind == 1) {
         const float a = w * expf(-m.gauss_c * azza.y * azza.y);
@@ -204,6 +206,7 @@ __device__ float wa_eval(const Model& m, const float2* __restrict__ planes, cons
     }
     const long long plane = (long long)m.n_za * m.n_az;
     float mx = 0.f;
+    float2 a_prev = make_float2(0.f, 0.f);
     for (int comp = 0; comp < ncomp; ++comp) {
         const float2* P = planes + ((long long)in.c * ncomp + comp) * plane;
         float re = 0.f, im = 0.f;
@@ -220,9 +223,19 @@ __device__ float wa_eval(const Model& m, const float2* __restrict__ planes, cons
             re = fmaf(sg[r], rr, re);
             im = fmaf(sg[r], ri, im);
         }
-        const float2 v = make_float2(w * re, w * im);
-        out[(long long)comp * wa_pitch] = v;
-        mx = fmaxf(mx, hypotf(v.x, v.y));
+        if (!m.pol_m) {
+            const float2 v = make_float2(w * re, w * im);
+            out[(long long)comp * wa_pitch] = v;
+            mx = fmaxf(mx, hypotf(v.x, v.y));
+        } else if ((comp & 1) == 0) {  // axis 0 of a (beam, feed): wait for axis 1
+            a_prev = make_float2(re, im);
+        } else {
+            float2 z0, z1;
+            apply_sky_sqrt(a_prev, make_float2(re, im), M, w, z0, z1);
+            out[(long long)(comp - 1) * wa_pitch] = z0;
+            out[(long long)comp * wa_pitch] = z1;
+            mx = fmaxf(mx, fmaxf(hypotf(z0.x, z0.y), hypotf(z1.x, z1.y)));
+        }
     }
     return mx;
 }

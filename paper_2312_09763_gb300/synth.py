@@ -158,6 +158,7 @@ class Workload:
     freqs: np.ndarray
     beam_idx: Optional[np.ndarray] = None
     notes: dict = field(default_factory=dict)
+    stokes_quv: Optional[np.ndarray] = None   # [3][n_src] Q, U, V (Jy at nu_ref) of a polarised sky
 
     @property
     def n_ant(self) -> int:
@@ -338,14 +339,19 @@ def gaussian_random_field(theta: np.ndarray, phi: np.ndarray, lmax: int, cl: np.
 
 
 def polarised_diffuse(n_ant: int = 350, nside: int = 128, n_chan: int = 32, n_times: int = 120,
-                      n_za: int = 91, n_az: int = 360, lmax: int = None) -> Workload:
+                      n_za: int = 91, n_az: int = 360, lmax: int = None, full_stokes: bool = False) -> Workload:
     """Workload 2: the HERA-like array, a diffuse sky of 12 nside^2 HEALPix
     pixel centres whose intensities are a log-normal Gaussian random field
     (C_l ~ l^-2.5 for l >= 1, C_0 = 0, field normalised to unit variance)
     turned into fluxes (intensity x pixel area, about 1e3 Jy in total, spectral
     index -2.5), 32 channels centred in 140-160 MHz, 120 LSTs 30 s apart, and
     a 2 feed x 2 axis dipole-like Jones beam on a 1 deg x 1 deg x 1 MHz grid
-    (138-162 MHz) with a 5 % ripple and a smooth phase of at most 0.1 rad."""
+    (138-162 MHz) with a 5 % ripple and a smooth phase of at most 0.1 rad.
+
+    full_stokes adds linear polarisation of fraction 0.2 with an angle
+    chi = pi Phi(h) from a second random field h (same spectrum, Phi the
+    normal CDF), Q = 0.2 I cos 2chi, U = 0.2 I sin 2chi, and circular
+    polarisation V = 0.01 I g' from a third field g' clipped to [-1, 1]."""
     lmax = 3 * nside - 1 if lmax is None else lmax
     theta, phi = healpix_ring_pix2ang(nside)
     ell = np.arange(lmax + 1, dtype=float)
@@ -375,6 +381,15 @@ def polarised_diffuse(n_ant: int = 350, nside: int = 128, n_chan: int = 32, n_ti
     J[0, 1, 1] = -np.sin(AZ)
     J = (J * (env * rip * np.exp(1j * pha))[None, None, None]).astype(np.complex64)
     beam = ("grid", J, 138e6, 1e6, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
-    return Workload(f"polarised_diffuse: {n_ant} ant x {npix} HEALPix pixels (nside {nside}) x {n_chan} ch x "
-                    f"{n_times} t, 2x2 Jones beam", ra, dec, flux, np.full(npix, -2.5), 150e6, enu, HERA_LAT,
-                    beam, lsts, freqs)
+    w = Workload(f"polarised_diffuse: {n_ant} ant x {npix} HEALPix pixels (nside {nside}) x {n_chan} ch x "
+                 f"{n_times} t, 2x2 Jones beam", ra, dec, flux, np.full(npix, -2.5), 150e6, enu, HERA_LAT,
+                 beam, lsts, freqs)
+    if full_stokes:
+        from scipy.special import ndtr
+        h = gaussian_random_field(theta, phi, lmax, cl, rng(2, "pol_angle"))
+        chi = np.pi * ndtr((h - h.mean()) / h.std())
+        gv = gaussian_random_field(theta, phi, lmax, cl, rng(2, "circular"))
+        gv = np.clip((gv - gv.mean()) / gv.std(), -1, 1)
+        w.stokes_quv = np.stack([0.2 * flux * np.cos(2 * chi), 0.2 * flux * np.sin(2 * chi), 0.01 * flux * gv])
+        w.name = w.name.replace("2x2 Jones beam", "2x2 Jones beam, full Stokes")
+    return w

@@ -13,7 +13,7 @@ def oracle_problem(w: synth.Workload, beam=None) -> oracle.Problem:
         vals, nu0, dnu, dza, daz, interp = beam[1:7]
         beam = ("grid", np.asarray(vals).astype(np.complex128), nu0, dnu, dza, daz, interp)
     return oracle.Problem(ra=w.ra, dec=w.dec, flux_ref=w.flux_ref, enu=w.enu, lat=w.lat, beam=beam,
-                          spec_idx=w.spec_idx, nu_ref=w.nu_ref, beam_idx=w.beam_idx)
+                          spec_idx=w.spec_idx, nu_ref=w.nu_ref, beam_idx=w.beam_idx, stokes_quv=w.stokes_quv)
 
 
 def simulator(w: synth.Workload, interp: str = "cubic", **kw):
@@ -22,6 +22,8 @@ def simulator(w: synth.Workload, interp: str = "cubic", **kw):
     sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
     sim.set_beam(w.beam)
     sim.set_antennas(w.enu, w.beam_idx, w.lat)
+    if w.stokes_quv is not None:
+        sim.set_sky_polarisation(w.stokes_quv)
     return sim
 
 
