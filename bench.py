@@ -95,8 +95,10 @@ def workload(args):
         return synth.polarised_diffuse()
     if args.workload == "uneven":
         return synth.batched_uneven()
-    if args.small:  # profiling captures: 64 channels of 1 LST, 1.5e4 sources (~2.7 GB of Z planes)
-        return synth.hera_like(n_ant=350, n_src=15_000, n_chan=64, n_times=1)
+    if args.small:  # profiling captures: 16 channels of 1 LST of the full sky (~2.2 GB of Z planes)
+        w = synth.hera_like(n_ant=350, n_src=100_000, n_chan=16, n_times=1)
+        w.freqs = synth.hera_like().freqs[24:40]
+        return w
     return synth.hera_like()
 
 

@@ -37,6 +37,8 @@ def _compile(src: str, extra) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
+    if extra:
+        sys.stderr.write(r.stderr)
     return obj
 
 

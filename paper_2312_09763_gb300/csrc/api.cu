@@ -60,10 +60,10 @@ struct mv_ctx {
     std::vector<double> h_flux;  // I at nu_ref (host copy, for the polarised sky's coherency)
     Buf xeq, sqrt_flux, half_alpha, pol_m, ant_e, ant_n, ant_u, bidx, grid;
     // workspace
-    Buf R, counts, offsets, le, ln, lu, lidx, lazza, nlive, chan, inst, groups, planes, vdev, err, partial, sched;
+    Buf R, counts, offsets, le, ln, lu, lsfix, lseps, lidx, lazza, nlive, chan, inst, groups, planes, vdev, err, partial, sched;
     // per-batch workspace, double-buffered so that the beam evaluation and Z
     // build of one batch (on zstream) overlap the HERK of the previous one
-    Buf wa[2], amax[2], u[2], ulo[2];
+    Buf wa[2], amax[2], u[2], ulo[2], aph[2];
     cudaStream_t zstream = nullptr;
     cudaEvent_t ev_prep = nullptr, ev_zdone[2] = {nullptr, nullptr}, ev_hdone[2] = {nullptr, nullptr};
     int n_sms = 148;
@@ -331,6 +331,7 @@ struct Prepared {
     int n_times = 0, n_chan = 0, n_inst = 0;
     int N = 0, rows = 0, bpt = 0, ncomp = 0, max_slots = 0, zprec = 0;
     int nbuf = 1;  // workspace sets in use (2: Z side and HERK overlap)
+    int n_phase = 2;  // AntPhase entries per group
     const Plan* plan = nullptr;
     std::vector<int> h_nlive;  // live counts on the host (learned-beam calls only)
     long long pitch = 0, k_pitch = 0;
@@ -437,13 +438,24 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if ((s = ensure(c, c->le, sizeof(double) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->ln, sizeof(double) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lu, sizeof(double) * (size_t)pitch * n_times))) return s;
+    if ((s = ensure(c, c->lsfix, sizeof(unsigned) * 3 * (size_t)pitch * n_times))) return s;
+    if ((s = ensure(c, c->lseps, sizeof(float) * 3 * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lidx, sizeof(int) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lazza, sizeof(float2) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
     p.nbuf = (P.batches.size() > 1 && c->opt.overlap_batches) ? 2 : 1;
+    // antenna phase factors: per batch, groups x wavenumbers per group x antennas
+    p.n_phase = 2;
+    int max_groups = 1;
+    for (auto& b : P.batches) {
+        max_groups = std::max(max_groups, b.ng);
+        for (int gi = b.g0; gi < b.g0 + b.ng; ++gi)
+            if (!P.groups[gi].uniform) p.n_phase = std::max(p.n_phase, P.groups[gi].n);
+    }
     for (int k = 0; k < p.nbuf; ++k) {
         if ((s = ensure(c, c->wa[k], sizeof(float2) * (size_t)max_slots * p.ncomp * pitch))) return s;
         if ((s = ensure(c, c->amax[k], sizeof(float) * (size_t)max_slots))) return s;
+        if ((s = ensure(c, c->aph[k], sizeof(AntPhase) * (size_t)max_groups * p.n_phase * m.n_ant))) return s;
     }
     if ((s = ensure(c, c->sched, sizeof(int) * (size_t)(max_slots + 8)))) return s;
     const size_t plane_elems = (size_t)p.rows * p.k_pitch * max_slots;
@@ -474,6 +486,8 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     lt.e = (double*)c->le.p;
     lt.n = (double*)c->ln.p;
     lt.u = (double*)c->lu.p;
+    lt.sfix = (unsigned*)c->lsfix.p;
+    lt.seps = (float*)c->lseps.p;
     lt.idx = (int*)c->lidx.p;
     lt.azza = (float2*)c->lazza.p;
     lt.n_live = (int*)c->nlive.p;
@@ -513,7 +527,8 @@ mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int 
     Timed tz(c, MV_KERNEL_ZBUILD, st);
     e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, p.lt,
                       (const float2*)c->wa[k].p, p.pitch, (const float*)c->amax[k].p, c->u[k].p, c->ulo[k].p,
-                      p.zprec, p.rows, p.k_pitch, p.nbuf == 2 ? 4 * c->n_sms : 0, st, L);
+                      p.zprec, p.rows, p.k_pitch, p.nbuf == 2 ? 4 * c->n_sms : 0, (AntPhase*)c->aph[k].p,
+                      p.n_phase, st, L);
     tz.end();
     return launched(e, "Z build", st);
 }
@@ -581,7 +596,8 @@ std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, co
                                 h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout, c->model_version};
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
                          &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
-                         &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err};
+                         &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err,
+                         &c->lsfix, &c->lseps, &c->aph[0], &c->aph[1], &c->pol_m};
     for (const Buf* b : bufs) k.push_back((long long)(uintptr_t)b->p);
     for (const auto& b : P.batches) {
         k.push_back(b.inst0);
@@ -798,7 +814,7 @@ void mv_destroy(mv_ctx* c) {
                   &c->R, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu, &c->lidx, &c->lazza, &c->nlive,
                   &c->chan, &c->inst, &c->groups, &c->planes, &c->wa[0], &c->amax[0], &c->u[0], &c->ulo[0],
                   &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->vdev, &c->err,
-                  &c->partial, &c->sched};
+                  &c->partial, &c->sched, &c->lsfix, &c->lseps, &c->aph[0], &c->aph[1], &c->pol_m};
     for (Buf* b : all) buf_free(c, *b);
     surrogate_destroy(c->sur);
     harvest(c);

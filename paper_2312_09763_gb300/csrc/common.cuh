@@ -42,6 +42,11 @@ struct LiveTables {
     double* e;        // [n_times][pitch] East component of s_hat
     double* n;        // North
     double* u;        // Up
+    // s_hat in fixed point for the phase (NULL: not written): component c of
+    // live source s at time t is sfix[(3 t + c) pitch + s] = S + 2^31 with
+    // S = rint(s_c 2^31) (clamped to int32), and seps[...] = s_c - S 2^-31
+    unsigned* sfix;
+    float* seps;
     int* idx;         // catalogue index of each live source
     float2* azza;     // (az, za) radians, FP32
     int* n_live;      // [n_times]
@@ -102,12 +107,27 @@ struct ZGroup {
     int uniform;      // channels are equally spaced: kappa_j = kappa0 + j dkappa
     double kappa0, dkappa;
 };
+// Antenna factor of the fixed-point phase for one wavenumber kappa (turns per
+// metre): y_c = kappa x_a,c, Y_c = rint(y_c 2^32) = yh_c 2^32 + yl_c (yl
+// unsigned), yf_c = (float) y_c, negk = -sum_c yl_c 2^31 mod 2^64.  With
+// the source's S_c + 2^31 and residual eps_c (LiveTables) the phase
+// frac(kappa x_a . s_hat) follows from integer multiply-adds (zbuild.cu).
+struct alignas(16) AntPhase {
+    unsigned yl[3];
+    int yh[3];
+    float yf[3];
+    unsigned negk_lo, negk_hi, pad;
+};
+
 // Z build of a batch of groups: writes FP32 planes (prec 0) or BF16 hi/lo
 // planes (prec 1) of U into workspace slots.
+// d_aph: workspace for n_groups x n_phase x n_ant AntPhase entries, n_phase
+// >= max(2, largest group of the batch).
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
                           int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
                           const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows,
-                          long long k_pitch, int max_blocks, cudaStream_t st, long long* launches);
+                          long long k_pitch, int max_blocks, AntPhase* d_aph, int n_phase, cudaStream_t st,
+                          long long* launches);
 cudaError_t launch_herk_fp32(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                              const float* d_u, int rows, long long k_pitch, float2* d_v, int N,
                              int flush_k, cudaStream_t st, long long* launches);

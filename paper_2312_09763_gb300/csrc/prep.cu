@@ -99,6 +99,16 @@ k_cull_scatter(Model m, const double* __restrict__ R, const int* __restrict__ of
     lt.n[o] = n;
     lt.u[o] = u;
     lt.idx[o] = (int)s;
+    if (lt.sfix) {
+        const double comp[3] = {e, n, u};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double q = fmin(rint(comp[c] * 2147483648.0), 2147483647.0);  // 2^31
+            const long long o3 = ((long long)t * 3 + c) * lt.pitch + pos;
+            lt.sfix[o3] = (unsigned)((long long)q + 2147483648ll);
+            lt.seps[o3] = (float)(comp[c] - q * 4.656612873077392578125e-10);  // 2^-31
+        }
+    }
     // az = atan2(E, N) in [0, 2 pi), za = atan2(|EN|, Up): well conditioned at the pole
     const float ef = (float)e, nf = (float)n, uf = (float)u;
     float az = atan2f(ef, nf);

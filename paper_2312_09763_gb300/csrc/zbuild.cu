@@ -5,13 +5,18 @@
 // rows 2(a n_feed + p) = Re Z, 2(a n_feed + p) + 1 = Im Z and columns
 // s n_ax + k, so that V = Z Z^dagger becomes the real product U U^T.
 //
-// The phase argument (nu/c) x_a . s_hat is formed in FP64 and reduced
-// exactly modulo one turn into 64-bit fixed point (bit operations on the
-// FP64 significand); only the reduced fraction is rounded to FP32 for
-// the sine and cosine.  For the channels of one time that are equally spaced in nu,
-// (x_a . s_hat) kappa_0 and (x_a . s_hat) dkappa are formed in FP64 once per
-// (antenna, source) and the channel phases are stepped by exact 64-bit
-// integer addition of their fractions.
+// The phase argument frac((nu/c) x_a . s_hat) is formed in 64-bit fixed
+// point (turns x 2^64) with integer arithmetic: per (wavenumber, antenna)
+// y = (nu/c) x_a is split into Y = rint(y 2^32) (AntPhase, from FP64), per
+// (time, source) s_hat into S = rint(s_hat 2^31) and a residual eps; the sum
+// of Y S (a 96-bit integer) is taken modulo 2^63 with 32 x 32 -> 64-bit
+// multiply-adds, and the small term y . eps is added in FP32 (its magnitude
+// is below |y| 2^-31, so its rounding error is below 1e-13 turns for the
+// arrays here).  The phase is exact to about 2^-32 turns, with no FP64
+// arithmetic per element.  For the channels of one time that are equally
+// spaced in nu, the phases at kappa_0 and dkappa are formed once per
+// (antenna, source) and the channel phases advance by exact 64-bit integer
+// addition.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -20,18 +25,67 @@
 namespace mv {
 namespace {
 
-// frac(p) * 2^64 modulo 2^64 for an FP64 value p: exact for |p| >= 2^-11,
-// truncated below 2^-64 turns otherwise.
-__device__ __forceinline__ unsigned long long frac64(double p) {
-    const long long b = __double_as_longlong(p);
-    const int ex = (int)((b >> 52) & 0x7FF);
-    const unsigned long long mant = ((unsigned long long)b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 1075 - ex;  // |p| = mant * 2^-sh
-    unsigned long long f;
-    if (ex == 0 || sh <= 0 || sh >= 117) f = 0ull;
-    else if (sh <= 64) f = mant << (64 - sh);
-    else f = mant >> (sh - 64);
-    return b < 0 ? (0ull - f) : f;
+// frac(kappa x_a . s_hat) x 2^64 for one antenna factor p and one source
+// (S[c] = S_c + 2^31, eps[c]).  With S_c = S'_c - 2^31:
+//   sum_c Y_c S_c = sum_c yl_c S'_c - sum_c yl_c 2^31 + 2^32 sum_c yh_c S'_c  (mod 2^63),
+// which is (acc << 1) below read in 2^-64 turns; the y . eps term is added
+// after rounding to 2^-32 turns.
+__device__ __forceinline__ unsigned long long phase64(const AntPhase& p, const unsigned* S, const float* eps) {
+    unsigned long long acc = ((unsigned long long)p.negk_hi << 32) | p.negk_lo;
+    acc += (unsigned long long)p.yl[0] * S[0];
+    acc += (unsigned long long)p.yl[1] * S[1];
+    acc += (unsigned long long)p.yl[2] * S[2];
+    const unsigned h = (unsigned)p.yh[0] * S[0] + (unsigned)p.yh[1] * S[1] + (unsigned)p.yh[2] * S[2];
+    acc += (unsigned long long)h << 32;
+    const float corr = fmaf(p.yf[0], eps[0], fmaf(p.yf[1], eps[1], p.yf[2] * eps[2]));
+    const int cf = __float2int_rn(corr * 4294967296.0f);  // 2^32
+    return (acc << 1) + ((unsigned long long)(long long)cf << 32);
+}
+
+__device__ __forceinline__ AntPhase load_phase(const AntPhase* __restrict__ t) {
+    const uint4* q = reinterpret_cast<const uint4*>(t);
+    const uint4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    AntPhase p;
+    p.yl[0] = a.x; p.yl[1] = a.y; p.yl[2] = a.z;
+    p.yh[0] = (int)a.w; p.yh[1] = (int)b.x; p.yh[2] = (int)b.y;
+    p.yf[0] = __uint_as_float(b.z); p.yf[1] = __uint_as_float(b.w); p.yf[2] = __uint_as_float(c.x);
+    p.negk_lo = c.y; p.negk_hi = c.z; p.pad = 0;
+    return p;
+}
+
+// Antenna factors of every wavenumber of a batch's groups: entry e of group
+// gl is kappa0 (e = 0) and dkappa (e = 1) of an equally spaced group, or the
+// wavenumber of its instance e otherwise.
+__global__ void k_ant_phase(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
+                            const ZGroup* __restrict__ groups, int g_first, int n_phase, AntPhase* __restrict__ tab) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.y, gl = blockIdx.z;
+    if (a >= m.n_ant) return;
+    const ZGroup g = groups[g_first + gl];
+    double kap;
+    if (g.uniform) {
+        if (e >= 2) return;
+        kap = e == 0 ? g.kappa0 : g.dkappa;
+    } else {
+        if (e >= g.n) return;
+        kap = chan[inst[g.inst0 + e].c].kappa;
+    }
+    const double x[3] = {m.ant_e[a], m.ant_n[a], m.ant_u[a]};
+    AntPhase p;
+    unsigned long long nk = 0ull;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double y = kap * x[c];
+        const long long Y = __double2ll_rn(y * 4294967296.0);  // 2^32
+        p.yl[c] = (unsigned)Y;
+        p.yh[c] = (int)(Y >> 32);
+        p.yf[c] = (float)y;
+        nk -= (unsigned long long)p.yl[c] << 31;
+    }
+    p.negk_lo = (unsigned)nk;
+    p.negk_hi = (unsigned)(nk >> 32);
+    p.pad = 0u;
+    tab[((long long)gl * n_phase + e) * m.n_ant + a] = p;
 }
 
 // cos(2 pi r), sin(2 pi r) for the fixed-point turn F (r = frac(F / 2^64)):
@@ -103,7 +157,8 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                                             const Chan* __restrict__ chan, const ZGroup* __restrict__ groups,
                                             int g_first, const LiveTables& lt, const float2* __restrict__ wa,
                                             long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo,
-                                            int rows, long long k_pitch, int ant_per_block, int bx, int by, int bz) {
+                                            int rows, long long k_pitch, int ant_per_block,
+                                            const AntPhase* __restrict__ aph, int n_phase, int bx, int by, int bz) {
     const ZGroup g = groups[g_first + bz];
     const int t = inst[g.inst0].t;
     const int nl = lt.n_live[t];
@@ -116,29 +171,40 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
     const int nfd = m.n_feed;
     const int ncomp = m.n_beam * nfd * NAX;
     const bool live0 = s0 < nl, live1 = s0 + 1 < nl;
-    double e0 = 0, n0 = 0, u0 = 0, e1 = 0, n1 = 0, u1 = 0;
-    const long long lo = (long long)t * lt.pitch + s0;
-    if (live0) { e0 = lt.e[lo]; n0 = lt.n[lo]; u0 = lt.u[lo]; }
-    if (live1) { e1 = lt.e[lo + 1]; n1 = lt.n[lo + 1]; u1 = lt.u[lo + 1]; }
+    // the two sources' direction in fixed point (zeros past the live count)
+    unsigned S0[3] = {0u, 0u, 0u}, S1[3] = {0u, 0u, 0u};
+    float E0[3] = {0.f, 0.f, 0.f}, E1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const long long o3 = ((long long)t * 3 + c) * lt.pitch + s0;
+        if (live0) {
+            const uint2 q = *reinterpret_cast<const uint2*>(lt.sfix + o3);
+            const float2 r = *reinterpret_cast<const float2*>(lt.seps + o3);
+            S0[c] = q.x; E0[c] = r.x;
+            if (live1) { S1[c] = q.y; E1[c] = r.y; }
+        }
+    }
     const long long col = (long long)s0 * NAX;
+    const AntPhase* tab = aph + (long long)bz * n_phase * m.n_ant;
+    const bool step = g.uniform && g.n > 1;
     for (int a = a_begin; a < a_end; ++a) {
-        // path lengths x_a . s_hat in metres (FP64)
-        const double ae = m.ant_e[a], an = m.ant_n[a], au = m.ant_u[a];
-        const double d0 = fma(ae, e0, fma(an, n0, au * u0));
-        const double d1 = fma(ae, e1, fma(an, n1, au * u1));
         const int beta = m.beam_idx[a];
         unsigned long long F0 = 0ull, F1 = 0ull, Q0 = 0ull, Q1 = 0ull;
         if (g.uniform) {
-            F0 = frac64(d0 * g.kappa0);
-            F1 = frac64(d1 * g.kappa0);
-            Q0 = frac64(d0 * g.dkappa);
-            Q1 = frac64(d1 * g.dkappa);
+            const AntPhase p0 = load_phase(tab + a);
+            F0 = phase64(p0, S0, E0);
+            F1 = phase64(p0, S1, E1);
+            if (step) {
+                const AntPhase pd = load_phase(tab + m.n_ant + a);
+                Q0 = phase64(pd, S0, E0);
+                Q1 = phase64(pd, S1, E1);
+            }
         }
         for (int j = 0; j < g.n; ++j) {
             if (!g.uniform) {
-                const double kap = chan[inst[g.inst0 + j].c].kappa;
-                F0 = frac64(d0 * kap);
-                F1 = frac64(d1 * kap);
+                const AntPhase pj = load_phase(tab + (long long)j * m.n_ant + a);
+                F0 = phase64(pj, S0, E0);
+                F1 = phase64(pj, S1, E1);
             }
             float c0, sn0, c1, sn1;
             cos_sin_turns(F0, c0, sn0);
@@ -178,12 +244,12 @@ __global__ void __launch_bounds__(128, 8)
 k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
          const ZGroup* __restrict__ groups, int g_first, LiveTables lt, const float2* __restrict__ wa,
          long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo, int rows, long long k_pitch,
-         int ant_per_block, int nx, int ny, long long n_items) {
+         int ant_per_block, const AntPhase* __restrict__ aph, int n_phase, int nx, int ny, long long n_items) {
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int bx = (int)(item % nx);
         const long long rest = item / nx;
         zbuild_item<PREC, NAX>(m, inst, chan, groups, g_first, lt, wa, wa_pitch, amax, u, ulo, rows, k_pitch,
-                               ant_per_block, bx, (int)(rest % ny), (int)(rest / ny));
+                               ant_per_block, aph, n_phase, bx, (int)(rest % ny), (int)(rest / ny));
     }
 }
 
@@ -192,14 +258,18 @@ k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
                           int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
                           const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows, long long k_pitch,
-                          int max_blocks, cudaStream_t st, long long* launches) {
+                          int max_blocks, AntPhase* d_aph, int n_phase, cudaStream_t st, long long* launches) {
+    if (!lt.sfix || !d_aph || n_phase < 2) return cudaErrorInvalidValue;
+    k_ant_phase<<<dim3((unsigned)((m.n_ant + 127) / 128), (unsigned)n_phase, (unsigned)n_groups), 128, 0, st>>>(
+        m, d_inst, d_chan, d_groups, g_first, n_phase, d_aph);
+    *launches += 1;
     const int apb = 32;
     const int nx = (int)((lt.pitch / 2 + 127) / 128), ny = (m.n_ant + apb - 1) / apb;
     const long long n_items = (long long)nx * ny * n_groups;
     const long long grid = max_blocks > 0 ? std::min<long long>(n_items, max_blocks) : n_items;
 #define MV_ZB(P, A) \
     k_zbuild<P, A><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, \
-                                                   d_u, d_u_lo, rows, k_pitch, apb, nx, ny, n_items)
+                                                   d_u, d_u_lo, rows, k_pitch, apb, d_aph, n_phase, nx, ny, n_items)
     if (m.n_ax == 1) {
         if (prec == 0) MV_ZB(0, 1); else if (prec == 1) MV_ZB(1, 1); else MV_ZB(2, 1);
     } else {
