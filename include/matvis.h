@@ -77,7 +77,7 @@ typedef struct {
 
 typedef struct {
     int interp;                 /* mv_interp for gridded beams (default cubic) */
-    int max_batch;              /* channels of one time processed per launch (0 = auto) */
+    int max_batch;              /* channels of one time processed per launch (0 = auto, at most 256) */
     int herk_flush_kblocks;     /* tensor-core HERK: 64-column k-blocks accumulated in one
                                    TMEM buffer before it is added into the FP32 running
                                    sum (0 = auto = 4) */

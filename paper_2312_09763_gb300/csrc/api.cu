@@ -278,7 +278,7 @@ ZGroup make_group(const Plan& P, int i0, int n, int slot0) {
 }
 
 int auto_batch(mv_ctx* c, long long slot_bytes) {
-    if (c->opt.max_batch > 0) return c->opt.max_batch;
+    if (c->opt.max_batch > 0) return std::min(c->opt.max_batch, kMaxBatch);
     const long long budget = 20ll << 30;  // workspace for the Z planes
     long long b = budget / std::max(slot_bytes, 1ll);
     return (int)std::max(1ll, std::min(b, 64ll));

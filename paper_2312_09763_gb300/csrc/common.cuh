@@ -107,6 +107,9 @@ struct ZGroup {
     int uniform;      // channels are equally spaced: kappa_j = kappa0 + j dkappa
     double kappa0, dkappa;
 };
+// Largest number of instances of one batch (channels of one time, or pairs).
+constexpr int kMaxBatch = 256;
+
 // Antenna factor of the fixed-point phase for one wavenumber kappa (turns per
 // metre): y_c = kappa x_a,c, Y_c = rint(y_c 2^32) = yh_c 2^32 + yl_c (yl
 // unsigned), yf_c = (float) y_c, negk = -sum_c yl_c 2^31 mod 2^64.  With

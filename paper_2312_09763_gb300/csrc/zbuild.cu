@@ -112,54 +112,59 @@ __device__ __forceinline__ void cos_sin_turns(unsigned long long F, float& c, fl
 // Store 2 n_ax consecutive entries of one row of U (two sources).
 template <int PREC, int NAX>
 __device__ __forceinline__ void put_row(void* u, void* ulo, long long o, const float* v, float scale) {
-    if (PREC == 0) {
+    if constexpr (PREC == 0) {
         float* p = static_cast<float*>(u) + o;
         if (NAX == 1) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
         else *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-        return;
-    }
-    uint32_t hi[NAX], lo[NAX];
-#pragma unroll
-    for (int i = 0; i < NAX; ++i) {
-        const float x0 = PREC == 2 ? v[2 * i] * scale : v[2 * i];
-        const float x1 = PREC == 2 ? v[2 * i + 1] * scale : v[2 * i + 1];
-        if (PREC == 1) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-            hi[i] = *reinterpret_cast<const uint32_t*>(&h);
-            lo[i] = *reinterpret_cast<const uint32_t*>(&l);
-        } else {
-            const __half2 h = __floats2half2_rn(x0, x1);
-            const float2 hf = __half22float2(h);
-            const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-            hi[i] = *reinterpret_cast<const uint32_t*>(&h);
-            lo[i] = *reinterpret_cast<const uint32_t*>(&l);
-        }
-    }
-    uint16_t* ph = static_cast<uint16_t*>(u) + o;
-    uint16_t* pl = static_cast<uint16_t*>(ulo) + o;
-    if (NAX == 1) {
-        *reinterpret_cast<uint32_t*>(ph) = hi[0];
-        *reinterpret_cast<uint32_t*>(pl) = lo[0];
     } else {
-        *reinterpret_cast<uint2*>(ph) = make_uint2(hi[0], hi[1]);
-        *reinterpret_cast<uint2*>(pl) = make_uint2(lo[0], lo[1]);
+        uint32_t hi[NAX], lo[NAX];
+#pragma unroll
+        for (int i = 0; i < NAX; ++i) {
+            const float x0 = PREC == 2 ? v[2 * i] * scale : v[2 * i];
+            const float x1 = PREC == 2 ? v[2 * i + 1] * scale : v[2 * i + 1];
+            if (PREC == 1) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                const float2 hf = __bfloat1622float2(h);
+                const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+                lo[i] = *reinterpret_cast<const uint32_t*>(&l);
+            } else {
+                const __half2 h = __floats2half2_rn(x0, x1);
+                const float2 hf = __half22float2(h);
+                const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+                hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+                lo[i] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+        }
+        uint16_t* ph = static_cast<uint16_t*>(u) + o;
+        uint16_t* pl = static_cast<uint16_t*>(ulo) + o;
+        if (NAX == 1) {
+            *reinterpret_cast<uint32_t*>(ph) = hi[0];
+            *reinterpret_cast<uint32_t*>(pl) = lo[0];
+        } else {
+            *reinterpret_cast<uint2*>(ph) = make_uint2(hi[0], hi[1]);
+            *reinterpret_cast<uint2*>(pl) = make_uint2(lo[0], lo[1]);
+        }
     }
 }
 
-// One work item (bx, by, bz): thread t builds the two adjacent sources
+// Channels between exact phase evaluations when the channels of a group are
+// equally spaced: in between, cos(2 pi F) + i sin(2 pi F) advances by one
+// complex product with e^{2 pi i dF} per channel (three FP32 steps at most,
+// each adding about 2^-23 relative error).
+constexpr int kAnchor = 4;
+
+// One work item (bx, by, group g): thread t builds the two adjacent sources
 // 2 (bx 128 + t) and +1 (columns 2 n_ax wide) for antennas
-// [by ant_per_block, +ant_per_block) and every instance of group bz.
+// [by ant_per_block, +ant_per_block) and every instance of the group.
 // Sources past the live count (up to the k padding) are written as zeros.
+// scale[j]: the FP16 scale of the group's instance j.
 template <int PREC, int NAX>
-__device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restrict__ inst,
-                                            const Chan* __restrict__ chan, const ZGroup* __restrict__ groups,
-                                            int g_first, const LiveTables& lt, const float2* __restrict__ wa,
-                                            long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo,
+__device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restrict__ inst, const ZGroup& g,
+                                            const LiveTables& lt, const float2* __restrict__ wa,
+                                            long long wa_pitch, const float* __restrict__ scale, void* u, void* ulo,
                                             int rows, long long k_pitch, int ant_per_block,
-                                            const AntPhase* __restrict__ aph, int n_phase, int bx, int by, int bz) {
-    const ZGroup g = groups[g_first + bz];
+                                            const AntPhase* __restrict__ tab, int bx, int by) {
     const int t = inst[g.inst0].t;
     const int nl = lt.n_live[t];
     const long long kpad = ((long long)nl * NAX + kKPad - 1) / kKPad * kKPad;
@@ -169,7 +174,7 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
     const int a_end = min(m.n_ant, a_begin + ant_per_block);
     const long long slot_stride = (long long)rows * k_pitch;
     const int nfd = m.n_feed;
-    const int ncomp = m.n_beam * nfd * NAX;
+    const long long wa_slot = (long long)m.n_beam * nfd * NAX * wa_pitch;
     const bool live0 = s0 < nl, live1 = s0 + 1 < nl;
     // the two sources' direction in fixed point (zeros past the live count)
     unsigned S0[3] = {0u, 0u, 0u}, S1[3] = {0u, 0u, 0u};
@@ -185,11 +190,11 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
         }
     }
     const long long col = (long long)s0 * NAX;
-    const AntPhase* tab = aph + (long long)bz * n_phase * m.n_ant;
     const bool step = g.uniform && g.n > 1;
     for (int a = a_begin; a < a_end; ++a) {
         const int beta = m.beam_idx[a];
         unsigned long long F0 = 0ull, F1 = 0ull, Q0 = 0ull, Q1 = 0ull;
+        float rc0 = 1.f, rs0 = 0.f, rc1 = 1.f, rs1 = 0.f;  // e^{2 pi i dF} of the two sources
         if (g.uniform) {
             const AntPhase p0 = load_phase(tab + a);
             F0 = phase64(p0, S0, E0);
@@ -198,21 +203,24 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                 const AntPhase pd = load_phase(tab + m.n_ant + a);
                 Q0 = phase64(pd, S0, E0);
                 Q1 = phase64(pd, S1, E1);
+                cos_sin_turns(Q0, rc0, rs0);
+                cos_sin_turns(Q1, rc1, rs1);
             }
         }
+        long long base = (long long)g.slot0 * slot_stride;
+        const float2* w = wa + (long long)g.slot0 * wa_slot + (long long)beta * nfd * NAX * wa_pitch + s0;
+        float c0 = 1.f, sn0 = 0.f, c1 = 1.f, sn1 = 0.f;
         for (int j = 0; j < g.n; ++j) {
             if (!g.uniform) {
                 const AntPhase pj = load_phase(tab + (long long)j * m.n_ant + a);
                 F0 = phase64(pj, S0, E0);
                 F1 = phase64(pj, S1, E1);
             }
-            float c0, sn0, c1, sn1;
-            cos_sin_turns(F0, c0, sn0);
-            cos_sin_turns(F1, c1, sn1);
-            const int slot = g.slot0 + j;
-            const long long base = (long long)slot * slot_stride;
-            const float scale = PREC == 2 ? ldexpf(1.f, fp16_scale_exp(amax[slot])) : 1.f;
-            const float2* w = wa + ((long long)slot * ncomp + (long long)beta * nfd * NAX) * wa_pitch + s0;
+            if (!step || j % kAnchor == 0) {
+                cos_sin_turns(F0, c0, sn0);
+                cos_sin_turns(F1, c1, sn1);
+            }
+            const float sc = PREC == 2 ? scale[j] : 1.f;
             for (int p = 0; p < nfd; ++p) {
                 float re[2 * NAX], im[2 * NAX];
 #pragma unroll
@@ -228,28 +236,47 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                     im[NAX + k] = fmaf(A.w, c1, -A.z * sn1);
                 }
                 const long long r = 2ll * (a * nfd + p);
-                put_row<PREC, NAX>(u, ulo, base + r * k_pitch + col, re, scale);
-                put_row<PREC, NAX>(u, ulo, base + (r + 1) * k_pitch + col, im, scale);
+                put_row<PREC, NAX>(u, ulo, base + r * k_pitch + col, re, sc);
+                put_row<PREC, NAX>(u, ulo, base + (r + 1) * k_pitch + col, im, sc);
             }
-            F0 += Q0;
-            F1 += Q1;
+            if (step) {
+                F0 += Q0;
+                F1 += Q1;
+                // (c + i s) e^{2 pi i dF}
+                const float nc0 = fmaf(c0, rc0, -sn0 * rs0), nc1 = fmaf(c1, rc1, -sn1 * rs1);
+                sn0 = fmaf(sn0, rc0, c0 * rs0);
+                sn1 = fmaf(sn1, rc1, c1 * rs1);
+                c0 = nc0;
+                c1 = nc1;
+            }
+            base += slot_stride;
+            w += wa_slot;
         }
     }
 }
 
 // Grid-stride over the work items, so that the launch can be held to a fixed
-// number of resident blocks per SM (room left for a concurrent HERK).
+// number of resident blocks per SM (room left for a concurrent HERK).  The
+// FP16 scales of the item's instances go to shared memory once per item.
 template <int PREC, int NAX>
 __global__ void __launch_bounds__(128, 8)
-k_zbuild(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
-         const ZGroup* __restrict__ groups, int g_first, LiveTables lt, const float2* __restrict__ wa,
-         long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo, int rows, long long k_pitch,
-         int ant_per_block, const AntPhase* __restrict__ aph, int n_phase, int nx, int ny, long long n_items) {
+k_zbuild(Model m, const Inst* __restrict__ inst, const ZGroup* __restrict__ groups, int g_first, LiveTables lt,
+         const float2* __restrict__ wa, long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo,
+         int rows, long long k_pitch, int ant_per_block, const AntPhase* __restrict__ aph, int n_phase, int nx,
+         int ny, long long n_items) {
+    __shared__ float scale[kMaxBatch];
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int bx = (int)(item % nx);
         const long long rest = item / nx;
-        zbuild_item<PREC, NAX>(m, inst, chan, groups, g_first, lt, wa, wa_pitch, amax, u, ulo, rows, k_pitch,
-                               ant_per_block, aph, n_phase, bx, (int)(rest % ny), (int)(rest / ny));
+        const int by = (int)(rest % ny), bz = (int)(rest / ny);
+        const ZGroup g = groups[g_first + bz];
+        __syncthreads();  // the previous item's readers are done
+        if (PREC == 2)
+            for (int j = threadIdx.x; j < g.n; j += blockDim.x)
+                scale[j] = ldexpf(1.f, fp16_scale_exp(amax[g.slot0 + j]));
+        __syncthreads();
+        zbuild_item<PREC, NAX>(m, inst, g, lt, wa, wa_pitch, scale, u, ulo, rows, k_pitch, ant_per_block,
+                               aph + (long long)bz * n_phase * m.n_ant, bx, by);
     }
 }
 
@@ -268,8 +295,8 @@ cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan
     const long long n_items = (long long)nx * ny * n_groups;
     const long long grid = max_blocks > 0 ? std::min<long long>(n_items, max_blocks) : n_items;
 #define MV_ZB(P, A) \
-    k_zbuild<P, A><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_chan, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, \
-                                                   d_u, d_u_lo, rows, k_pitch, apb, d_aph, n_phase, nx, ny, n_items)
+    k_zbuild<P, A><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u, \
+                                                   d_u_lo, rows, k_pitch, apb, d_aph, n_phase, nx, ny, n_items)
     if (m.n_ax == 1) {
         if (prec == 0) MV_ZB(0, 1); else if (prec == 1) MV_ZB(1, 1); else MV_ZB(2, 1);
     } else {
