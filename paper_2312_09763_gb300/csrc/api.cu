@@ -293,6 +293,8 @@ long long slot_bytes_of(mv_ctx* c) {
     return 4ll * 2 * N * round_up((long long)m.n_ax * src, kKPad) + 8ll * ncomp * round_up(src, kKPad);
 }
 
+constexpr int kZGroup = 16;
+
 // Every (LST, channel) pair; batches are up to B channels of one LST.
 void plan_grid(mv_ctx* c, int n_t, const double* lst, int n_nu, const double* nu, Plan& P) {
     P.lst.assign(lst, lst + n_t);
@@ -305,8 +307,12 @@ void plan_grid(mv_ctx* c, int n_t, const double* lst, int n_nu, const double* nu
         for (int f0 = 0; f0 < n_nu; f0 += B) {
             const int n = std::min(B, n_nu - f0);
             const int i0 = t * n_nu + f0;
-            Plan::Batch b{i0, n, (int)P.groups.size(), 1};
-            P.groups.push_back(make_group(P, i0, n, 0));
+            // Z build groups of at most kZGroup channels: one launch covers the
+            // batch, but its blocks work through the groups in order, so the
+            // slots written at any time (and their pages) stay few
+            Plan::Batch b{i0, n, (int)P.groups.size(), 0};
+            for (int c0 = 0; c0 < n; c0 += kZGroup, ++b.ng)
+                P.groups.push_back(make_group(P, i0 + c0, std::min(kZGroup, n - c0), c0));
             P.batches.push_back(b);
         }
 }

@@ -93,8 +93,9 @@ __device__ __forceinline__ void apply_sky_sqrt(float2 a0, float2 a1, float4 M, f
     z1.y = w * (a1.y * M.w);
 }
 
-// WA[slot] = sqrt(I_s) A(s) for the live sources; amax[slot] (zeroed by the
-// caller) receives max |WA| over the slot's components, as float bits.
+// WA[slot] = sqrt(I_s) A(s) for the live sources and zero for the rest of
+// the pitch; amax[slot] (zeroed by the caller) receives max |WA| over the
+// slot's components, as float bits.
 cudaError_t launch_wa(const Model& m, const float2* d_planes, const Chan* d_chan, const Inst* d_inst,
                       int inst0, int n_inst, LiveTables lt, float2* d_wa, long long wa_pitch,
                       float* d_amax, cudaStream_t st, long long* launches);

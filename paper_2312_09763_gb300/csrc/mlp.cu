@@ -771,6 +771,10 @@ cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& 
             ++*L;
             e = cudaGetLastError();
         }
+        // zeros past the live count (the Z build reads whole source pairs)
+        if (e == cudaSuccess && K < wa_pitch)
+            e = cudaMemset2DAsync(wslot + K, sizeof(float2) * wa_pitch, 0, sizeof(float2) * (wa_pitch - K),
+                                  (size_t)m.n_beam * ncomp, st);
     }
     return e;
 }

@@ -169,7 +169,12 @@ k_wa(Model m, const float2* __restrict__ planes, const Chan* __restrict__ chan,
     const int nl = lt.n_live[in.t];
     const int ncomp = m.n_beam * m.n_feed * m.n_ax;
     float mx = 0.f;
-    if (s < nl) mx = wa_eval(m, planes, chan[in.c], in, lt, s, wa + (long long)slot * ncomp * wa_pitch + s, wa_pitch);
+    float2* out = wa + (long long)slot * ncomp * wa_pitch + s;
+    if (s < nl) {
+        mx = wa_eval(m, planes, chan[in.c], in, lt, s, out, wa_pitch);
+    } else if (s < wa_pitch) {  // zeros past the live count: the Z build reads whole source pairs
+        for (int comp = 0; comp < ncomp; ++comp) out[(long long)comp * wa_pitch] = make_float2(0.f, 0.f);
+    }
     fold_amax(mx, amax + slot);
 }
 

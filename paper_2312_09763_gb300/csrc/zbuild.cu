@@ -109,20 +109,21 @@ __device__ __forceinline__ void cos_sin_turns(unsigned long long F, float& c, fl
     s = __int_as_float(__float_as_int(b) ^ (int)(((q & 2u)) << 30));
 }
 
-// Store 2 n_ax consecutive entries of one row of U (two sources).
+// Store 2 n_ax consecutive entries of one row of U (two sources): FP32, or
+// the hi and lo halves (BF16 or, scaled by sc, FP16) in the two planes.
 template <int PREC, int NAX>
-__device__ __forceinline__ void put_row(void* u, void* ulo, long long o, const float* v, float scale) {
+__device__ __forceinline__ void put_row(void* pu, void* pl, const float* v, float sc) {
     if constexpr (PREC == 0) {
-        float* p = static_cast<float*>(u) + o;
-        if (NAX == 1) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        float* p = static_cast<float*>(pu);
+        if constexpr (NAX == 1) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
         else *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
         uint32_t hi[NAX], lo[NAX];
 #pragma unroll
         for (int i = 0; i < NAX; ++i) {
-            const float x0 = PREC == 2 ? v[2 * i] * scale : v[2 * i];
-            const float x1 = PREC == 2 ? v[2 * i + 1] * scale : v[2 * i + 1];
-            if (PREC == 1) {
+            const float x0 = PREC == 2 ? v[2 * i] * sc : v[2 * i];
+            const float x1 = PREC == 2 ? v[2 * i + 1] * sc : v[2 * i + 1];
+            if constexpr (PREC == 1) {
                 const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
                 const float2 hf = __bfloat1622float2(h);
                 const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
@@ -136,14 +137,12 @@ __device__ __forceinline__ void put_row(void* u, void* ulo, long long o, const f
                 lo[i] = *reinterpret_cast<const uint32_t*>(&l);
             }
         }
-        uint16_t* ph = static_cast<uint16_t*>(u) + o;
-        uint16_t* pl = static_cast<uint16_t*>(ulo) + o;
-        if (NAX == 1) {
-            *reinterpret_cast<uint32_t*>(ph) = hi[0];
-            *reinterpret_cast<uint32_t*>(pl) = lo[0];
+        if constexpr (NAX == 1) {
+            *static_cast<uint32_t*>(pu) = hi[0];
+            *static_cast<uint32_t*>(pl) = lo[0];
         } else {
-            *reinterpret_cast<uint2*>(ph) = make_uint2(hi[0], hi[1]);
-            *reinterpret_cast<uint2*>(pl) = make_uint2(lo[0], lo[1]);
+            *static_cast<uint2*>(pu) = make_uint2(hi[0], hi[1]);
+            *static_cast<uint2*>(pl) = make_uint2(lo[0], lo[1]);
         }
     }
 }
@@ -154,17 +153,22 @@ __device__ __forceinline__ void put_row(void* u, void* ulo, long long o, const f
 // each adding about 2^-23 relative error).
 constexpr int kAnchor = 4;
 
+// Element type of the U planes.
+template <int PREC> struct Plane { using T = uint16_t; };
+template <> struct Plane<0> { using T = float; };
+
 // One work item (bx, by, group g): thread t builds the two adjacent sources
 // 2 (bx 128 + t) and +1 (columns 2 n_ax wide) for antennas
 // [by ant_per_block, +ant_per_block) and every instance of the group.
-// Sources past the live count (up to the k padding) are written as zeros.
-// scale[j]: the FP16 scale of the group's instance j.
-template <int PREC, int NAX>
+// Sources past the live count (up to the k padding) are written as zeros
+// (their WA entries are zero).  scale[j]: the FP16 scale of instance j.
+template <int PREC, int NAX, int NFD>
 __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restrict__ inst, const ZGroup& g,
                                             const LiveTables& lt, const float2* __restrict__ wa,
                                             long long wa_pitch, const float* __restrict__ scale, void* u, void* ulo,
                                             int rows, long long k_pitch, int ant_per_block,
                                             const AntPhase* __restrict__ tab, int bx, int by) {
+    using T = typename Plane<PREC>::T;
     const int t = inst[g.inst0].t;
     const int nl = lt.n_live[t];
     const long long kpad = ((long long)nl * NAX + kKPad - 1) / kKPad * kKPad;
@@ -173,8 +177,7 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
     const int a_begin = by * ant_per_block;
     const int a_end = min(m.n_ant, a_begin + ant_per_block);
     const long long slot_stride = (long long)rows * k_pitch;
-    const int nfd = m.n_feed;
-    const long long wa_slot = (long long)m.n_beam * nfd * NAX * wa_pitch;
+    const long long wa_slot = (long long)m.n_beam * NFD * NAX * wa_pitch;
     const bool live0 = s0 < nl, live1 = s0 + 1 < nl;
     // the two sources' direction in fixed point (zeros past the live count)
     unsigned S0[3] = {0u, 0u, 0u}, S1[3] = {0u, 0u, 0u};
@@ -190,67 +193,73 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
         }
     }
     const long long col = (long long)s0 * NAX;
+    T* const ub = static_cast<T*>(u) + g.slot0 * slot_stride + col;
+    T* const lb = PREC != 0 ? static_cast<T*>(ulo) + g.slot0 * slot_stride + col : nullptr;
+    const float2* const wb = wa + g.slot0 * wa_slot + s0;
     const bool step = g.uniform && g.n > 1;
     for (int a = a_begin; a < a_end; ++a) {
-        const int beta = m.beam_idx[a];
-        unsigned long long F0 = 0ull, F1 = 0ull, Q0 = 0ull, Q1 = 0ull;
-        float rc0 = 1.f, rs0 = 0.f, rc1 = 1.f, rs1 = 0.f;  // e^{2 pi i dF} of the two sources
-        if (g.uniform) {
-            const AntPhase p0 = load_phase(tab + a);
-            F0 = phase64(p0, S0, E0);
-            F1 = phase64(p0, S1, E1);
-            if (step) {
-                const AntPhase pd = load_phase(tab + m.n_ant + a);
-                Q0 = phase64(pd, S0, E0);
-                Q1 = phase64(pd, S1, E1);
-                cos_sin_turns(Q0, rc0, rs0);
-                cos_sin_turns(Q1, rc1, rs1);
-            }
-        }
-        long long base = (long long)g.slot0 * slot_stride;
-        const float2* w = wa + (long long)g.slot0 * wa_slot + (long long)beta * nfd * NAX * wa_pitch + s0;
-        float c0 = 1.f, sn0 = 0.f, c1 = 1.f, sn1 = 0.f;
-        for (int j = 0; j < g.n; ++j) {
-            if (!g.uniform) {
-                const AntPhase pj = load_phase(tab + (long long)j * m.n_ant + a);
-                F0 = phase64(pj, S0, E0);
-                F1 = phase64(pj, S1, E1);
-            }
-            if (!step || j % kAnchor == 0) {
-                cos_sin_turns(F0, c0, sn0);
-                cos_sin_turns(F1, c1, sn1);
-            }
+        const float2* w = wb + (long long)m.beam_idx[a] * (NFD * NAX) * wa_pitch;
+        T* ur = ub + 2ll * a * NFD * k_pitch;
+        T* lr = PREC != 0 ? lb + 2ll * a * NFD * k_pitch : nullptr;
+        // U rows 2(a NFD + p) + {0, 1} of instance j of the group, at phase (c, s)
+        auto emit = [&](int j, float c0, float sn0, float c1, float sn1) {
             const float sc = PREC == 2 ? scale[j] : 1.f;
-            for (int p = 0; p < nfd; ++p) {
+#pragma unroll
+            for (int p = 0; p < NFD; ++p) {
                 float re[2 * NAX], im[2 * NAX];
 #pragma unroll
                 for (int k = 0; k < NAX; ++k) {
                     // WA of the two sources: one 16-byte load (s0 is even)
-                    float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (live0) A = *reinterpret_cast<const float4*>(w + (long long)(p * NAX + k) * wa_pitch);
-                    if (!live1) { A.z = 0.f; A.w = 0.f; }
+                    const float4 A = *reinterpret_cast<const float4*>(w + (long long)(p * NAX + k) * wa_pitch);
                     // Z = WA * exp(-2 pi i phase) = WA * (c - i s)
                     re[k] = fmaf(A.x, c0, A.y * sn0);
                     im[k] = fmaf(A.y, c0, -A.x * sn0);
                     re[NAX + k] = fmaf(A.z, c1, A.w * sn1);
                     im[NAX + k] = fmaf(A.w, c1, -A.z * sn1);
                 }
-                const long long r = 2ll * (a * nfd + p);
-                put_row<PREC, NAX>(u, ulo, base + r * k_pitch + col, re, sc);
-                put_row<PREC, NAX>(u, ulo, base + (r + 1) * k_pitch + col, im, sc);
+                const long long r0 = 2ll * p * k_pitch;
+                put_row<PREC, NAX>(ur + r0, PREC != 0 ? lr + r0 : nullptr, re, sc);
+                put_row<PREC, NAX>(ur + r0 + k_pitch, PREC != 0 ? lr + r0 + k_pitch : nullptr, im, sc);
             }
-            if (step) {
-                F0 += Q0;
-                F1 += Q1;
-                // (c + i s) e^{2 pi i dF}
-                const float nc0 = fmaf(c0, rc0, -sn0 * rs0), nc1 = fmaf(c1, rc1, -sn1 * rs1);
-                sn0 = fmaf(sn0, rc0, c0 * rs0);
-                sn1 = fmaf(sn1, rc1, c1 * rs1);
-                c0 = nc0;
-                c1 = nc1;
-            }
-            base += slot_stride;
             w += wa_slot;
+            ur += slot_stride;
+            if (PREC != 0) lr += slot_stride;
+        };
+        if (step) {
+            // equally spaced channels: exact fixed-point phase every kAnchor
+            // channels, complex recurrence in between
+            const AntPhase p0 = load_phase(tab + a), pd = load_phase(tab + m.n_ant + a);
+            unsigned long long F0 = phase64(p0, S0, E0), F1 = phase64(p0, S1, E1);
+            const unsigned long long Q0 = phase64(pd, S0, E0), Q1 = phase64(pd, S1, E1);
+            float rc0, rs0, rc1, rs1;
+            cos_sin_turns(Q0, rc0, rs0);
+            cos_sin_turns(Q1, rc1, rs1);
+            for (int j0 = 0; j0 < g.n; j0 += kAnchor) {
+                float c0, sn0, c1, sn1;
+                cos_sin_turns(F0, c0, sn0);
+                cos_sin_turns(F1, c1, sn1);
+                F0 += Q0 * kAnchor;
+                F1 += Q1 * kAnchor;
+#pragma unroll
+                for (int jj = 0; jj < kAnchor; ++jj) {
+                    if (j0 + jj < g.n) emit(j0 + jj, c0, sn0, c1, sn1);
+                    if (jj + 1 < kAnchor) {  // (c + i s) e^{2 pi i dF}
+                        const float nc0 = fmaf(c0, rc0, -sn0 * rs0), nc1 = fmaf(c1, rc1, -sn1 * rs1);
+                        sn0 = fmaf(sn0, rc0, c0 * rs0);
+                        sn1 = fmaf(sn1, rc1, c1 * rs1);
+                        c0 = nc0;
+                        c1 = nc1;
+                    }
+                }
+            }
+        } else {
+            for (int j = 0; j < g.n; ++j) {
+                const AntPhase pj = load_phase(tab + (long long)(g.uniform ? 0 : j) * m.n_ant + a);
+                float c0, sn0, c1, sn1;
+                cos_sin_turns(phase64(pj, S0, E0), c0, sn0);
+                cos_sin_turns(phase64(pj, S1, E1), c1, sn1);
+                emit(j, c0, sn0, c1, sn1);
+            }
         }
     }
 }
@@ -258,8 +267,8 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
 // Grid-stride over the work items, so that the launch can be held to a fixed
 // number of resident blocks per SM (room left for a concurrent HERK).  The
 // FP16 scales of the item's instances go to shared memory once per item.
-template <int PREC, int NAX>
-__global__ void __launch_bounds__(128, 8)
+template <int PREC, int NAX, int NFD>
+__global__ void __launch_bounds__(128, NAX * NFD > 1 ? 6 : 8)
 k_zbuild(Model m, const Inst* __restrict__ inst, const ZGroup* __restrict__ groups, int g_first, LiveTables lt,
          const float2* __restrict__ wa, long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo,
          int rows, long long k_pitch, int ant_per_block, const AntPhase* __restrict__ aph, int n_phase, int nx,
@@ -275,8 +284,8 @@ k_zbuild(Model m, const Inst* __restrict__ inst, const ZGroup* __restrict__ grou
             for (int j = threadIdx.x; j < g.n; j += blockDim.x)
                 scale[j] = ldexpf(1.f, fp16_scale_exp(amax[g.slot0 + j]));
         __syncthreads();
-        zbuild_item<PREC, NAX>(m, inst, g, lt, wa, wa_pitch, scale, u, ulo, rows, k_pitch, ant_per_block,
-                               aph + (long long)bz * n_phase * m.n_ant, bx, by);
+        zbuild_item<PREC, NAX, NFD>(m, inst, g, lt, wa, wa_pitch, scale, u, ulo, rows, k_pitch, ant_per_block,
+                                    aph + (long long)bz * n_phase * m.n_ant, bx, by);
     }
 }
 
@@ -294,14 +303,17 @@ cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan
     const int nx = (int)((lt.pitch / 2 + 127) / 128), ny = (m.n_ant + apb - 1) / apb;
     const long long n_items = (long long)nx * ny * n_groups;
     const long long grid = max_blocks > 0 ? std::min<long long>(n_items, max_blocks) : n_items;
-#define MV_ZB(P, A) \
-    k_zbuild<P, A><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u, \
-                                                   d_u_lo, rows, k_pitch, apb, d_aph, n_phase, nx, ny, n_items)
+#define MV_ZB(P, A, F) \
+    k_zbuild<P, A, F><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u, \
+                                                      d_u_lo, rows, k_pitch, apb, d_aph, n_phase, nx, ny, n_items)
+#define MV_ZB_P(A, F) \
+    do { if (prec == 0) MV_ZB(0, A, F); else if (prec == 1) MV_ZB(1, A, F); else MV_ZB(2, A, F); } while (0)
     if (m.n_ax == 1) {
-        if (prec == 0) MV_ZB(0, 1); else if (prec == 1) MV_ZB(1, 1); else MV_ZB(2, 1);
+        if (m.n_feed == 1) MV_ZB_P(1, 1); else MV_ZB_P(1, 2);
     } else {
-        if (prec == 0) MV_ZB(0, 2); else if (prec == 1) MV_ZB(1, 2); else MV_ZB(2, 2);
+        if (m.n_feed == 1) MV_ZB_P(2, 1); else MV_ZB_P(2, 2);
     }
+#undef MV_ZB_P
 #undef MV_ZB
     *launches += 1;
     return cudaGetLastError();
