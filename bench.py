@@ -32,6 +32,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) per instance of k_herk_tc<128> on the 350-antenna,
+# 1e5-source workload in FP16x3: one ncu capture of 16 instances (2.4454 GB),
+# summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
+HERK_DRAM_BYTES_PER_INSTANCE = 2.4454e9 / 16
 METRIC = "vis/s (bl·chan·time) at 350 ant×1e5 src; split-prec TC vs FP32 @1e-5 rel err"
 UNIT = "vis/s"
 
@@ -284,8 +288,12 @@ def main():
         # triangle of the 2N x 2N real Gram matrix, for every instance
         flops_step = float(np.sum(3 * 2.0 * rows * (rows + 1) / 2 * K))
         achieved = flops_step * args.steps / (ms_h / 1e3) / 1e12
+        traffic = None
+        if (args.workload == "hera" and not args.small and args.precision == "fp16x3" and tuning
+                and tuning.get("tile_n") == 128):
+            traffic = HERK_DRAM_BYTES_PER_INSTANCE * n_instances(w, pairs) / max(n_h / args.steps, 1)
         roof = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
-                "frac": achieved / sustained, "traffic": None,
+                "frac": achieved / sustained, "traffic": traffic, "traffic_unit": "B per launch",
                 "kernel": "k_herk_tc", "launches": n_h, "avg_launch_ms": ms_h / max(n_h, 1),
                 "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
