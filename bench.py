@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
     ap.add_argument("--max-batch", type=int, default=0, help="instances per launch (mv_options.max_batch; 0 = auto)")
+    ap.add_argument("--no-fuse", action="store_true", help="Z build as its own launch (mv_options.fuse_zbuild = 0)")
     ap.add_argument("--herk-config", default=None, metavar="BN,SPLIT,FLUSH",
                     help="fix the tensor-core HERK tile width, split-K and flush interval (skips autotune)")
     return ap.parse_args()
@@ -236,7 +237,7 @@ def main():
         bn, split, flush = (int(x) for x in args.herk_config.split(","))
         hk = dict(herk_tile_n=bn, herk_split=split, herk_flush_kblocks=flush)
         args.no_autotune = True
-    sim = Simulator(local, overlap_batches=args.overlap, max_batch=args.max_batch, **hk)
+    sim = Simulator(local, overlap_batches=args.overlap, max_batch=args.max_batch, fuse_zbuild=not args.no_fuse, **hk)
     sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
     sim.set_beam(w.beam)
     sim.set_antennas(w.enu, None, w.lat)

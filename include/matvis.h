@@ -89,6 +89,12 @@ typedef struct {
     int overlap_batches;        /* 1: with two or more batches, build the Z matrices of one batch
                                    on a second stream while the HERK of the previous one runs (two
                                    workspace sets); 0 (default): one set, strictly in order */
+    int fuse_zbuild;            /* 1 (default): with two or more batches and a tensor-core
+                                   precision, the HERK launch of batch b also builds the Z matrices
+                                   of batch b + 1 on extra warps of every SM (two workspace sets,
+                                   128-column tiles; one feed and one axis, or two and two); 0: the
+                                   Z build runs as its own launch.  Takes precedence over
+                                   overlap_batches. */
 } mv_options;
 
 /* A tensor-core HERK configuration chosen by mv_autotune. */

@@ -50,7 +50,7 @@ class _Allocator(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("interp", ctypes.c_int), ("max_batch", ctypes.c_int), ("herk_flush_kblocks", ctypes.c_int),
                 ("herk_split", ctypes.c_int), ("allocator", _Allocator), ("herk_tile_n", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("overlap_batches", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("overlap_batches", ctypes.c_int), ("fuse_zbuild", ctypes.c_int)]
 
 
 class _MlpConfig(ctypes.Structure):
@@ -137,7 +137,7 @@ class Simulator:
 
     def __init__(self, device: int = 0, interp: str = "cubic", max_batch: int = 0, herk_flush_kblocks: int = 0,
                  herk_split: int = 0, herk_tile_n: int = 0, use_graph: bool = True, overlap_batches: bool = False,
-                 torch_allocator: bool = True):
+                 fuse_zbuild: bool = True, torch_allocator: bool = True):
         import torch  # device memory and streams
         self._torch = torch
         self._lib = load_library()
@@ -151,6 +151,7 @@ class Simulator:
         opt.herk_tile_n = herk_tile_n
         opt.use_graph = 1 if use_graph else 0
         opt.overlap_batches = 1 if overlap_batches else 0
+        opt.fuse_zbuild = 1 if fuse_zbuild else 0
         self._cb = None
         if torch_allocator:
             def _alloc(nbytes, dev, stream, user):

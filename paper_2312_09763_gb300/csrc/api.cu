@@ -293,7 +293,8 @@ long long slot_bytes_of(mv_ctx* c) {
     return 4ll * 2 * N * round_up((long long)m.n_ax * src, kKPad) + 8ll * ncomp * round_up(src, kKPad);
 }
 
-constexpr int kZGroup = 16;
+constexpr int kZGroup = 16;  // the fused Z build keeps a group's FP16 scales in 16 floats per warp
+static_assert(kZGroup <= 16, "Z groups of at most 16 instances");
 
 // Every (LST, channel) pair; batches are up to B channels of one LST.
 void plan_grid(mv_ctx* c, int n_t, const double* lst, int n_nu, const double* nu, Plan& P) {
@@ -336,7 +337,8 @@ void plan_pairs(mv_ctx* c, int n_pairs, const double* lst, const double* nu, Pla
 struct Prepared {
     int n_times = 0, n_chan = 0, n_inst = 0;
     int N = 0, rows = 0, bpt = 0, ncomp = 0, max_slots = 0, zprec = 0;
-    int nbuf = 1;  // workspace sets in use (2: Z side and HERK overlap)
+    int nbuf = 1;  // workspace sets in use (2: Z side and HERK overlap, or fused Z build)
+    bool fuse = false;  // the HERK of batch b builds the Z planes of batch b + 1
     int n_phase = 2;  // AntPhase entries per group
     const Plan* plan = nullptr;
     std::vector<int> h_nlive;  // live counts on the host (learned-beam calls only)
@@ -351,7 +353,8 @@ struct Prepared {
 // at least 32 k-blocks of the expected live count (half the catalogue).
 HerkCfg heuristic_cfg(mv_ctx* c, const Prepared& p) {
     HerkCfg h;
-    h.bn = c->opt.herk_tile_n == 128 || c->opt.herk_tile_n == 256 ? c->opt.herk_tile_n : (p.rows > 128 ? 256 : 128);
+    h.bn = c->opt.herk_tile_n == 128 || c->opt.herk_tile_n == 256 ? c->opt.herk_tile_n
+                                                                   : (p.fuse || p.rows <= 128 ? 128 : 256);
     h.flush = c->opt.herk_flush_kblocks > 0 ? c->opt.herk_flush_kblocks : 4;
     const int base = herk_tc_units(p.rows, p.max_slots, 1, h.bn);
     const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
@@ -449,7 +452,9 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if ((s = ensure(c, c->lidx, sizeof(int) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lazza, sizeof(float2) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
-    p.nbuf = (P.batches.size() > 1 && c->opt.overlap_batches) ? 2 : 1;
+    p.fuse = c->opt.fuse_zbuild && p.zprec != 0 && P.batches.size() > 1 && c->opt.herk_tile_n != 256 &&
+             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed);
+    p.nbuf = (P.batches.size() > 1 && (c->opt.overlap_batches || p.fuse)) ? 2 : 1;
     // antenna phase factors: per batch, groups x wavenumbers per group x antennas
     p.n_phase = 2;
     int max_groups = 1;
@@ -503,7 +508,7 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
 
 // HERK of one batch with configuration h.
 cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, const HerkCfg& h, int k,
-                         cudaStream_t st, long long* L) {
+                         cudaStream_t st, long long* L, const ZJob* zj = nullptr) {
     const Inst* d_inst = (const Inst*)c->inst.p;
     if (p.zprec == 0)
         return launch_herk_fp32(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const float*)c->u[k].p, p.rows,
@@ -511,11 +516,32 @@ cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, con
     return launch_herk_tc(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const __nv_bfloat16*)c->u[k].p,
                           (const __nv_bfloat16*)c->ulo[k].p, p.rows, p.k_pitch, p.max_slots, p.zprec == 2 ? 1 : 0,
                           (const float*)c->amax[k].p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
-                          (float*)c->partial.p, (int*)c->err.p, st, L);
+                          (float*)c->partial.p, (int*)c->err.p, zj, p.zprec, st, L);
 }
 
-// Beam evaluation and Z build of one batch.
-mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, cudaStream_t st, long long* L) {
+// The Z build of batch b into workspace set k, for the HERK of the batch before.
+ZJob make_zjob(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k) {
+    ZJob z{};
+    z.m = c->model;
+    z.inst = (const Inst*)c->inst.p;
+    z.groups = (const ZGroup*)c->groups.p;
+    z.g_first = b.g0;
+    z.n_groups = b.ng;
+    z.lt = p.lt;
+    z.wa = (const float2*)c->wa[k].p;
+    z.wa_pitch = p.pitch;
+    z.amax = (const float*)c->amax[k].p;
+    z.u = c->u[k].p;
+    z.ulo = c->ulo[k].p;
+    z.rows = p.rows;
+    z.k_pitch = p.k_pitch;
+    z.aph = (const AntPhase*)c->aph[k].p;
+    z.n_phase = p.n_phase;
+    return z;
+}
+
+// Beam evaluation of one batch into workspace set k.
+mv_status enqueue_wa(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, cudaStream_t st, long long* L) {
     mv_status s;
     const Model& m = c->model;
     const Inst* d_inst = (const Inst*)c->inst.p;
@@ -529,11 +555,29 @@ mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int 
         e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, p.lt,
                       (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
     tw.end();
-    if ((s = launched(e, "beam evaluation", st))) return s;
+    return launched(e, "beam evaluation", st);
+}
+
+// Antenna phase table of one batch into workspace set k (fused Z build).
+mv_status enqueue_ant_phase(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, cudaStream_t st,
+                            long long* L) {
     Timed tz(c, MV_KERNEL_ZBUILD, st);
-    e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, p.lt,
+    cudaError_t e = launch_ant_phase(c->model, (const Inst*)c->inst.p, (const Chan*)c->chan.p,
+                                     (const ZGroup*)c->groups.p, b.g0, b.ng, (AntPhase*)c->aph[k].p, p.n_phase, st, L);
+    tz.end();
+    return launched(e, "phase table", st);
+}
+
+// Beam evaluation and Z build of one batch.
+mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, cudaStream_t st, long long* L) {
+    mv_status s;
+    const Model& m = c->model;
+    const Inst* d_inst = (const Inst*)c->inst.p;
+    if ((s = enqueue_wa(c, p, b, k, st, L))) return s;
+    Timed tz(c, MV_KERNEL_ZBUILD, st);
+    cudaError_t e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, p.lt,
                       (const float2*)c->wa[k].p, p.pitch, (const float*)c->amax[k].p, c->u[k].p, c->ulo[k].p,
-                      p.zprec, p.rows, p.k_pitch, p.nbuf == 2 ? 4 * c->n_sms : 0, (AntPhase*)c->aph[k].p,
+                      p.zprec, p.rows, p.k_pitch, p.nbuf == 2 && !p.fuse ? 4 * c->n_sms : 0, (AntPhase*)c->aph[k].p,
                       p.n_phase, st, L);
     tz.end();
     return launched(e, "Z build", st);
@@ -562,6 +606,28 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
                                st, L);
         tb.end();
         if ((s = launched(e, "beam planes", st))) return s;
+    }
+    if (p.fuse) {
+        // batch 0 alone; then the HERK launch of batch b also builds the Z
+        // planes of batch b + 1 (its beam evaluation and phase table first)
+        // into the other workspace set
+        if ((s = enqueue_zside(c, p, P.batches[0], 0, st, L))) return s;
+        for (size_t i = 0; i < P.batches.size(); ++i) {
+            const int k = (int)(i & 1);
+            ZJob zj{};
+            const bool next = i + 1 < P.batches.size();
+            if (next) {
+                const auto& bn = P.batches[i + 1];
+                if ((s = enqueue_wa(c, p, bn, k ^ 1, st, L))) return s;
+                if ((s = enqueue_ant_phase(c, p, bn, k ^ 1, st, L))) return s;
+                zj = make_zjob(c, p, bn, k ^ 1);
+            }
+            Timed th(c, MV_KERNEL_HERK, st);
+            e = enqueue_herk(c, p, P.batches[i], h, k, st, L, next ? &zj : nullptr);
+            th.end();
+            if ((s = launched(e, "HERK tc", st))) return s;
+        }
+        return MV_OK;
     }
     if (p.nbuf == 1) {
         for (const auto& b : P.batches) {
@@ -599,7 +665,7 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
 // Key of a captured launch sequence: every value its kernel arguments depend on.
 std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, const HerkCfg& h) {
     std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch, p.nbuf,
-                                h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout, c->model_version};
+                                p.fuse, h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout, c->model_version};
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
                          &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
                          &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err,
@@ -620,6 +686,7 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     mv_status s = prepare(c, P, prec, V, V_on_device, st, p);
     if (s || p.n_inst == 0) return s;
     const HerkCfg h = chosen_cfg(c, p);
+    if (h.bn != 128) p.fuse = false;  // a tuned or forced 256-column tile runs the Z build on its own
     long long L = 0;
     // CUDA graph: the launch sequence is captured once per key (on the
     // context's own stream) and replayed on the caller's stream.  Kernel
@@ -687,7 +754,10 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
     const Plan::Batch b0 = P.batches[0];
     std::vector<HerkCfg> cands;
     const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
-    for (int bn : {128, 256})
+    // with the fused Z build the tile width is 128, and each trial carries the
+    // Z build of the first batch (into the second workspace set)
+    const std::vector<int> widths = p.fuse ? std::vector<int>{128} : std::vector<int>{128, 256};
+    for (int bn : widths)
         for (int split : {1, 2, 4, 8, 16, 32, 64})
             for (int flush : {4, 8}) {
                 if (split > 1 && est_kb / split < 8) continue;
@@ -712,15 +782,22 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
         if ((s = cuda_check(e, "beam planes"))) return s;
     }
     if ((s = enqueue_zside(c, p, b0, 0, st, &L))) return s;
+    ZJob zj{};
+    if (p.fuse) {
+        if ((s = enqueue_wa(c, p, b0, 1, st, &L))) return s;
+        if ((s = enqueue_ant_phase(c, p, b0, 1, st, &L))) return s;
+        zj = make_zjob(c, p, b0, 1);
+    }
+    const ZJob* zp = p.fuse ? &zj : nullptr;
     cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
     HerkCfg best;
     double best_ms = 1e300;
     for (const auto& h : cands) {
-        if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L), "trial HERK"))) return s;  // warm-up
+        if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L, zp), "trial HERK"))) return s;  // warm-up
         cudaEventRecord(e0, st);
         const int reps = 2;
         for (int r = 0; r < reps; ++r)
-            if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L), "trial HERK"))) return s;
+            if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L, zp), "trial HERK"))) return s;
         cudaEventRecord(e1, st);
         if ((s = cuda_check(cudaEventSynchronize(e1), "trial timing"))) return s;
         float ms = 0.f;
@@ -758,6 +835,7 @@ void mv_default_options(mv_options* opt) {
     std::memset(opt, 0, sizeof(*opt));
     opt->interp = MV_INTERP_CUBIC;
     opt->use_graph = 1;
+    opt->fuse_zbuild = 1;
 }
 
 const char* mv_last_error(void) { return g_err.c_str(); }

@@ -125,6 +125,30 @@ struct alignas(16) AntPhase {
 
 // Z build of a batch of groups: writes FP32 planes (prec 0) or BF16 hi/lo
 // planes (prec 1) of U into workspace slots.
+// Everything the Z build of one batch needs, for Z-build warps running
+// inside another kernel (the HERK of the previous batch).
+struct ZJob {
+    Model m;
+    const Inst* inst;
+    const ZGroup* groups;
+    int g_first, n_groups;
+    LiveTables lt;
+    const float2* wa;
+    long long wa_pitch;
+    const float* amax;
+    void* u;
+    void* ulo;
+    int rows;
+    long long k_pitch;
+    const AntPhase* aph;
+    int n_phase;
+};
+
+// Antenna phase table of a batch (the first half of launch_zbuild).
+cudaError_t launch_ant_phase(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
+                             int g_first, int n_groups, AntPhase* d_aph, int n_phase, cudaStream_t st,
+                             long long* launches);
+
 // d_aph: workspace for n_groups x n_phase x n_ant AntPhase entries, n_phase
 // >= max(2, largest group of the batch).
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
@@ -138,13 +162,19 @@ cudaError_t launch_herk_fp32(const Inst* d_inst, int inst0, int n_inst, LiveTabl
 // Persistent tensor-core HERK over n_inst instance slots: tiles 128 x bn
 // (bn = 128 or 256), the source axis split `split` ways (split > 1 writes
 // 128 x bn FP32 partial tiles, summed by a finalize kernel), TMEM flushed into
-// FP32 register sums every flush_kblocks k-blocks.  d_sched holds n_inst + 1
-// ints (instance order and the work counter).
+// FP32 sums every flush_kblocks k-blocks.  d_sched holds n_inst + 1 ints
+// (instance order and the work counter).  zj (optional, see
+// herk_tc_fusable): the Z build of the next batch, run by extra warps of the
+// same launch on every SM.
 cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                            const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows,
                            long long k_pitch, int n_slots, int fp16, const float* d_amax, float2* d_v,
                            int N, int flush_kblocks, int split, int bn, int n_ctas, int* d_sched,
-                           float* d_partial, int* d_err, cudaStream_t st, long long* launches);
+                           float* d_partial, int* d_err, const ZJob* zj, int zprec, cudaStream_t st,
+                           long long* launches);
+// Whether the HERK can carry the Z build (tile width 128; one feed and one
+// axis, or two and two; BF16x3 or FP16x3).
+bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed);
 // Set kernel attributes of the tensor-core HERK (once per process, outside
 // any stream capture).
 cudaError_t herk_tc_init();

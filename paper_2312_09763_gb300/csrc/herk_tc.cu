@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include "common.cuh"
+#include "zcore.cuh"
 
 namespace mv {
 namespace {
@@ -125,6 +126,19 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ------------------------------------------------------------------ tiling
 // Lower-triangle tiles of G: row tile ti (BM rows), column tile tj (BN rows of
 // U) with tj <= ti BM / BN; tile index runs over (ti, tj) in row order.
@@ -147,18 +161,23 @@ int n_tiles_for(int rows) {
     return n;
 }
 
-// Kernel-wide configuration for a tile width BN (128 or 256 columns).
-template <int BN>
+// Kernel-wide configuration for a tile width BN (128 or 256 columns); FZ:
+// the kernel also runs the Z build of the next batch on Z_WARPS extra warps,
+// and keeps the epilogue's running sums in TMEM (columns [2 BN, 3 BN)) so
+// that its registers are free for them.
+template <int BN, bool FZ = false>
 struct Cfg {
+    static_assert(!FZ || BN == 128, "the fused Z build runs with 128-column tiles");
     static constexpr int A_BYTES = BM * BK * 2;                    // 16 KB per plane
     static constexpr int B_BYTES = BN * BK * 2;                    // 16 or 32 KB per plane
     static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 64 or 96 KB
     static constexpr int STAGES = BN == 256 ? 2 : 3;               // 192 KB of ring either way
-    static constexpr int TMEM_COLS = BN == 256 ? 512 : 256;        // two accumulator buffers
+    static constexpr int TMEM_COLS = (BN == 256 || FZ) ? 512 : 256;  // two accumulators (+ running sums)
     static constexpr int EPI_WARPS = BN / 32;                      // 128 columns per epilogue warp
-    static constexpr int THREADS = (2 + EPI_WARPS) * 32;
+    static constexpr int Z_WARPS = FZ ? 10 : 0;
+    static constexpr int THREADS = (2 + EPI_WARPS + Z_WARPS) * 32;
     static constexpr int QDEPTH = 4;                               // unit-id queue depth
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512 + Z_WARPS * 16 * 4;
 };
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16 (format 1) or FP16
@@ -216,14 +235,21 @@ __global__ void k_slot_order(const Inst* __restrict__ inst, int inst0, int n_slo
 // MMA warp and the epilogue warps through a shared-memory queue; the ring
 // and the two TMEM buffers carry across units, so the MMA warp starts the
 // next unit while the epilogue writes out the last one.
-template <int BN>
-__global__ void __launch_bounds__(Cfg<BN>::THREADS, 1)
+//
+// With ZP != 0 the kernel also carries Z_WARPS warps that build the U planes
+// of the next batch (zj, written to the other workspace set) with the Z-build
+// core (precision ZP, ZA axes, ZF feeds) while the tensor cores work on this
+// batch: the two use different units (integer/FP32 pipes and HBM writes vs
+// the tensor pipe), and nothing in one waits on the other.
+template <int BN, int ZP = 0, int ZA = 1, int ZF = 1>
+__global__ void __launch_bounds__(Cfg<BN, (ZP != 0)>::THREADS, 1)
 k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           const Inst* __restrict__ inst, int inst0, LiveTables lt, int n_ax, uint32_t idesc, int fp16,
           const float* __restrict__ amax, float2* __restrict__ V, int N, int n_tiles, int n_units, int S,
           int flush, const int* __restrict__ order, int* __restrict__ counter, float* __restrict__ partial,
-          int* __restrict__ err) {
-    using C = Cfg<BN>;
+          int* __restrict__ err, const __grid_constant__ ZJob zj) {
+    constexpr bool FZ = ZP != 0;
+    using C = Cfg<BN, FZ>;
     constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
     constexpr int QD = C::QDEPTH;
     extern __shared__ uint8_t smem_raw[];
@@ -233,6 +259,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     int* qslot = reinterpret_cast<int*>(bars + 2 * STAGES + 4 + 2 * QD);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(qslot + QD);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* zsw = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 512);  // 16 floats per Z warp
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     auto full = [&](int s) { return smem_u32(&bars[s]); };
@@ -336,7 +363,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 if (!ok) break;
             }
         }
-    } else {
+    } else if (!FZ || warp < 2 + C::EPI_WARPS) {
         // epilogue warps: TMEM lane quadrant q4, 128-column group h
         const int ew = warp - 2;
         const int q4 = warp & 3, h = ew >> 2;
@@ -349,37 +376,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             if (lane == 0) mbar_arrive(qempty(qi));
             if (u < 0) break;
             const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
-            float run[128];
-#pragma unroll
-            for (int i = 0; i < 128; ++i) run[i] = 0.f;
-            bool ok = true;
-            for (int kc = w.kb0; kc < w.kb1; kc += flush, ++cg) {
-                const int buf = cg & 1;
-                const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
-                if (!wait_bounded(tfull(buf), ph, abort_flag, err)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t ta = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * BN + h * 128);
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    uint32_t r[32];
-                    tmem_ld32(ta + g * 32, r);
-                    tmem_wait_ld(r);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) run[g * 32 + i] += __uint_as_float(r[i]);
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty(buf));
-            }
-            if (!ok || *abort_flag) break;
             const int rl = q4 * 32 + lane;  // row of the tile held by this thread
-            if (S > 1) {
-                // raw partial tile, column-major [BN][128] (coalesced along rows)
-                float* p = partial + (long long)w.part * (BN * BM) + (long long)h * 128 * BM + rl;
-#pragma unroll
-                for (int j = 0; j < 128; ++j) p[j * BM] = run[j];
-                continue;
-            }
             const int r = w.ti * BM + rl;
             const int a = r >> 1;
             const bool even = (lane & 1) == 0;
@@ -387,23 +384,116 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             const int c0 = w.tj * BN + h * 128;
             // undo the FP16 scaling 2^e of both operands: two exact power-of-two steps
             const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[w.slot])) : 1.f;
+            // one 32-column chunk of the tile (columns c0 + 32 g ...): raw partial
+            // tile, or the 2 x 2 blocks of G folded into V
+            auto write_chunk = [&](int g, const float* x) {
+                if (S > 1) {
+                    // column-major [BN][128] (coalesced along rows)
+                    float* p = partial + (long long)w.part * (BN * BM) + (long long)(h * 128 + g * 32) * BM + rl;
 #pragma unroll
-            for (int jj = 0; jj < 64; ++jj) {
-                const float x0 = run[2 * jj], x1 = run[2 * jj + 1];
-                const float y0 = __shfl_xor_sync(0xffffffffu, x0, 1);
-                const float y1 = __shfl_xor_sync(0xffffffffu, x1, 1);
-                const float g00 = even ? x0 : y0, g01 = even ? x1 : y1;
-                const float g10 = even ? y0 : x0, g11 = even ? y1 : x1;
-                const int b = (c0 + 2 * jj) >> 1;
-                if ((jj & 1) == (lane & 1) && a < N && b < N && a >= b) {
-                    const float re = ((g00 + g11) * unscale) * unscale;
-                    // autocorrelations are real: the tensor core rounds the two
-                    // symmetric entries of G separately, so drop that residue
-                    const float im = a == b ? 0.f : ((g10 - g01) * unscale) * unscale;
-                    Vb[(long long)a * N + b] = make_float2(re, im);
-                    if (a != b) Vb[(long long)b * N + a] = make_float2(re, -im);
+                    for (int j = 0; j < 32; ++j) p[j * BM] = x[j];
+                    return;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const float x0 = x[2 * jj], x1 = x[2 * jj + 1];
+                    const float y0 = __shfl_xor_sync(0xffffffffu, x0, 1);
+                    const float y1 = __shfl_xor_sync(0xffffffffu, x1, 1);
+                    const float g00 = even ? x0 : y0, g01 = even ? x1 : y1;
+                    const float g10 = even ? y0 : x0, g11 = even ? y1 : x1;
+                    const int b = (c0 + g * 32 + 2 * jj) >> 1;
+                    if ((jj & 1) == (lane & 1) && a < N && b < N && a >= b) {
+                        const float re = ((g00 + g11) * unscale) * unscale;
+                        // autocorrelations are real: the tensor core rounds the two
+                        // symmetric entries of G separately, so drop that residue
+                        const float im = a == b ? 0.f : ((g10 - g01) * unscale) * unscale;
+                        Vb[(long long)a * N + b] = make_float2(re, im);
+                        if (a != b) Vb[(long long)b * N + a] = make_float2(re, -im);
+                    }
+                }
+            };
+            bool ok = true;
+            if constexpr (!FZ) {
+                // running sums in registers
+                float run[128];
+#pragma unroll
+                for (int i = 0; i < 128; ++i) run[i] = 0.f;
+                for (int kc = w.kb0; kc < w.kb1; kc += flush, ++cg) {
+                    const int buf = cg & 1;
+                    const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
+                    if (!wait_bounded(tfull(buf), ph, abort_flag, err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ta = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * BN + h * 128);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t rr[32];
+                        tmem_ld32(ta + g * 32, rr);
+                        tmem_wait_ld(rr);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) run[g * 32 + i] += __uint_as_float(rr[i]);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty(buf));
+                }
+                if (!ok || *abort_flag) break;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) write_chunk(g, run + g * 32);
+            } else {
+                // running sums in TMEM columns [2 BN, 3 BN) of this warp's lanes
+                const uint32_t tl = tmem_base + ((uint32_t)(q4 * 32) << 16);
+                const uint32_t trun = tl + 2 * BN;
+                bool any = false;
+                for (int kc = w.kb0; kc < w.kb1; kc += flush, ++cg) {
+                    const int buf = cg & 1;
+                    const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
+                    if (!wait_bounded(tfull(buf), ph, abort_flag, err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t ta = tl + (uint32_t)(buf * BN);
+#pragma unroll 1
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t acc[32];
+                        tmem_ld32(ta + g * 32, acc);
+                        tmem_wait_ld(acc);
+                        if (any) {
+                            uint32_t sum[32];
+                            tmem_ld32(trun + g * 32, sum);
+                            tmem_wait_ld(sum);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                acc[i] = __float_as_uint(__uint_as_float(sum[i]) + __uint_as_float(acc[i]));
+                        }
+                        tmem_st32(trun + g * 32, acc);
+                    }
+                    tmem_wait_st();
+                    any = true;
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty(buf));
+                }
+                if (!ok || *abort_flag) break;
+#pragma unroll 1
+                for (int g = 0; g < 4; ++g) {
+                    float x[32];
+                    if (any) {
+                        uint32_t sum[32];
+                        tmem_ld32(trun + g * 32, sum);
+                        tmem_wait_ld(sum);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(sum[i]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) x[i] = 0.f;
+                    }
+                    write_chunk(g, x);
                 }
             }
+        }
+    } else if constexpr (FZ) {
+        // Z build of the next batch
+        if (zj.n_groups > 0) {
+            const int zw = warp - 2 - C::EPI_WARPS;
+            zcore::zjob_warp<ZP, ZA, ZF>(zj, blockIdx.x * C::Z_WARPS + zw, gridDim.x * C::Z_WARPS, zsw + zw * 16);
         }
     }
     __syncthreads();
@@ -484,12 +574,12 @@ bool make_map(CUtensorMap* map, const void* base, long long k_pitch, int rows, i
     return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int ZP = 0, int ZA = 1, int ZF = 1>
 cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* d_inst, int inst0, int n_inst,
                       LiveTables lt, int n_ax, int fp16, const float* d_amax, float2* d_v, int N, int rows,
                       int flush, int split, int n_ctas, int* d_sched, float* d_partial, int* d_err,
-                      cudaStream_t st, long long* launches) {
-    using C = Cfg<BN>;
+                      const ZJob* zj, cudaStream_t st, long long* launches) {
+    using C = Cfg<BN, (ZP != 0)>;
     const int n_tiles = n_tiles_for<BN>(rows);
     const int n_units = n_tiles * n_inst * split;
     int* order = d_sched;            // [n_inst]
@@ -497,10 +587,14 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     k_slot_order<<<1, 256, 0, st>>>(d_inst, inst0, n_inst, lt, order);
-    const int grid = std::max(1, std::min(n_ctas, n_units));
-    k_herk_tc<BN><<<grid, C::THREADS, C::SMEM, st>>>(mh, ml, d_inst, inst0, lt, n_ax, idesc_for(fp16 != 0, BN), fp16,
-                                                     d_amax, d_v, N, n_tiles, n_units, split, flush, order, counter,
-                                                     d_partial, d_err);
+    // with a fused Z build every SM takes part (CTAs without HERK units build Z)
+    const int grid = ZP != 0 ? std::max(1, n_ctas) : std::max(1, std::min(n_ctas, n_units));
+    ZJob z{};
+    if (zj) z = *zj;
+    k_herk_tc<BN, ZP, ZA, ZF><<<grid, C::THREADS, C::SMEM, st>>>(mh, ml, d_inst, inst0, lt, n_ax,
+                                                                 idesc_for(fp16 != 0, BN), fp16, d_amax, d_v, N,
+                                                                 n_tiles, n_units, split, flush, order, counter,
+                                                                 d_partial, d_err, z);
     *launches += 2;
     if (split > 1) {
         e = cudaGetLastError();
@@ -517,10 +611,23 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
 bool herk_tc_available() { return get_encode() != nullptr; }
 
 cudaError_t herk_tc_init() {
+    const int fz = Cfg<128, true>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_herk_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<256>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<128, 2, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<128, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
     return e;
+}
+
+bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed) {
+    return bn == 128 && (zprec == 1 || zprec == 2) && n_ax == n_feed && (n_ax == 1 || n_ax == 2);
 }
 
 int herk_tc_units(int rows, int n_slots, int split, int bn) {
@@ -530,19 +637,29 @@ int herk_tc_units(int rows, int n_slots, int split, int bn) {
 cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,
                            const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows, long long k_pitch,
                            int n_slots, int fp16, const float* d_amax, float2* d_v, int N, int flush, int split,
-                           int bn, int n_ctas, int* d_sched, float* d_partial, int* d_err, cudaStream_t st,
-                           long long* launches) {
+                           int bn, int n_ctas, int* d_sched, float* d_partial, int* d_err, const ZJob* zj,
+                           int zprec, cudaStream_t st, long long* launches) {
     CUtensorMap mh, ml;
     if (!make_map(&mh, d_hi, k_pitch, rows, n_slots, fp16) || !make_map(&ml, d_lo, k_pitch, rows, n_slots, fp16))
         return cudaErrorInvalidValue;
     if (flush < 1) flush = 4;
     if (split < 1) split = 1;
     if ((split > 1 && !d_partial) || !d_sched || n_inst > 4096) return cudaErrorInvalidValue;
-    if (bn == 128)
-        return launch_bn<128>(mh, ml, d_inst, inst0, n_inst, lt, n_ax, fp16, d_amax, d_v, N, rows, flush, split, n_ctas,
-                              d_sched, d_partial, d_err, st, launches);
-    return launch_bn<256>(mh, ml, d_inst, inst0, n_inst, lt, n_ax, fp16, d_amax, d_v, N, rows, flush, split, n_ctas,
-                          d_sched, d_partial, d_err, st, launches);
+#define MV_LB(BN_, ZP_, ZA_, ZF_)                                                                                \
+    return launch_bn<BN_, ZP_, ZA_, ZF_>(mh, ml, d_inst, inst0, n_inst, lt, n_ax, fp16, d_amax, d_v, N, rows, flush, \
+                                         split, n_ctas, d_sched, d_partial, d_err, zj, st, launches)
+    if (zj) {
+        if (!herk_tc_fusable(bn, zprec, zj->m.n_ax, zj->m.n_feed)) return cudaErrorInvalidValue;
+        if (zj->m.n_ax == 1) {
+            if (zprec == 1) MV_LB(128, 1, 1, 1);
+            MV_LB(128, 2, 1, 1);
+        }
+        if (zprec == 1) MV_LB(128, 1, 2, 2);
+        MV_LB(128, 2, 2, 2);
+    }
+    if (bn == 128) MV_LB(128, 0, 1, 1);
+    MV_LB(256, 0, 1, 1);
+#undef MV_LB
 }
 
 }  // namespace mv

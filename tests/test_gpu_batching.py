@@ -59,13 +59,37 @@ def test_graph_replay_matches_uncaptured_run():
 def test_overlapped_batches_match_serial(prec):
     # batches of 2 channels: the Z side of batch b+1 overlaps the HERK of batch b
     w = synth.hera_like(n_ant=90, n_src=12_000, n_chan=6, n_times=2, n_za=46, n_az=120)
-    a = simulator(w, max_batch=2).simulate(w.lsts, w.freqs, prec).cpu().numpy()
+    a = simulator(w, max_batch=2, fuse_zbuild=False).simulate(w.lsts, w.freqs, prec).cpu().numpy()
     for use_graph in (False, True):
-        sim = simulator(w, max_batch=2, use_graph=use_graph, overlap_batches=True)
+        sim = simulator(w, max_batch=2, use_graph=use_graph, overlap_batches=True, fuse_zbuild=False)
         for _ in range(2):
             assert np.array_equal(sim.simulate(w.lsts, w.freqs, prec).cpu().numpy(), a)
     P = oracle_problem(w)
     assert rel_err(a[1, 4], oracle.vis(P, w.lsts[1], w.freqs[4])) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("beam", ["scalar", "jones_full_stokes"])
+@pytest.mark.parametrize("split", [1, 3])
+def test_fused_zbuild_matches_separate(prec, beam, split):
+    # batches of 2 channels: the HERK launch of batch b builds the Z planes of
+    # batch b + 1; the same arithmetic as the separate Z-build launch, so the
+    # result is bit-identical (the epilogue's TMEM running sums add in the same
+    # order as the register sums)
+    if beam == "scalar":
+        w = synth.hera_like(n_ant=90, n_src=12_000, n_chan=6, n_times=2, n_za=46, n_az=120)
+    else:
+        w = synth.polarised_diffuse(n_ant=40, nside=16, n_chan=4, n_times=2, n_za=31, n_az=72, lmax=40,
+                                    full_stokes=True)
+    kw = dict(max_batch=2, herk_tile_n=128, herk_split=split)
+    a = simulator(w, fuse_zbuild=False, **kw).simulate(w.lsts, w.freqs, prec).cpu().numpy()
+    for use_graph in (False, True):
+        sim = simulator(w, use_graph=use_graph, **kw)
+        for _ in range(2):
+            assert np.array_equal(sim.simulate(w.lsts, w.freqs, prec).cpu().numpy(), a)
+    P = oracle_problem(w)
+    it, ic = 1, len(w.freqs) - 1
+    assert rel_err(a[it, ic], oracle.vis(P, w.lsts[it], w.freqs[ic])) <= TOL[prec]
 
 
 @pytest.mark.parametrize("tile_n,split,flush",[(128, 1, 4), (128, 8, 1), (256, 1, 8), (256, 5, 2), (256, 64, 4)])
