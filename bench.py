@@ -50,9 +50,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
-    ap.add_argument("--workload", default="hera", choices=["hera", "diffuse", "uneven"],
+    ap.add_argument("--workload", default="hera", choices=["hera", "diffuse", "uneven", "learned"],
                     help="hera: 350 ant x 1e5 src x 64 ch x 60 t (default); diffuse: 350 ant x 196,608 HEALPix "
-                         "pixels x 32 ch x 120 t, 2x2 Jones beam; uneven: 256 (LST, nu) pairs, one call")
+                         "pixels x 32 ch x 120 t, 2x2 Jones beam; uneven: 256 (LST, nu) pairs, one call; "
+                         "learned: one LST x 8 channels of the learned-beam workload (350 per-antenna Jones "
+                         "beams replaced by the trained surrogate)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
     ap.add_argument("--max-batch", type=int, default=0, help="instances per launch (mv_options.max_batch; 0 = auto)")
@@ -103,6 +105,13 @@ def workload(args):
         return synth.polarised_diffuse()
     if args.workload == "uneven":
         return synth.batched_uneven()
+    if args.workload == "learned":
+        # one LST x 8 channels (146.5-153.5 MHz) of the learned-beam workload;
+        # per-antenna grids over 143-157 MHz cover the cubic stencil
+        w = synth.learned_beam(n_chan=8, n_times=1, nu_lo=143e6, nu_hi=157e6)
+        w.freqs = 146.5e6 + np.arange(8) * 1e6
+        w.name = w.name.replace("x 8 ch x 1 t", "x 8 ch (146.5-153.5 MHz) x 1 t")
+        return w
     if args.small:  # profiling captures: 16 channels of 1 LST of the full sky (~2.2 GB of Z planes)
         w = synth.hera_like(n_ant=350, n_src=100_000, n_chan=16, n_times=1)
         w.freqs = synth.hera_like().freqs[24:40]
@@ -240,14 +249,34 @@ def main():
     sim = Simulator(local, overlap_batches=args.overlap, max_batch=args.max_batch, fuse_zbuild=not args.no_fuse, **hk)
     sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
     sim.set_beam(w.beam)
-    sim.set_antennas(w.enu, None, w.lat)
+    sim.set_antennas(w.enu, w.beam_idx, w.lat)
+    learned = None
+    if args.workload == "learned":
+        # no host round trip of the 5.5 GB of per-antenna grids each step, and
+        # no CPU baseline over 350 per-antenna beams: device-side numbers only
+        args.no_e2e = args.no_cpu_baseline = True
+        # the surrogate of the 350 gridded beams: 1221 Adam steps of 8192 samples (1e7 samples)
+        sim.surrogate_create()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        l0, l1 = sim.surrogate_train(steps=1221, batch=8192, lr0=2e-3, lr1=1e-5, seed=1)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        # the gridded path's V on this sample, for the surrogate's modelling error
+        tuning = None if args.precision == "fp32" or args.no_autotune else sim.autotune(w.lsts, w.freqs, args.precision)
+        args.no_autotune = True
+        Vg = sim.simulate(w.lsts, w.freqs, args.precision)
+        sim.set_beam_surrogate(True)
+        learned = {"train_samples": 1221 * 8192, "train_s": t_train, "train_samples_per_s": 1221 * 8192 / t_train,
+                   "loss_first": l0, "loss_last": l1}
     N = w.n_ant
     nf, nax = sim.n_feed, sim._n_ax()
     shape = (len(w.lsts), N * nf, N * nf) if pairs else (len(w.lsts), len(w.freqs), N * nf, N * nf)
     V = torch.empty(shape, dtype=torch.complex64, device=f"cuda:{local}")
     run = sim.simulate_pairs if pairs else sim.simulate
     stream = torch.cuda.current_stream()
-    tuning = None
+    if learned is None:
+        tuning = None
     if args.precision != "fp32" and not args.no_autotune:
         tuning = sim.autotune(w.lsts, w.freqs, args.precision, pairs=pairs)
     for _ in range(args.warmup):
@@ -297,6 +326,23 @@ def main():
                 "frac": achieved / sustained, "traffic": traffic, "traffic_unit": "B per launch",
                 "kernel": "k_herk_tc", "launches": n_h, "avg_launch_ms": ms_h / max(n_h, 1),
                 "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)"}
+    if learned is not None:
+        # the surrogate's forward pass dominates: 2 x multiply-adds per row of
+        # the network, one row per (antenna beam, live source) of each instance
+        _, _, lay = sim.surrogate_params()
+        F, E, H, D = (sim._mlp[k] for k in ("n_freq", "emb_dim", "width", "depth"))
+        d0p = int(lay[-1])
+        macs = d0p * H + (D - 1) * H * H + H * 8
+        rows_step = float(np.sum(live.astype(np.float64) * w.n_ant))
+        n_b, ms_b = prof["beam"]
+        mlp_tf = 2.0 * macs * rows_step * args.steps / (ms_b / 1e3) / 1e12
+        err = float((V - Vg).abs().max() / Vg.abs().max())
+        learned.update({"network_rows_per_step": rows_step, "flop_per_row": 2 * macs,
+                        "surrogate_vs_grid_rel_err": err})
+        roof = {"bound": "tensor", "achieved": mlp_tf, "peak": sustained, "unit": "TFLOP/s",
+                "frac": mlp_tf / sustained, "traffic": None, "kernel": "learned-beam forward (k_gemm, mma.sync)",
+                "launches": n_b, "avg_launch_ms": ms_b / max(n_b, 1),
+                "peak_source": f"{src} bf16 sustained (kernels timed inside a long step)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -304,7 +350,7 @@ def main():
                        "live_sources_mean": float(live.mean()), "precision": args.precision,
                        "l2": "inputs larger than L2: Z planes of one batch ~4.5 GB, re-streamed each step",
                        "parallelism": f"{world} replica(s), instances simulated independently"},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk, "herk_tuning": tuning,
+            "gpu_launches": launches, "roofline": roof, "clocks": clk, "herk_tuning": tuning, "learned_beam": learned,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
     if rank == 0 and not args.no_e2e:

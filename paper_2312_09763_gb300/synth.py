@@ -248,15 +248,16 @@ def dipole_feed_offset_grids(n_ant: int, nu_grid: np.ndarray, n_za: int, n_az: i
 
 
 def learned_beam(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times: int = 60, n_za: int = 91,
-                 n_az: int = 360, dnu: float = 1e6) -> Workload:
+                 n_az: int = 360, dnu: float = 1e6, nu_lo: float = 98e6, nu_hi: float = 202e6) -> Workload:
     """Workload 4: the HERA-like array and sky of workload 1 with one beam per
     antenna (dipole_feed_offset_grids on a 1 deg x 1 deg x 1 MHz grid over
-    98-202 MHz), the setting where a learned surrogate replaces n_ant grids."""
+    98-202 MHz, or [nu_lo, nu_hi] for samples of it), the setting where a
+    learned surrogate replaces n_ant grids."""
     w = hera_like(n_ant=n_ant, n_src=n_src, n_chan=n_chan, n_times=n_times, n_za=31, n_az=60)
-    n_nu = int(round(104e6 / dnu)) + 1
-    nu_grid = 98e6 + np.arange(n_nu) * dnu
+    n_nu = int(round((nu_hi - nu_lo) / dnu)) + 1
+    nu_grid = nu_lo + np.arange(n_nu) * dnu
     grids = dipole_feed_offset_grids(n_ant, nu_grid, n_za, n_az, rng(4, "feed_offsets"))
-    w.beam = ("grid", grids, 98e6, dnu, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
+    w.beam = ("grid", grids, nu_lo, dnu, (np.pi / 2) / (n_za - 1), 2 * np.pi / n_az, "cubic")
     w.beam_idx = np.arange(n_ant, dtype=np.int32)
     w.name = (f"learned_beam: {n_ant} ant (one Jones beam each) x {n_src} src x {n_chan} ch x {n_times} t, "
               f"Fourier-feature MLP beam")
