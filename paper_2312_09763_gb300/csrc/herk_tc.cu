@@ -23,6 +23,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <type_traits>
 #include "common.cuh"
 #include "zcore.cuh"
 
@@ -137,6 +138,30 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
         "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+          "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+        :
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ tiling
@@ -161,12 +186,13 @@ int n_tiles_for(int rows) {
     return n;
 }
 
-// Kernel-wide configuration for a tile width BN (128 or 256 columns); FZ:
-// the kernel also runs the Z build of the next batch on Z_WARPS extra warps,
-// and keeps the epilogue's running sums in TMEM (columns [2 BN, 3 BN)) so
-// that its registers are free for them.
-template <int BN, bool FZ = false>
+// Kernel-wide configuration for a tile width BN (128 or 256 columns); ZW > 0:
+// the kernel also runs the Z build of the next batch on ZW extra warps, and
+// keeps the epilogue's running sums in TMEM (columns [2 BN, 3 BN)) so that
+// registers are free for them (the whole block fits 64 K registers).
+template <int BN, int ZW = 0>
 struct Cfg {
+    static constexpr bool FZ = ZW > 0;
     static_assert(!FZ || BN == 128, "the fused Z build runs with 128-column tiles");
     static constexpr int A_BYTES = BM * BK * 2;                    // 16 KB per plane
     static constexpr int B_BYTES = BN * BK * 2;                    // 16 or 32 KB per plane
@@ -174,11 +200,16 @@ struct Cfg {
     static constexpr int STAGES = BN == 256 ? 2 : 3;               // 192 KB of ring either way
     static constexpr int TMEM_COLS = (BN == 256 || FZ) ? 512 : 256;  // two accumulators (+ running sums)
     static constexpr int EPI_WARPS = BN / 32;                      // 128 columns per epilogue warp
-    static constexpr int Z_WARPS = FZ ? 10 : 0;
+    static constexpr int Z_WARPS = ZW;
     static constexpr int THREADS = (2 + EPI_WARPS + Z_WARPS) * 32;
     static constexpr int QDEPTH = 4;                               // unit-id queue depth
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512 + Z_WARPS * 16 * 4;
 };
+
+// Z-build warps of a fused HERK: as many as 64 K registers allow with the
+// Z core's register use (one-component beams: 64 registers, 1024 threads;
+// Jones beams: 80 registers, 768 threads).
+__host__ __device__ constexpr int zwarps(int zp, int za, int zf) { return zp == 0 ? 0 : (za * zf == 1 ? 22 : 14); }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16 (format 1) or FP16
 // (format 0), both K-major, N = BN, M = 128.
@@ -242,14 +273,14 @@ __global__ void k_slot_order(const Inst* __restrict__ inst, int inst0, int n_slo
 // batch: the two use different units (integer/FP32 pipes and HBM writes vs
 // the tensor pipe), and nothing in one waits on the other.
 template <int BN, int ZP = 0, int ZA = 1, int ZF = 1>
-__global__ void __launch_bounds__(Cfg<BN, (ZP != 0)>::THREADS, 1)
+__global__ void __launch_bounds__(Cfg<BN, zwarps(ZP, ZA, ZF)>::THREADS, 1)
 k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           const Inst* __restrict__ inst, int inst0, LiveTables lt, int n_ax, uint32_t idesc, int fp16,
           const float* __restrict__ amax, float2* __restrict__ V, int N, int n_tiles, int n_units, int S,
           int flush, const int* __restrict__ order, int* __restrict__ counter, float* __restrict__ partial,
           int* __restrict__ err, const __grid_constant__ ZJob zj) {
     constexpr bool FZ = ZP != 0;
-    using C = Cfg<BN, FZ>;
+    using C = Cfg<BN, zwarps(ZP, ZA, ZF)>;
     constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
     constexpr int QD = C::QDEPTH;
     extern __shared__ uint8_t smem_raw[];
@@ -386,22 +417,23 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[w.slot])) : 1.f;
             // one 32-column chunk of the tile (columns c0 + 32 g ...): raw partial
             // tile, or the 2 x 2 blocks of G folded into V
-            auto write_chunk = [&](int g, const float* x) {
+            auto write_chunk = [&](auto ncol, int g, const float* x) {
+                constexpr int NCOL = decltype(ncol)::value;
                 if (S > 1) {
                     // column-major [BN][128] (coalesced along rows)
-                    float* p = partial + (long long)w.part * (BN * BM) + (long long)(h * 128 + g * 32) * BM + rl;
+                    float* p = partial + (long long)w.part * (BN * BM) + (long long)(h * 128 + g * NCOL) * BM + rl;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) p[j * BM] = x[j];
+                    for (int j = 0; j < NCOL; ++j) p[j * BM] = x[j];
                     return;
                 }
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
+                for (int jj = 0; jj < NCOL / 2; ++jj) {
                     const float x0 = x[2 * jj], x1 = x[2 * jj + 1];
                     const float y0 = __shfl_xor_sync(0xffffffffu, x0, 1);
                     const float y1 = __shfl_xor_sync(0xffffffffu, x1, 1);
                     const float g00 = even ? x0 : y0, g01 = even ? x1 : y1;
                     const float g10 = even ? y0 : x0, g11 = even ? y1 : x1;
-                    const int b = (c0 + g * 32 + 2 * jj) >> 1;
+                    const int b = (c0 + g * NCOL + 2 * jj) >> 1;
                     if ((jj & 1) == (lane & 1) && a < N && b < N && a >= b) {
                         const float re = ((g00 + g11) * unscale) * unscale;
                         // autocorrelations are real: the tensor core rounds the two
@@ -438,9 +470,10 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 }
                 if (!ok || *abort_flag) break;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) write_chunk(g, run + g * 32);
+                for (int g = 0; g < 4; ++g) write_chunk(std::integral_constant<int, 32>{}, g, run + g * 32);
             } else {
-                // running sums in TMEM columns [2 BN, 3 BN) of this warp's lanes
+                // running sums in TMEM columns [2 BN, 3 BN) of this warp's lanes,
+                // 16 columns at a time
                 const uint32_t tl = tmem_base + ((uint32_t)(q4 * 32) << 16);
                 const uint32_t trun = tl + 2 * BN;
                 bool any = false;
@@ -451,19 +484,19 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                     tc_fence_after();
                     const uint32_t ta = tl + (uint32_t)(buf * BN);
 #pragma unroll 1
-                    for (int g = 0; g < 4; ++g) {
-                        uint32_t acc[32];
-                        tmem_ld32(ta + g * 32, acc);
-                        tmem_wait_ld(acc);
+                    for (int g = 0; g < 8; ++g) {
+                        uint32_t acc[16];
+                        tmem_ld16(ta + g * 16, acc);
+                        tmem_wait_ld16(acc);
                         if (any) {
-                            uint32_t sum[32];
-                            tmem_ld32(trun + g * 32, sum);
-                            tmem_wait_ld(sum);
+                            uint32_t sum[16];
+                            tmem_ld16(trun + g * 16, sum);
+                            tmem_wait_ld16(sum);
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
+                            for (int i = 0; i < 16; ++i)
                                 acc[i] = __float_as_uint(__uint_as_float(sum[i]) + __uint_as_float(acc[i]));
                         }
-                        tmem_st32(trun + g * 32, acc);
+                        tmem_st16(trun + g * 16, acc);
                     }
                     tmem_wait_st();
                     any = true;
@@ -473,19 +506,19 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 }
                 if (!ok || *abort_flag) break;
 #pragma unroll 1
-                for (int g = 0; g < 4; ++g) {
-                    float x[32];
+                for (int g = 0; g < 8; ++g) {
+                    float x[16];
                     if (any) {
-                        uint32_t sum[32];
-                        tmem_ld32(trun + g * 32, sum);
-                        tmem_wait_ld(sum);
+                        uint32_t sum[16];
+                        tmem_ld16(trun + g * 16, sum);
+                        tmem_wait_ld16(sum);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(sum[i]);
+                        for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(sum[i]);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) x[i] = 0.f;
+                        for (int i = 0; i < 16; ++i) x[i] = 0.f;
                     }
-                    write_chunk(g, x);
+                    write_chunk(std::integral_constant<int, 16>{}, g, x);
                 }
             }
         }
@@ -579,7 +612,7 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
                       LiveTables lt, int n_ax, int fp16, const float* d_amax, float2* d_v, int N, int rows,
                       int flush, int split, int n_ctas, int* d_sched, float* d_partial, int* d_err,
                       const ZJob* zj, cudaStream_t st, long long* launches) {
-    using C = Cfg<BN, (ZP != 0)>;
+    using C = Cfg<BN, zwarps(ZP, ZA, ZF)>;
     const int n_tiles = n_tiles_for<BN>(rows);
     const int n_units = n_tiles * n_inst * split;
     int* order = d_sched;            // [n_inst]
@@ -611,18 +644,18 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
 bool herk_tc_available() { return get_encode() != nullptr; }
 
 cudaError_t herk_tc_init() {
-    const int fz = Cfg<128, true>::SMEM;
+    const int f1 = Cfg<128, zwarps(1, 1, 1)>::SMEM, f2 = Cfg<128, zwarps(1, 2, 2)>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_herk_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<256>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, f1);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<128, 2, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+        e = cudaFuncSetAttribute(k_herk_tc<128, 2, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, f1);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, f2);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<128, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, fz);
+        e = cudaFuncSetAttribute(k_herk_tc<128, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, f2);
     return e;
 }
 

@@ -57,7 +57,7 @@ __global__ void k_ant_phase(Model m, const Inst* __restrict__ inst, const Chan* 
 // number of resident blocks per SM (room left for a concurrent HERK).  The
 // FP16 scales of the item's instances go to shared memory once per item.
 template <int PREC, int NAX, int NFD>
-__global__ void __launch_bounds__(128, NAX * NFD > 1 ? 6 : 8)
+__global__ void __launch_bounds__(128, NAX * NFD > 1 ? 6 : 7)
 k_zbuild(Model m, const Inst* __restrict__ inst, const ZGroup* __restrict__ groups, int g_first, LiveTables lt,
          const float2* __restrict__ wa, long long wa_pitch, const float* __restrict__ amax, void* u, void* ulo,
          int rows, long long k_pitch, int ant_per_block, const AntPhase* __restrict__ aph, int n_phase, int nx,

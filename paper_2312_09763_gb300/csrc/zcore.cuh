@@ -165,27 +165,33 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
         const float2* w = wb + (long long)m.beam_idx[a] * (NFD * NAX) * wa_pitch;
         T* ur = ub + 2ll * a * NFD * k_pitch;
         T* lr = PREC != 0 ? lb + 2ll * a * NFD * k_pitch : nullptr;
+        // WA of the two sources for the group's instance w + jrel: one 16-byte load
+        // per component (s0 is even)
+        constexpr int NC = NFD * NAX;
+        auto load_wa = [&](int jrel, float4 (&A)[NC]) {
+            const float2* wj = w + (long long)jrel * wa_slot;
+#pragma unroll
+            for (int c = 0; c < NC; ++c) A[c] = *reinterpret_cast<const float4*>(wj + (long long)c * wa_pitch);
+        };
         // U rows 2(a NFD + p) + {0, 1} of instance j of the group, at phase (c, s)
-        auto emit = [&](int j, float c0, float sn0, float c1, float sn1) {
+        auto emit = [&](int j, const float4 (&A)[NC], float c0, float sn0, float c1, float sn1) {
             const float sc = PREC == 2 ? scale[j] : 1.f;
 #pragma unroll
             for (int p = 0; p < NFD; ++p) {
                 float re[2 * NAX], im[2 * NAX];
 #pragma unroll
                 for (int k = 0; k < NAX; ++k) {
-                    // WA of the two sources: one 16-byte load (s0 is even)
-                    const float4 A = *reinterpret_cast<const float4*>(w + (long long)(p * NAX + k) * wa_pitch);
+                    const float4 a4 = A[p * NAX + k];
                     // Z = WA * exp(-2 pi i phase) = WA * (c - i s)
-                    re[k] = fmaf(A.x, c0, A.y * sn0);
-                    im[k] = fmaf(A.y, c0, -A.x * sn0);
-                    re[NAX + k] = fmaf(A.z, c1, A.w * sn1);
-                    im[NAX + k] = fmaf(A.w, c1, -A.z * sn1);
+                    re[k] = fmaf(a4.x, c0, a4.y * sn0);
+                    im[k] = fmaf(a4.y, c0, -a4.x * sn0);
+                    re[NAX + k] = fmaf(a4.z, c1, a4.w * sn1);
+                    im[NAX + k] = fmaf(a4.w, c1, -a4.z * sn1);
                 }
                 const long long r0 = 2ll * p * k_pitch;
                 put_row<PREC, NAX>(ur + r0, PREC != 0 ? lr + r0 : nullptr, re, sc);
                 put_row<PREC, NAX>(ur + r0 + k_pitch, PREC != 0 ? lr + r0 + k_pitch : nullptr, im, sc);
             }
-            w += wa_slot;
             ur += slot_stride;
             if (PREC != 0) lr += slot_stride;
         };
@@ -199,6 +205,14 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
             cos_sin_turns(Q0, rc0, rs0);
             cos_sin_turns(Q1, rc1, rs1);
             for (int j0 = 0; j0 < g.n; j0 += kAnchor) {
+                // one-component beams: the block's WA loads go out together
+                constexpr int PF = NC == 1 ? kAnchor : 1;
+                float4 Apf[PF][NC];
+                if constexpr (PF > 1) {
+#pragma unroll
+                    for (int jj = 0; jj < PF; ++jj)
+                        if (j0 + jj < g.n) load_wa(jj, Apf[jj]);
+                }
                 float c0, sn0, c1, sn1;
                 cos_sin_turns(F0, c0, sn0);
                 cos_sin_turns(F1, c1, sn1);
@@ -206,7 +220,14 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                 F1 += Q1 * kAnchor;
 #pragma unroll
                 for (int jj = 0; jj < kAnchor; ++jj) {
-                    if (j0 + jj < g.n) emit(j0 + jj, c0, sn0, c1, sn1);
+                    if (j0 + jj < g.n) {
+                        if constexpr (PF > 1) {
+                            emit(j0 + jj, Apf[jj], c0, sn0, c1, sn1);
+                        } else {
+                            load_wa(jj, Apf[0]);
+                            emit(j0 + jj, Apf[0], c0, sn0, c1, sn1);
+                        }
+                    }
                     if (jj + 1 < kAnchor) {  // (c + i s) e^{2 pi i dF}
                         const float nc0 = fmaf(c0, rc0, -sn0 * rs0), nc1 = fmaf(c1, rc1, -sn1 * rs1);
                         sn0 = fmaf(sn0, rc0, c0 * rs0);
@@ -215,14 +236,18 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                         c1 = nc1;
                     }
                 }
+                w += kAnchor * wa_slot;
             }
         } else {
             for (int j = 0; j < g.n; ++j) {
                 const AntPhase pj = load_phase(tab + (long long)(g.uniform ? 0 : j) * m.n_ant + a);
+                float4 A[NC];
+                load_wa(0, A);
                 float c0, sn0, c1, sn1;
                 cos_sin_turns(phase64(pj, S0, E0), c0, sn0);
                 cos_sin_turns(phase64(pj, S1, E1), c1, sn1);
-                emit(j, c0, sn0, c1, sn1);
+                emit(j, A, c0, sn0, c1, sn1);
+                w += wa_slot;
             }
         }
     }
