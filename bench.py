@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="small workload (profiling captures)")
+    ap.add_argument("--small-lsts", type=int, default=1, help="LSTs of the small workload")
     ap.add_argument("--workload", default="hera", choices=["hera", "diffuse", "uneven", "learned"],
                     help="hera: 350 ant x 1e5 src x 64 ch x 60 t (default); diffuse: 350 ant x 196,608 HEALPix "
                          "pixels x 32 ch x 120 t, 2x2 Jones beam; uneven: 256 (LST, nu) pairs, one call; "
@@ -113,7 +114,7 @@ def workload(args):
         w.name = w.name.replace("x 8 ch x 1 t", "x 8 ch (146.5-153.5 MHz) x 1 t")
         return w
     if args.small:  # profiling captures: 16 channels of 1 LST of the full sky (~2.2 GB of Z planes)
-        w = synth.hera_like(n_ant=350, n_src=100_000, n_chan=16, n_times=1)
+        w = synth.hera_like(n_ant=350, n_src=100_000, n_chan=16, n_times=args.small_lsts)
         w.freqs = synth.hera_like().freqs[24:40]
         return w
     return synth.hera_like()

@@ -209,7 +209,7 @@ struct Cfg {
 // Z-build warps of a fused HERK: as many as 64 K registers allow with the
 // Z core's register use (one-component beams: 64 registers, 1024 threads;
 // Jones beams: 80 registers, 768 threads).
-__host__ __device__ constexpr int zwarps(int zp, int za, int zf) { return zp == 0 ? 0 : (za * zf == 1 ? 22 : 14); }
+__host__ __device__ constexpr int zwarps(int zp, int za, int zf) { return zp == 0 ? 0 : (za * zf == 1 ? 18 : 14); }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16 (format 1) or FP16
 // (format 0), both K-major, N = BN, M = 128.
