@@ -550,7 +550,7 @@ mv_status enqueue_wa(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, 
     cudaError_t e;
     if (c->use_sur)
         e = surrogate_wa(c->sur, m, p.plan->inst, b.inst0, b.n, p.h_nlive, p.plan->nu, c->nu_ref, p.lt,
-                         (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
+                         (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, (int*)c->err.p, c->n_sms, st, L);
     else
         e = launch_wa(m, (const float2*)c->planes.p, (const Chan*)c->chan.p, d_inst, b.inst0, b.n, p.lt,
                       (float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, st, L);
@@ -858,7 +858,7 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
     mv_ctx* c = new mv_ctx();
     c->device = device;
     c->n_sms = pr.multiProcessorCount;
-    if (herk_tc_init() != cudaSuccess) {
+    if (herk_tc_init() != cudaSuccess || mlp_tc_init() != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return fail(MV_ERR_CUDA, "kernel attribute set-up failed");

@@ -204,7 +204,27 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
                             double* loss_first, double* loss_last, long long* L);
 cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& h_inst, int inst0, int n_inst,
                          const std::vector<int>& h_nlive, const std::vector<double>& h_nu, double nu_ref,
-                         LiveTables lt, float2* wa, long long wa_pitch, float* amax, cudaStream_t st, long long* L);
+                         LiveTables lt, float2* wa, long long wa_pitch, float* amax, int* d_err, int n_sms,
+                         cudaStream_t st, long long* L);
+
+// The network of a surrogate, for the tensor-core forward pass (mlp_tc.cu).
+struct MlpTcArgs {
+    int F, E, H, depth, d0p, n_beam, n_out;
+    float nu_mid, nu_half;
+    const float* p;               // FP32 parameters (biases, embedding)
+    const __nv_bfloat16* pb;      // BF16 copy (weights)
+    long long off_w[9], off_b[9];  // per layer: hidden layers, then the output layer
+    long long off_emb;
+    const float* Bf;              // Fourier matrix [F][3]
+};
+// Whether the tensor-core forward pass handles this network shape.
+bool mlp_tc_supported(int F, int E, int H, int depth, int d0p, int n_out);
+cudaError_t mlp_tc_init();
+// WA of one instance (live count K at time index t, frequency nu) from the
+// network: rows (beam b, source s), b < n_beam; WA[b][comp][s] as launch_wa.
+cudaError_t launch_mlp_wa_tc(const MlpTcArgs& a, const Model& m, LiveTables lt, int t, int K, float nu,
+                             float ln_ratio, float2* wa_slot, long long wa_pitch, float* amax, int* d_err,
+                             int n_sms, cudaStream_t st, long long* launches);
 
 // Exponent e of the exact power-of-two scale 2^e that brings max |Z| of an
 // instance into [2^13, 2^14) before the FP16 hi/lo split (the HERK epilogue

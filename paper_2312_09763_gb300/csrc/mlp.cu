@@ -746,11 +746,22 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
 // inst0 + n_inst - 1 from the network, into WA slots (n_beam = n_ant layout).
 cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& h_inst, int inst0, int n_inst,
                          const std::vector<int>& h_nlive, const std::vector<double>& h_nu, double nu_ref, LiveTables lt,
-                         float2* wa, long long wa_pitch, float* amax, cudaStream_t st, long long* L) {
+                         float2* wa, long long wa_pitch, float* amax, int* d_err, int n_sms, cudaStream_t st,
+                         long long* L) {
     const Dims& d = S->d;
     const int ncomp = m.n_feed * m.n_ax;
     const long long chunk = 1 << 19;
-    cudaError_t e = ensure_rows(S, chunk);
+    // the tensor-core forward pass (features, layers and WA in one launch per
+    // instance) where the network shape allows, else the mma.sync GEMMs
+    const bool tc = mlp_tc_supported(d.F, d.E, d.H, d.depth, d.d0p, d.n_out);
+    MlpTcArgs ta{};
+    if (tc) {
+        ta.F = d.F; ta.E = d.E; ta.H = d.H; ta.depth = d.depth; ta.d0p = d.d0p; ta.n_beam = d.n_ant;
+        ta.n_out = d.n_out; ta.nu_mid = d.nu_mid; ta.nu_half = d.nu_half;
+        ta.p = S->p; ta.pb = S->pb; ta.off_emb = S->off_emb; ta.Bf = S->Bf;
+        for (int l = 0; l <= d.depth; ++l) { ta.off_w[l] = S->off_w[l]; ta.off_b[l] = S->off_b[l]; }
+    }
+    cudaError_t e = tc ? cudaSuccess : ensure_rows(S, chunk);
     for (int j = 0; j < n_inst && e == cudaSuccess; ++j) {
         const Inst& in = h_inst[inst0 + j];
         const int K = h_nlive[in.t];
@@ -758,7 +769,8 @@ cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& 
         const float nu = (float)h_nu[in.c];
         const float lnr = (float)std::log(h_nu[in.c] / nu_ref);
         float2* wslot = wa + (long long)j * m.n_beam * ncomp * wa_pitch;
-        for (long long r0 = 0; r0 < rows && e == cudaSuccess; r0 += chunk) {
+        if (tc) e = launch_mlp_wa_tc(ta, m, lt, in.t, K, nu, lnr, wslot, wa_pitch, amax + j, d_err, n_sms, st, L);
+        for (long long r0 = 0; !tc && r0 < rows && e == cudaSuccess; r0 += chunk) {
             const int R = (int)std::min(chunk, rows - r0);
             k_rows<<<gridsz(R, 256), 256, 0, st>>>(d.n_ant, K, r0, R, in.t, nu, lt, S->ant, S->az, S->za, S->nu);
             k_features<<<gridsz((long long)R * d.d0p, 256), 256, 0, st>>>(d, S->Bf, S->p + S->off_emb, R, S->ant,

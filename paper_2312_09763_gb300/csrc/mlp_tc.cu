@@ -1,0 +1,357 @@
+// mlp_tc.cu -- the learned beam's forward pass on the sm_103a tensor cores,
+// fused with the beam-times-flux step of the simulator: for every row
+// (antenna beam b, live source s) of one instance it builds the network's
+// input features, runs the hidden layers and the output layer with
+// tcgen05.mma, and writes WA[b][comp][s] = sqrt(I_s(nu)) A^{pk}_b(s) (or,
+// for a polarised sky, A M with the coherency square root, eq. "fullz") --
+// Algorithm 2 step (ii) of arXiv:2312.09763 with the network in place of the
+// interpolation of Sec. 2.4.
+//
+// The network (mlp.cu): x = (az / 2 pi, za / (pi/2), (nu - nu_mid) / nu_half),
+// f = [sin(2 pi B x), cos(2 pi B x), e_b, 0...] (d0p columns), h_l = relu(W_l
+// h_{l-1} + b_l) for the hidden layers, y = W_out h + b_out.  Operands are
+// BF16, accumulation FP32 in TMEM, as in the training kernels.
+//
+// One persistent CTA per SM walks 128-row tiles.  Warp 0 streams the weight
+// panels (64 input columns x H rows, 128-byte swizzle) with TMA into a ring of
+// four slots; warp 1 owns TMEM and issues the MMAs (M = 128, N = H, K = 16);
+// warps 2..9 (two per TMEM lane quadrant, one per half of the columns) write
+// the features, drain each layer's accumulator through bias and ReLU back
+// into the shared-memory activation panels, and write WA from the output
+// layer.  A weight slot is reloaded for the next layer as soon as the MMAs
+// that read it complete, so the weight stream overlaps the MMAs and the
+// epilogue.  Every mbarrier wait is bounded (tc.cuh).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace mv {
+namespace {
+
+using namespace tc;
+
+constexpr int TM = 128;          // rows per tile
+constexpr int KP = 64;           // input columns per swizzled panel (128 B of BF16)
+constexpr int MAXL = 8;          // hidden layers at most
+constexpr int A_PANEL = TM * 128;                // 16 KB
+constexpr int W_PANEL_MAX = 256 * 128;           // 32 KB (H = 256)
+constexpr int O_PANEL = 16 * 128;                // 2 KB (output rows padded to 16 with zeros)
+constexpr int SMEM_A = 4 * A_PANEL;              // 64 KB
+constexpr int SMEM_W = 4 * W_PANEL_MAX;          // 128 KB
+constexpr int SMEM_O = 4 * O_PANEL;              // 8 KB
+constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + 256 + 1024;
+constexpr int THREADS = 10 * 32;
+
+struct Maps {
+    CUtensorMap w[MAXL + 1];  // hidden layers, then the output layer
+};
+
+struct Net {
+    int F, E, H, depth, d0p, n_beam, n_out;
+    float nu_mid, nu_half;
+    const float* p;  // FP32 parameters (biases, embedding)
+    long long off_b[MAXL + 1];
+    long long off_emb;
+    const float* Bf;  // [F][3]
+};
+
+// Shared-memory address of the 16-byte chunk holding input columns
+// [8 j, 8 j + 8) of panel `panel`, row r (128-byte swizzle: chunk j ^ (r & 7)).
+__device__ __forceinline__ uint32_t a_chunk(uint32_t a_base, int r, int col) {
+    const int panel = col / KP, j = (col % KP) / 8;
+    return a_base + panel * A_PANEL + r * 128 + ((j ^ (r & 7)) << 4);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Model m, LiveTables lt, int t, int K,
+         float nu, float ln_ratio, float2* __restrict__ wa, long long wa_pitch, float* __restrict__ amax,
+         int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t a_base = smem_u32(smem);
+    const uint32_t w_base = a_base + SMEM_A;
+    const uint32_t o_base = w_base + SMEM_W;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O);
+    // wfull[4], wfree[4], afull, dfull, ofull
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    auto wfull = [&](int i) { return smem_u32(&bars[i]); };
+    auto wfree = [&](int i) { return smem_u32(&bars[4 + i]); };
+    const uint32_t afull = smem_u32(&bars[8]), dfull = smem_u32(&bars[9]), ofull = smem_u32(&bars[10]);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int H = net.H, D = net.depth;
+    const long long R = (long long)net.n_beam * K;
+    const int n_tiles = (int)((R + TM - 1) / TM);
+    const int w_panel = H * 128;
+    auto panels = [&](int l) { return l == 0 ? (net.d0p + KP - 1) / KP : H / KP; };
+    auto ksteps = [&](int l, int pnl) {  // 16-column MMA steps in panel pnl of layer l
+        const int kin = l == 0 ? net.d0p : H;
+        return min(KP, kin - pnl * KP) / 16;
+    };
+
+    // output-layer panels: rows 8..15 stay zero (the tensor map fills rows 0..7)
+    for (int i = threadIdx.x; i < SMEM_O / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(smem + SMEM_A + SMEM_W)[i] = make_uint4(0u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) { mbar_init(wfull(i), 1); mbar_init(wfree(i), 1); }
+        mbar_init(afull, 8);
+        mbar_init(dfull, 1);
+        mbar_init(ofull, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // output layer once: its 8 rows (one 1 KB swizzle atom per panel)
+            mbar_expect_tx(ofull, (uint32_t)((H / KP) * (O_PANEL / 2)));
+            for (int pnl = 0; pnl < H / KP; ++pnl) tma_load_2d(o_base + pnl * O_PANEL, &maps.w[D], pnl * KP, 0, ofull);
+            int use[4] = {0, 0, 0, 0};
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
+                for (int l = 0; l < D && ok; ++l)
+                    for (int pnl = 0; pnl < panels(l); ++pnl) {
+                        if (!wait_bounded(wfree(pnl), ((uint32_t)use[pnl] & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
+                        ++use[pnl];
+                        mbar_expect_tx(wfull(pnl), (uint32_t)w_panel);
+                        tma_load_2d(w_base + pnl * W_PANEL_MAX, &maps.w[l], pnl * KP, 0, wfull(pnl));
+                    }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id_hidden = idesc_f16(false, TM, H), id_out = idesc_f16(false, TM, 16);
+            int use[4] = {0, 0, 0, 0};
+            int na = 0;
+            bool ok = wait_bounded(ofull, 0u, abort_flag, err);
+            for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+                for (int l = 0; l <= D && ok; ++l) {
+                    if (!wait_bounded(afull, (uint32_t)(na++) & 1u, abort_flag, err)) { ok = false; break; }
+                    tc_fence_after();
+                    const bool out = l == D;
+                    const int np = out ? H / KP : panels(l);
+                    for (int pnl = 0; pnl < np; ++pnl) {
+                        if (!out) {
+                            if (!wait_bounded(wfull(pnl), (uint32_t)(use[pnl]++) & 1u, abort_flag, err)) { ok = false; break; }
+                            tc_fence_after();
+                        }
+                        const uint32_t b0 = out ? o_base + pnl * O_PANEL : w_base + pnl * W_PANEL_MAX;
+                        const int ns = out ? KP / 16 : ksteps(l, pnl);
+                        for (int kk = 0; kk < ns; ++kk)
+                            tc_mma(tmem, sdesc(a_base + pnl * A_PANEL + kk * 32), sdesc(b0 + kk * 32),
+                                   out ? id_out : id_hidden, (pnl | kk) != 0 ? 1u : 0u);
+                        if (!out) tc_commit(wfree(pnl));
+                    }
+                    if (!ok) break;
+                    tc_commit(dfull);
+                }
+            }
+        }
+    } else {
+        // epilogue warps: lane quadrant q, column half h
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int r_loc = q * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        const int F = net.F, E = net.E;
+        int nd = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            const long long r = (long long)tile * TM + r_loc;
+            const bool valid = r < R;
+            const int b = valid ? (int)(r / K) : 0, s = valid ? (int)(r % K) : 0;
+            // ---- input features of row r (this warp's half of them)
+            {
+                float2 azza = make_float2(0.f, 0.f);
+                if (valid) azza = lt.azza[(long long)t * lt.pitch + s];
+                const float x0 = azza.x * 0.15915494309189535f;   // az / 2 pi
+                const float x1 = azza.y * 0.63661977236758134f;   // za / (pi / 2)
+                const float x2 = (nu - net.nu_mid) / net.nu_half;
+                const int f0 = h * (F / 2);
+                for (int c8 = 0; c8 < F / 2; c8 += 8) {
+                    float sv[8], cv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int f = f0 + c8 + i;
+                        float ph = net.Bf[3 * f] * x0 + net.Bf[3 * f + 1] * x1 + net.Bf[3 * f + 2] * x2;
+                        ph -= rintf(ph);
+                        sincospif(2.f * ph, &sv[i], &cv[i]);
+                        if (!valid) sv[i] = cv[i] = 0.f;
+                    }
+                    st_shared_v4(a_chunk(a_base, r_loc, f0 + c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
+                                 pack_bf16(sv[4], sv[5]), pack_bf16(sv[6], sv[7]));
+                    st_shared_v4(a_chunk(a_base, r_loc, F + f0 + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
+                                 pack_bf16(cv[4], cv[5]), pack_bf16(cv[6], cv[7]));
+                }
+                if (h == 1) {
+                    const float* e = net.p + net.off_emb + (long long)b * E;
+                    for (int c8 = 0; c8 < net.d0p - 2 * F; c8 += 8) {
+                        float v[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) v[i] = valid && c8 + i < E ? e[c8 + i] : 0.f;
+                        st_shared_v4(a_chunk(a_base, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                                     pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(afull);
+            // ---- hidden layers: accumulator -> bias, ReLU -> BF16 activations
+            for (int l = 0; l < D; ++l) {
+                if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
+                tc_fence_after();
+                const float* bias = net.p + net.off_b[l];
+                for (int g = 0; g < H / 64; ++g) {
+                    const int c0 = h * (H / 2) + g * 32;
+                    uint32_t acc[32];
+                    tmem_ld32(trow + c0, acc);
+                    tmem_wait_ld(acc);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float v[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            v[i] = fmaxf(__uint_as_float(acc[8 * j + i]) + bias[c0 + 8 * j + i], 0.f);
+                        st_shared_v4(a_chunk(a_base, r_loc, c0 + 8 * j), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                                     pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+                    }
+                }
+                tc_fence_before();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(afull);
+            }
+            if (!ok) break;
+            // ---- output layer -> WA
+            if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
+            tc_fence_after();
+            if (h == 0) {
+                uint32_t acc[16];
+                tmem_ld16(trow, acc);
+                tmem_wait_ld16(acc);
+                float mx = 0.f;
+                if (valid) {
+                    const float* bo = net.p + net.off_b[D];
+                    float y[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) y[i] = __uint_as_float(acc[i]) + bo[i];
+                    const long long o = (long long)t * lt.pitch + s;
+                    const int src = lt.idx[o];
+                    const float spec = expf(m.half_alpha[src] * ln_ratio);
+                    const int ncomp = net.n_out / 2;
+                    float2* wb = wa + (long long)b * ncomp * wa_pitch + s;
+                    if (!m.pol_m) {
+                        const float w = m.sqrt_flux[src] * spec;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (c < ncomp) {
+                                const float2 v = make_float2(w * y[2 * c], w * y[2 * c + 1]);
+                                wb[(long long)c * wa_pitch] = v;
+                                mx = fmaxf(mx, hypotf(v.x, v.y));
+                            }
+                    } else {  // two axes per feed: z = A M (eq. "fullz")
+                        const float4 M = m.pol_m[src];
+#pragma unroll
+                        for (int c = 0; c < 4; c += 2)
+                            if (c + 1 < ncomp) {
+                                float2 z0, z1;
+                                apply_sky_sqrt(make_float2(y[2 * c], y[2 * c + 1]),
+                                               make_float2(y[2 * c + 2], y[2 * c + 3]), M, spec, z0, z1);
+                                wb[(long long)c * wa_pitch] = z0;
+                                wb[(long long)(c + 1) * wa_pitch] = z1;
+                                mx = fmaxf(mx, fmaxf(hypotf(z0.x, z0.y), hypotf(z1.x, z1.y)));
+                            }
+                    }
+                }
+                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                if (lane == 0 && mx > 0.f) atomicMax(reinterpret_cast<int*>(amax), __float_as_int(mx));
+                tc_fence_before();
+            }
+        }
+    }
+    __syncthreads();
+    if (*abort_flag) {
+        // let copies and MMAs already issued land before TMEM and smem go away
+        const unsigned long long t0 = gtimer();
+        while (gtimer() - t0 < 2000000ull) {}
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    }
+}
+
+bool make_wmap(CUtensorMap* map, const void* base, int kin, int rows, int box_rows) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)kin, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kin * 2};
+    cuuint32_t box[2] = {KP, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool mlp_tc_supported(int F, int E, int H, int depth, int d0p, int n_out) {
+    return (H == 128 || H == 256) && depth >= 1 && depth <= MAXL && d0p <= 256 && d0p % 16 == 0 && F % 16 == 0 &&
+           E % 8 == 0 && n_out <= 8 && 2 * F + E <= d0p && get_encode() != nullptr;
+}
+
+cudaError_t mlp_tc_init() {
+    return cudaFuncSetAttribute(k_mlp_wa, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+cudaError_t launch_mlp_wa_tc(const MlpTcArgs& a, const Model& m, LiveTables lt, int t, int K, float nu,
+                             float ln_ratio, float2* wa_slot, long long wa_pitch, float* amax, int* d_err, int n_sms,
+                             cudaStream_t st, long long* launches) {
+    if (K <= 0 || a.n_beam <= 0) return cudaSuccess;
+    if (!mlp_tc_supported(a.F, a.E, a.H, a.depth, a.d0p, a.n_out)) return cudaErrorInvalidValue;
+    Maps maps{};
+    for (int l = 0; l <= a.depth; ++l) {
+        const int kin = l == 0 ? a.d0p : a.H;
+        const int rows = l == a.depth ? 8 : a.H;
+        const int box_rows = rows;
+        if (!make_wmap(&maps.w[l], a.pb + a.off_w[l], kin, rows, box_rows)) return cudaErrorInvalidValue;
+    }
+    Net net{};
+    net.F = a.F; net.E = a.E; net.H = a.H; net.depth = a.depth; net.d0p = a.d0p; net.n_beam = a.n_beam;
+    net.n_out = a.n_out;
+    net.nu_mid = a.nu_mid; net.nu_half = a.nu_half;
+    net.p = a.p;
+    for (int l = 0; l <= a.depth; ++l) net.off_b[l] = a.off_b[l];
+    net.off_emb = a.off_emb;
+    net.Bf = a.Bf;
+    const long long R = (long long)a.n_beam * K;
+    const int n_tiles = (int)((R + TM - 1) / TM);
+    const int grid = std::max(1, std::min(n_sms, n_tiles));
+    k_mlp_wa<<<grid, THREADS, SMEM_BYTES, st>>>(maps, net, m, lt, t, K, nu, ln_ratio, wa_slot, wa_pitch, amax, d_err);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace mv
