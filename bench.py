@@ -341,7 +341,7 @@ def main():
         learned.update({"network_rows_per_step": rows_step, "flop_per_row": 2 * macs,
                         "surrogate_vs_grid_rel_err": err})
         roof = {"bound": "tensor", "achieved": mlp_tf, "peak": sustained, "unit": "TFLOP/s",
-                "frac": mlp_tf / sustained, "traffic": None, "kernel": "learned-beam forward (k_gemm, mma.sync)",
+                "frac": mlp_tf / sustained, "traffic": None, "kernel": "k_mlp_wa (learned-beam forward + WA, tcgen05)",
                 "launches": n_b, "avg_launch_ms": ms_b / max(n_b, 1),
                 "peak_source": f"{src} bf16 sustained (kernels timed inside a long step)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
