@@ -15,7 +15,7 @@
 // One persistent CTA per SM walks 128-row tiles.  Warp 0 streams the weight
 // panels (64 input columns x H rows, 128-byte swizzle) with TMA into a ring of
 // four slots; warp 1 owns TMEM and issues the MMAs (M = 128, N = H, K = 16);
-// warps 2..9 (two per TMEM lane quadrant, one per half of the columns) write
+// warps 2..17 (four per TMEM lane quadrant, one per quarter of the columns) write
 // the features, drain each layer's accumulator through bias and ReLU back
 // into the shared-memory activation panels, and write WA from the output
 // layer.  A weight slot is reloaded for the next layer as soon as the MMAs
@@ -41,8 +41,10 @@ constexpr int O_PANEL = 16 * 128;                // 2 KB (output rows padded to 
 constexpr int SMEM_A = 4 * A_PANEL;              // 64 KB
 constexpr int SMEM_W = 4 * W_PANEL_MAX;          // 128 KB
 constexpr int SMEM_O = 4 * O_PANEL;              // 8 KB
-constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + 256 + 1024;
-constexpr int THREADS = 10 * 32;
+constexpr int SMEM_BIAS = (MAXL + 1) * 256 * 4;  // every layer's biases
+constexpr int NEPI = 16;                          // epilogue warps: four per TMEM lane quadrant
+constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + 256 + 1024;
+constexpr int THREADS = (2 + NEPI) * 32;
 
 struct Maps {
     CUtensorMap w[MAXL + 1];  // hidden layers, then the output layer
@@ -82,7 +84,8 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     const uint32_t a_base = smem_u32(smem);
     const uint32_t w_base = a_base + SMEM_A;
     const uint32_t o_base = w_base + SMEM_W;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O);
+    float* sbias = reinterpret_cast<float*>(smem + SMEM_A + SMEM_W + SMEM_O);  // [layer][256]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS);
     // wfull[4], wfree[4], afull, dfull, ofull
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -105,9 +108,13 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     for (int i = threadIdx.x; i < SMEM_O / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(smem + SMEM_A + SMEM_W)[i] = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int l = 0; l <= D; ++l) {
+        const int n = l == D ? 8 : H;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sbias[l * 256 + i] = net.p[net.off_b[l] + i];
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i) { mbar_init(wfull(i), 1); mbar_init(wfree(i), 1); }
-        mbar_init(afull, 8);
+        mbar_init(afull, NEPI);
         mbar_init(dfull, 1);
         mbar_init(ofull, 1);
         *abort_flag = 0;
@@ -170,7 +177,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             }
         }
     } else {
-        // epilogue warps: lane quadrant q, column half h
+        // epilogue warps: lane quadrant q, column quarter h
         const int q = warp & 3, h = (warp - 2) >> 2;
         const int r_loc = q * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
@@ -181,38 +188,35 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             const long long r = (long long)tile * TM + r_loc;
             const bool valid = r < R;
             const int b = valid ? (int)(r / K) : 0, s = valid ? (int)(r % K) : 0;
-            // ---- input features of row r (this warp's half of them)
+            // ---- input features of row r: chunks of 8 columns, chunk c by quarter c % 4
             {
                 float2 azza = make_float2(0.f, 0.f);
                 if (valid) azza = lt.azza[(long long)t * lt.pitch + s];
                 const float x0 = azza.x * 0.15915494309189535f;   // az / 2 pi
                 const float x1 = azza.y * 0.63661977236758134f;   // za / (pi / 2)
                 const float x2 = (nu - net.nu_mid) / net.nu_half;
-                const int f0 = h * (F / 2);
-                for (int c8 = 0; c8 < F / 2; c8 += 8) {
+                for (int c8 = 8 * h; c8 < F; c8 += 32) {
                     float sv[8], cv[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int f = f0 + c8 + i;
+                        const int f = c8 + i;
                         float ph = net.Bf[3 * f] * x0 + net.Bf[3 * f + 1] * x1 + net.Bf[3 * f + 2] * x2;
                         ph -= rintf(ph);
                         sincospif(2.f * ph, &sv[i], &cv[i]);
                         if (!valid) sv[i] = cv[i] = 0.f;
                     }
-                    st_shared_v4(a_chunk(a_base, r_loc, f0 + c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
+                    st_shared_v4(a_chunk(a_base, r_loc, c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
                                  pack_bf16(sv[4], sv[5]), pack_bf16(sv[6], sv[7]));
-                    st_shared_v4(a_chunk(a_base, r_loc, F + f0 + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
+                    st_shared_v4(a_chunk(a_base, r_loc, F + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
                                  pack_bf16(cv[4], cv[5]), pack_bf16(cv[6], cv[7]));
                 }
-                if (h == 1) {
-                    const float* e = net.p + net.off_emb + (long long)b * E;
-                    for (int c8 = 0; c8 < net.d0p - 2 * F; c8 += 8) {
-                        float v[8];
+                const float* e = net.p + net.off_emb + (long long)b * E;
+                for (int c8 = 8 * h; c8 < net.d0p - 2 * F; c8 += 32) {
+                    float v[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) v[i] = valid && c8 + i < E ? e[c8 + i] : 0.f;
-                        st_shared_v4(a_chunk(a_base, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                     pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                    }
+                    for (int i = 0; i < 8; ++i) v[i] = valid && c8 + i < E ? e[c8 + i] : 0.f;
+                    st_shared_v4(a_chunk(a_base, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                                 pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -222,18 +226,20 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             for (int l = 0; l < D; ++l) {
                 if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
-                const float* bias = net.p + net.off_b[l];
-                for (int g = 0; g < H / 64; ++g) {
-                    const int c0 = h * (H / 2) + g * 32;
+                const float* bias = sbias + l * 256;
+                for (int g = 0; g < H / 128; ++g) {
+                    const int c0 = h * (H / 4) + g * 32;
                     uint32_t acc[32];
                     tmem_ld32(trow + c0, acc);
                     tmem_wait_ld(acc);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
+                        const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j);
+                        const float4 b1 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j + 4);
+                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                         float v[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            v[i] = fmaxf(__uint_as_float(acc[8 * j + i]) + bias[c0 + 8 * j + i], 0.f);
+                        for (int i = 0; i < 8; ++i) v[i] = fmaxf(__uint_as_float(acc[8 * j + i]) + bb[i], 0.f);
                         st_shared_v4(a_chunk(a_base, r_loc, c0 + 8 * j), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
                                      pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
                     }
@@ -253,7 +259,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                 tmem_wait_ld16(acc);
                 float mx = 0.f;
                 if (valid) {
-                    const float* bo = net.p + net.off_b[D];
+                    const float* bo = sbias + D * 256;
                     float y[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) y[i] = __uint_as_float(acc[i]) + bo[i];
@@ -318,7 +324,7 @@ bool make_wmap(CUtensorMap* map, const void* base, int kin, int rows, int box_ro
 }  // namespace
 
 bool mlp_tc_supported(int F, int E, int H, int depth, int d0p, int n_out) {
-    return (H == 128 || H == 256) && depth >= 1 && depth <= MAXL && d0p <= 256 && d0p % 16 == 0 && F % 16 == 0 &&
+    return (H == 128 || H == 256) && depth >= 1 && depth <= MAXL && d0p <= 256 && d0p % 16 == 0 && F % 8 == 0 &&
            E % 8 == 0 && n_out <= 8 && 2 * F + E <= d0p && get_encode() != nullptr;
 }
 
