@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
     ap.add_argument("--max-batch", type=int, default=0, help="instances per launch (mv_options.max_batch; 0 = auto)")
+    ap.add_argument("--train-steps", type=int, default=1221,
+                    help="learned workload: Adam steps of 8192 samples (default 1221, i.e. 1e7 samples)")
     ap.add_argument("--no-fuse", action="store_true", help="Z build as its own launch (mv_options.fuse_zbuild = 0)")
     ap.add_argument("--herk-config", default=None, metavar="BN,SPLIT,FLUSH",
                     help="fix the tensor-core HERK tile width, split-K and flush interval (skips autotune)")
@@ -256,11 +258,11 @@ def main():
         # no host round trip of the 5.5 GB of per-antenna grids each step, and
         # no CPU baseline over 350 per-antenna beams: device-side numbers only
         args.no_e2e = args.no_cpu_baseline = True
-        # the surrogate of the 350 gridded beams: 1221 Adam steps of 8192 samples (1e7 samples)
+        # the surrogate of the 350 gridded beams: by default 1221 Adam steps of 8192 samples (1e7 samples)
         sim.surrogate_create()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        l0, l1 = sim.surrogate_train(steps=1221, batch=8192, lr0=2e-3, lr1=1e-5, seed=1)
+        l0, l1 = sim.surrogate_train(steps=args.train_steps, batch=8192, lr0=2e-3, lr1=1e-5, seed=1)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         # the gridded path's V on this sample, for the surrogate's modelling error
@@ -268,7 +270,8 @@ def main():
         args.no_autotune = True
         Vg = sim.simulate(w.lsts, w.freqs, args.precision)
         sim.set_beam_surrogate(True)
-        learned = {"train_samples": 1221 * 8192, "train_s": t_train, "train_samples_per_s": 1221 * 8192 / t_train,
+        learned = {"train_samples": args.train_steps * 8192, "train_s": t_train,
+                   "train_samples_per_s": args.train_steps * 8192 / t_train,
                    "loss_first": l0, "loss_last": l1}
     N = w.n_ant
     nf, nax = sim.n_feed, sim._n_ax()
