@@ -42,8 +42,10 @@ constexpr int SMEM_A = 4 * A_PANEL;              // 64 KB
 constexpr int SMEM_W = 4 * W_PANEL_MAX;          // 128 KB
 constexpr int SMEM_O = 4 * O_PANEL;              // 8 KB
 constexpr int SMEM_BIAS = (MAXL + 1) * 256 * 4;  // every layer's biases
+constexpr int MAXF = 128;                         // Fourier frequencies at most
+constexpr int SMEM_FB = MAXF * 16;                // B as float4 rows
 constexpr int NEPI = 16;                          // epilogue warps: four per TMEM lane quadrant
-constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + 256 + 1024;
+constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB + 256 + 1024;
 constexpr int THREADS = (2 + NEPI) * 32;
 
 struct Maps {
@@ -70,6 +72,24 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
+// max(lo, 0) in the low half, max(hi, 0) in the high half, rounded to BF16.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// Registers of a second tcgen05.ld: no use of them may move above the
+// tcgen05.wait::ld that precedes this point.
+__device__ __forceinline__ void keep_after_wait(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&v);
@@ -85,7 +105,8 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     const uint32_t w_base = a_base + SMEM_A;
     const uint32_t o_base = w_base + SMEM_W;
     float* sbias = reinterpret_cast<float*>(smem + SMEM_A + SMEM_W + SMEM_O);  // [layer][256]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS);
+    float4* sB = reinterpret_cast<float4*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS);  // [F] (B_f0, B_f1, B_f2, 0)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB);
     // wfull[4], wfree[4], afull, dfull, ofull
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -112,6 +133,8 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
         const int n = l == D ? 8 : H;
         for (int i = threadIdx.x; i < n; i += blockDim.x) sbias[l * 256 + i] = net.p[net.off_b[l] + i];
     }
+    for (int f = threadIdx.x; f < net.F; f += blockDim.x)
+        sB[f] = make_float4(net.Bf[3 * f], net.Bf[3 * f + 1], net.Bf[3 * f + 2], 0.f);
     if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i) { mbar_init(wfull(i), 1); mbar_init(wfree(i), 1); }
         mbar_init(afull, NEPI);
@@ -199,10 +222,12 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                     float sv[8], cv[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int f = c8 + i;
-                        float ph = net.Bf[3 * f] * x0 + net.Bf[3 * f + 1] * x1 + net.Bf[3 * f + 2] * x2;
+                        const float4 bf = sB[c8 + i];
+                        float ph = bf.x * x0 + bf.y * x1 + bf.z * x2;
                         ph -= rintf(ph);
-                        sincospif(2.f * ph, &sv[i], &cv[i]);
+                        // |2 pi ph| <= pi: the fast sine and cosine are accurate to ~1e-6
+                        // there, far below the BF16 rounding of the features
+                        __sincosf(6.283185307179586f * ph, &sv[i], &cv[i]);
                         if (!valid) sv[i] = cv[i] = 0.f;
                     }
                     st_shared_v4(a_chunk(a_base, r_loc, c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
@@ -227,23 +252,27 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                 if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
                 const float* bias = sbias + l * 256;
-                for (int g = 0; g < H / 128; ++g) {
-                    const int c0 = h * (H / 4) + g * 32;
-                    uint32_t acc[32];
-                    tmem_ld32(trow + c0, acc);
-                    tmem_wait_ld(acc);
+                // this warp's H / 4 columns: both 32-column loads in flight at once
+                uint32_t acc[2][32];
+                const int c00 = h * (H / 4);
+                tmem_ld32(trow + c00, acc[0]);
+                if (H == 256) tmem_ld32(trow + c00 + 32, acc[1]);
+                tmem_wait_ld(acc[0]);
+                if (H == 256) keep_after_wait(acc[1]);
+                auto drain = [&](const uint32_t (&a32)[32], int c0) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j);
                         const float4 b1 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j + 4);
-                        const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                        float v[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) v[i] = fmaxf(__uint_as_float(acc[8 * j + i]) + bb[i], 0.f);
-                        st_shared_v4(a_chunk(a_base, r_loc, c0 + 8 * j), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                     pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+                        st_shared_v4(a_chunk(a_base, r_loc, c0 + 8 * j),
+                                     relu_bf16x2(__uint_as_float(a32[8 * j]) + b0.x, __uint_as_float(a32[8 * j + 1]) + b0.y),
+                                     relu_bf16x2(__uint_as_float(a32[8 * j + 2]) + b0.z, __uint_as_float(a32[8 * j + 3]) + b0.w),
+                                     relu_bf16x2(__uint_as_float(a32[8 * j + 4]) + b1.x, __uint_as_float(a32[8 * j + 5]) + b1.y),
+                                     relu_bf16x2(__uint_as_float(a32[8 * j + 6]) + b1.z, __uint_as_float(a32[8 * j + 7]) + b1.w));
                     }
-                }
+                };
+                drain(acc[0], c00);
+                if (H == 256) drain(acc[1], c00 + 32);
                 tc_fence_before();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -325,7 +354,7 @@ bool make_wmap(CUtensorMap* map, const void* base, int kin, int rows, int box_ro
 
 bool mlp_tc_supported(int F, int E, int H, int depth, int d0p, int n_out) {
     return (H == 128 || H == 256) && depth >= 1 && depth <= MAXL && d0p <= 256 && d0p % 16 == 0 && F % 8 == 0 &&
-           E % 8 == 0 && n_out <= 8 && 2 * F + E <= d0p && get_encode() != nullptr;
+           E % 8 == 0 && n_out <= 8 && 2 * F + E <= d0p && F <= MAXF && get_encode() != nullptr;
 }
 
 cudaError_t mlp_tc_init() {
