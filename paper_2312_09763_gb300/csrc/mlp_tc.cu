@@ -12,15 +12,15 @@
 // h_{l-1} + b_l) for the hidden layers, y = W_out h + b_out.  Operands are
 // BF16, accumulation FP32 in TMEM, as in the training kernels.
 //
-// One persistent CTA per SM walks 128-row tiles.  Warp 0 streams the weight
-// panels (64 input columns x H rows, 128-byte swizzle) with TMA into a ring of
-// four slots; warp 1 owns TMEM and issues the MMAs (M = 128, N = H, K = 16);
-// warps 2..17 (four per TMEM lane quadrant, one per quarter of the columns) write
-// the features, drain each layer's accumulator through bias and ReLU back
-// into the shared-memory activation panels, and write WA from the output
-// layer.  A weight slot is reloaded for the next layer as soon as the MMAs
-// that read it complete, so the weight stream overlaps the MMAs and the
-// epilogue.  Every mbarrier wait is bounded (tc.cuh).
+// One persistent CTA per SM walks 256-row tiles made of two 128-row
+// sub-tiles with their own activation panels and TMEM accumulators (columns 0
+// and 256), so that every weight panel feeds the MMAs of both.  Warp 0 streams
+// the weight panels (64 input columns x H rows, 128-byte swizzle) with TMA
+// through a ring of two slots; warp 1 owns TMEM and issues the MMAs (M = 128,
+// N = H, K = 16); warps 2..17 (one per TMEM lane quadrant, sub-tile and half
+// of the columns) write the features, drain each layer's accumulator through
+// bias and ReLU back into the shared-memory activation panels, and write WA
+// from the output layer.  Every mbarrier wait is bounded (tc.cuh).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -32,14 +32,17 @@ namespace {
 
 using namespace tc;
 
-constexpr int TM = 128;          // rows per tile
+constexpr int TM = 128;          // rows per sub-tile (one TMEM accumulator)
+constexpr int TILE = 2 * TM;     // rows per tile: two sub-tiles share every weight panel
 constexpr int KP = 64;           // input columns per swizzled panel (128 B of BF16)
 constexpr int MAXL = 8;          // hidden layers at most
 constexpr int A_PANEL = TM * 128;                // 16 KB
 constexpr int W_PANEL_MAX = 256 * 128;           // 32 KB (H = 256)
 constexpr int O_PANEL = 16 * 128;                // 2 KB (output rows padded to 16 with zeros)
-constexpr int SMEM_A = 4 * A_PANEL;              // 64 KB
-constexpr int SMEM_W = 4 * W_PANEL_MAX;          // 128 KB
+constexpr int SUB_A = 4 * A_PANEL;               // 64 KB of activations per sub-tile
+constexpr int SMEM_A = 2 * SUB_A;                // 128 KB
+constexpr int NSLOT = 2;                         // weight-panel ring
+constexpr int SMEM_W = NSLOT * W_PANEL_MAX;      // 64 KB
 constexpr int SMEM_O = 4 * O_PANEL;              // 8 KB
 constexpr int SMEM_BIAS = (MAXL + 1) * 256 * 4;  // every layer's biases
 constexpr int MAXF = 128;                         // Fourier frequencies at most
@@ -107,17 +110,18 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     float* sbias = reinterpret_cast<float*>(smem + SMEM_A + SMEM_W + SMEM_O);  // [layer][256]
     float4* sB = reinterpret_cast<float4*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS);  // [F] (B_f0, B_f1, B_f2, 0)
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB);
-    // wfull[4], wfree[4], afull, dfull, ofull
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
+    // wfull[NSLOT], wfree[NSLOT], afull, dfull, ofull
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT + 3);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     auto wfull = [&](int i) { return smem_u32(&bars[i]); };
-    auto wfree = [&](int i) { return smem_u32(&bars[4 + i]); };
-    const uint32_t afull = smem_u32(&bars[8]), dfull = smem_u32(&bars[9]), ofull = smem_u32(&bars[10]);
+    auto wfree = [&](int i) { return smem_u32(&bars[NSLOT + i]); };
+    const uint32_t afull = smem_u32(&bars[2 * NSLOT]), dfull = smem_u32(&bars[2 * NSLOT + 1]),
+                   ofull = smem_u32(&bars[2 * NSLOT + 2]);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int H = net.H, D = net.depth;
     const long long R = (long long)net.n_beam * K;
-    const int n_tiles = (int)((R + TM - 1) / TM);
+    const int n_tiles = (int)((R + TILE - 1) / TILE);
     const int w_panel = H * 128;
     auto panels = [&](int l) { return l == 0 ? (net.d0p + KP - 1) / KP : H / KP; };
     auto ksteps = [&](int l, int pnl) {  // 16-column MMA steps in panel pnl of layer l
@@ -136,7 +140,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     for (int f = threadIdx.x; f < net.F; f += blockDim.x)
         sB[f] = make_float4(net.Bf[3 * f], net.Bf[3 * f + 1], net.Bf[3 * f + 2], 0.f);
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) { mbar_init(wfull(i), 1); mbar_init(wfree(i), 1); }
+        for (int i = 0; i < NSLOT; ++i) { mbar_init(wfull(i), 1); mbar_init(wfree(i), 1); }
         mbar_init(afull, NEPI);
         mbar_init(dfull, 1);
         mbar_init(ofull, 1);
@@ -146,7 +150,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         tc_fence_before();
     }
@@ -159,21 +163,21 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             // output layer once: its 8 rows (one 1 KB swizzle atom per panel)
             mbar_expect_tx(ofull, (uint32_t)((H / KP) * (O_PANEL / 2)));
             for (int pnl = 0; pnl < H / KP; ++pnl) tma_load_2d(o_base + pnl * O_PANEL, &maps.w[D], pnl * KP, 0, ofull);
-            int use[4] = {0, 0, 0, 0};
+            int it = 0;  // weight panels streamed so far (ring position)
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
                 for (int l = 0; l < D && ok; ++l)
-                    for (int pnl = 0; pnl < panels(l); ++pnl) {
-                        if (!wait_bounded(wfree(pnl), ((uint32_t)use[pnl] & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
-                        ++use[pnl];
-                        mbar_expect_tx(wfull(pnl), (uint32_t)w_panel);
-                        tma_load_2d(w_base + pnl * W_PANEL_MAX, &maps.w[l], pnl * KP, 0, wfull(pnl));
+                    for (int pnl = 0; pnl < panels(l); ++pnl, ++it) {
+                        const int sl = it % NSLOT;
+                        if (!wait_bounded(wfree(sl), ((uint32_t)(it / NSLOT) & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
+                        mbar_expect_tx(wfull(sl), (uint32_t)w_panel);
+                        tma_load_2d(w_base + sl * W_PANEL_MAX, &maps.w[l], pnl * KP, 0, wfull(sl));
                     }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t id_hidden = idesc_f16(false, TM, H), id_out = idesc_f16(false, TM, 16);
-            int use[4] = {0, 0, 0, 0};
+            int it = 0;
             int na = 0;
             bool ok = wait_bounded(ofull, 0u, abort_flag, err);
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
@@ -183,16 +187,22 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                     const bool out = l == D;
                     const int np = out ? H / KP : panels(l);
                     for (int pnl = 0; pnl < np; ++pnl) {
+                        const int sl = it % NSLOT;
                         if (!out) {
-                            if (!wait_bounded(wfull(pnl), (uint32_t)(use[pnl]++) & 1u, abort_flag, err)) { ok = false; break; }
+                            if (!wait_bounded(wfull(sl), (uint32_t)(it / NSLOT) & 1u, abort_flag, err)) { ok = false; break; }
                             tc_fence_after();
                         }
-                        const uint32_t b0 = out ? o_base + pnl * O_PANEL : w_base + pnl * W_PANEL_MAX;
+                        const uint32_t b0 = out ? o_base + pnl * O_PANEL : w_base + sl * W_PANEL_MAX;
                         const int ns = out ? KP / 16 : ksteps(l, pnl);
-                        for (int kk = 0; kk < ns; ++kk)
-                            tc_mma(tmem, sdesc(a_base + pnl * A_PANEL + kk * 32), sdesc(b0 + kk * 32),
-                                   out ? id_out : id_hidden, (pnl | kk) != 0 ? 1u : 0u);
-                        if (!out) tc_commit(wfree(pnl));
+                        // both sub-tiles from the same weight panel (accumulators at columns 0 and 256)
+                        for (int u = 0; u < 2; ++u)
+                            for (int kk = 0; kk < ns; ++kk)
+                                tc_mma(tmem + (uint32_t)(u * 256), sdesc(a_base + u * SUB_A + pnl * A_PANEL + kk * 32),
+                                       sdesc(b0 + kk * 32), out ? id_out : id_hidden, (pnl | kk) != 0 ? 1u : 0u);
+                        if (!out) {
+                            tc_commit(wfree(sl));
+                            ++it;
+                        }
                     }
                     if (!ok) break;
                     tc_commit(dfull);
@@ -200,25 +210,26 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             }
         }
     } else {
-        // epilogue warps: lane quadrant q, column quarter h
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        const int r_loc = q * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        // epilogue warps: lane quadrant q, sub-tile u, column half h
+        const int q = warp & 3, u = ((warp - 2) >> 2) & 1, h = (warp - 2) >> 3;
+        const int r_loc = q * 32 + lane;  // row within the sub-tile
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * 256);
+        const uint32_t ab = a_base + u * SUB_A;
         const int F = net.F, E = net.E;
         int nd = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            const long long r = (long long)tile * TM + r_loc;
+            const long long r = (long long)tile * TILE + u * TM + r_loc;
             const bool valid = r < R;
             const int b = valid ? (int)(r / K) : 0, s = valid ? (int)(r % K) : 0;
-            // ---- input features of row r: chunks of 8 columns, chunk c by quarter c % 4
+            // ---- input features of row r: chunks of 8 columns, chunk c by half c % 2
             {
                 float2 azza = make_float2(0.f, 0.f);
                 if (valid) azza = lt.azza[(long long)t * lt.pitch + s];
                 const float x0 = azza.x * 0.15915494309189535f;   // az / 2 pi
                 const float x1 = azza.y * 0.63661977236758134f;   // za / (pi / 2)
                 const float x2 = (nu - net.nu_mid) / net.nu_half;
-                for (int c8 = 8 * h; c8 < F; c8 += 32) {
+                for (int c8 = 8 * h; c8 < F; c8 += 16) {
                     float sv[8], cv[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -230,17 +241,17 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                         __sincosf(6.283185307179586f * ph, &sv[i], &cv[i]);
                         if (!valid) sv[i] = cv[i] = 0.f;
                     }
-                    st_shared_v4(a_chunk(a_base, r_loc, c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
+                    st_shared_v4(a_chunk(ab, r_loc, c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
                                  pack_bf16(sv[4], sv[5]), pack_bf16(sv[6], sv[7]));
-                    st_shared_v4(a_chunk(a_base, r_loc, F + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
+                    st_shared_v4(a_chunk(ab, r_loc, F + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
                                  pack_bf16(cv[4], cv[5]), pack_bf16(cv[6], cv[7]));
                 }
                 const float* e = net.p + net.off_emb + (long long)b * E;
-                for (int c8 = 8 * h; c8 < net.d0p - 2 * F; c8 += 32) {
+                for (int c8 = 8 * h; c8 < net.d0p - 2 * F; c8 += 16) {
                     float v[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) v[i] = valid && c8 + i < E ? e[c8 + i] : 0.f;
-                    st_shared_v4(a_chunk(a_base, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                    st_shared_v4(a_chunk(ab, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
                                  pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
                 }
             }
@@ -252,27 +263,28 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                 if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
                 const float* bias = sbias + l * 256;
-                // this warp's H / 4 columns: both 32-column loads in flight at once
-                uint32_t acc[2][32];
-                const int c00 = h * (H / 4);
-                tmem_ld32(trow + c00, acc[0]);
-                if (H == 256) tmem_ld32(trow + c00 + 32, acc[1]);
-                tmem_wait_ld(acc[0]);
-                if (H == 256) keep_after_wait(acc[1]);
+                // this warp's H / 2 columns, two 32-column TMEM loads in flight at a time
                 auto drain = [&](const uint32_t (&a32)[32], int c0) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j);
                         const float4 b1 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j + 4);
-                        st_shared_v4(a_chunk(a_base, r_loc, c0 + 8 * j),
+                        st_shared_v4(a_chunk(ab, r_loc, c0 + 8 * j),
                                      relu_bf16x2(__uint_as_float(a32[8 * j]) + b0.x, __uint_as_float(a32[8 * j + 1]) + b0.y),
                                      relu_bf16x2(__uint_as_float(a32[8 * j + 2]) + b0.z, __uint_as_float(a32[8 * j + 3]) + b0.w),
                                      relu_bf16x2(__uint_as_float(a32[8 * j + 4]) + b1.x, __uint_as_float(a32[8 * j + 5]) + b1.y),
                                      relu_bf16x2(__uint_as_float(a32[8 * j + 6]) + b1.z, __uint_as_float(a32[8 * j + 7]) + b1.w));
                     }
                 };
-                drain(acc[0], c00);
-                if (H == 256) drain(acc[1], c00 + 32);
+                for (int c00 = h * (H / 2); c00 < (h + 1) * (H / 2); c00 += 64) {
+                    uint32_t acc[2][32];
+                    tmem_ld32(trow + c00, acc[0]);
+                    tmem_ld32(trow + c00 + 32, acc[1]);
+                    tmem_wait_ld(acc[0]);
+                    keep_after_wait(acc[1]);
+                    drain(acc[0], c00);
+                    drain(acc[1], c00 + 32);
+                }
                 tc_fence_before();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
