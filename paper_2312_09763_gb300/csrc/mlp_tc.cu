@@ -42,6 +42,7 @@ constexpr int O_PANEL = 16 * 128;                // 2 KB (output rows padded to 
 constexpr int SUB_A = 4 * A_PANEL;               // 64 KB of activations per sub-tile
 constexpr int SMEM_A = 2 * SUB_A;                // 128 KB
 constexpr int NSLOT = 2;                         // weight-panel ring
+constexpr int TMEM_COLS = 512;                   // two 256-column accumulators
 constexpr int SMEM_W = NSLOT * W_PANEL_MAX;      // 64 KB
 constexpr int SMEM_O = 4 * O_PANEL;              // 8 KB
 constexpr int SMEM_BIAS = (MAXL + 1) * 256 * 4;  // every layer's biases
@@ -150,7 +151,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(512));
+                     "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         tc_fence_before();
     }
@@ -346,7 +347,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
