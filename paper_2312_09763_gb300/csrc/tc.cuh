@@ -44,19 +44,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait: false if the wait gave up (timeout or another role aborted).
+// try_wait that may suspend the thread in hardware until the phase completes
+// or about ns nanoseconds pass, so that waiting warps do not take issue slots
+// from the warps doing work.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
-    unsigned long long t0 = 0;
-    for (uint32_t i = 0;; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63u) == 63u) {
-            if (*abort_flag) return false;
-            const unsigned long long now = gtimer();
-            if (t0 == 0) t0 = now;
-            else if (now - t0 > kTimeoutNs) {
-                *abort_flag = 1;
-                atomicCAS(err, 0, (int)kDevTimeout);
-                return false;
-            }
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            atomicCAS(err, 0, (int)kDevTimeout);
+            return false;
         }
     }
 }
