@@ -36,6 +36,10 @@ sys.path.insert(0, ROOT)
 # 1e5-source workload in FP16x3: one ncu capture of 16 instances (2.4454 GB),
 # summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
 HERK_DRAM_BYTES_PER_INSTANCE = 2.4454e9 / 16
+# The same for the HERK launch that also builds the next batch's U planes
+# (k_herk_tc<128, 2, 1, 1>): 2.9755 GB read + 2.2701 GB written for 16 + 16
+# instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
+FUSED_DRAM_BYTES_PER_INSTANCE = (2.9755e9 + 2.2701e9) / 16
 METRIC = "vis/s (bl·chan·time) at 350 ant×1e5 src; split-prec TC vs FP32 @1e-5 rel err"
 UNIT = "vis/s"
 
@@ -322,14 +326,28 @@ def main():
         # triangle of the 2N x 2N real Gram matrix, for every instance
         flops_step = float(np.sum(3 * 2.0 * rows * (rows + 1) / 2 * K))
         achieved = flops_step * args.steps / (ms_h / 1e3) / 1e12
+        # with the fused Z build (the default for 128-column tiles) the timed
+        # HERK launches also write the next batch's U planes
+        fused = not args.no_fuse and tuning is not None and tuning.get("tile_n") == 128 and nf == nax
         traffic = None
-        if (args.workload == "hera" and not args.small and args.precision == "fp16x3" and tuning
-                and tuning.get("tile_n") == 128):
-            traffic = HERK_DRAM_BYTES_PER_INSTANCE * n_instances(w, pairs) / max(n_h / args.steps, 1)
+        if args.workload == "hera" and not args.small and args.precision == "fp16x3" and tuning \
+                and tuning.get("tile_n") == 128:
+            per = FUSED_DRAM_BYTES_PER_INSTANCE if fused else HERK_DRAM_BYTES_PER_INSTANCE
+            traffic = per * n_instances(w, pairs) / max(n_h / args.steps, 1)
         roof = {"bound": "tensor", "achieved": achieved, "peak": sustained, "unit": "TFLOP/s",
                 "frac": achieved / sustained, "traffic": traffic, "traffic_unit": "B per launch",
-                "kernel": "k_herk_tc", "launches": n_h, "avg_launch_ms": ms_h / max(n_h, 1),
+                "kernel": "k_herk_tc" + (" (fused with the next batch's Z build)" if fused else ""),
+                "launches": n_h, "avg_launch_ms": ms_h / max(n_h, 1),
                 "peak_source": f"{src} bf16 sustained (kernel timed inside a long step)"}
+        if fused:
+            # its second bound: the U planes written (next batch) and read (this
+            # batch) once each, hi + lo halves
+            kpad = np.ceil(K / 256.0) * 256
+            z_bytes = float(np.sum(rows * kpad * 4.0))
+            roof["hbm_bytes_per_step"] = 2 * z_bytes
+            roof["hbm_achieved_gbs"] = 2 * z_bytes * args.steps / (ms_h / 1e3) / 1e9
+            roof["hbm_frac"] = roof["hbm_achieved_gbs"] / hbm
+            roof["hbm_peak_gbs"] = hbm
     if learned is not None:
         # the surrogate's forward pass dominates: 2 x multiply-adds per row of
         # the network, one row per (antenna beam, live source) of each instance
