@@ -37,9 +37,9 @@ sys.path.insert(0, ROOT)
 # summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
 HERK_DRAM_BYTES_PER_INSTANCE = 2.4454e9 / 16
 # The same for the HERK launch that also builds the next batch's U planes
-# (k_herk_tc<128, 2, 1, 1>): 2.9755 GB read + 2.2701 GB written for 16 + 16
+# (k_herk_tc<128, 2, 1, 1>): 3.4525 GB read + 2.2655 GB written for 16 + 16
 # instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
-FUSED_DRAM_BYTES_PER_INSTANCE = (2.9755e9 + 2.2701e9) / 16
+FUSED_DRAM_BYTES_PER_INSTANCE = (3.4525e9 + 2.2655e9) / 16
 METRIC = "vis/s (bl·chan·time) at 350 ant×1e5 src; split-prec TC vs FP32 @1e-5 rel err"
 UNIT = "vis/s"
 
