@@ -181,10 +181,12 @@ mv_status mv_simulate_pairs(mv_ctx *ctx, int n_pairs, const double *lst, const d
  * project's own and its tile width, source-axis split and flush interval are
  * tuned).  Runs the first batch of the call (mv_simulate's plan, or
  * mv_simulate_pairs' plan if pairs != 0 with n_t == n_nu pairs), times the
- * HERK of that batch under each candidate with CUDA events on the context's
- * stream, and keeps the fastest for later calls with the same matrix size,
- * batch size and precision.  Synchronises.  prec must be a tensor-core
- * precision.  out may be NULL. */
+ * HERK of that batch under each candidate (tile width 128 or 256 -- 128 only
+ * when the Z build is fused, and then every trial also builds a batch of Z
+ * planes --, split of the source axis 1 to 64, flush every 4, 8 or 16
+ * k-blocks) with CUDA events on the context's stream, and keeps the fastest
+ * for later calls with the same matrix size, batch size and precision.
+ * Synchronises.  prec must be a tensor-core precision.  out may be NULL. */
 mv_status mv_autotune(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const double *nu,
                       mv_precision prec, int pairs, mv_tuning *out);
 

@@ -759,7 +759,7 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
     const std::vector<int> widths = p.fuse ? std::vector<int>{128} : std::vector<int>{128, 256};
     for (int bn : widths)
         for (int split : {1, 2, 4, 8, 16, 32, 64})
-            for (int flush : {4, 8}) {
+            for (int flush : {4, 8, 16}) {
                 if (split > 1 && est_kb / split < 8) continue;
                 HerkCfg h;
                 h.bn = bn;
