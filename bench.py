@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
     ap.add_argument("--max-batch", type=int, default=0, help="instances per launch (mv_options.max_batch; 0 = auto)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="scaling sweep instead of the benchmark line: time per instance over sources 2^10..2^19 "
+                         "x antennas 2^3..2^8 (one LST x 16 channels each), one JSON line per point")
     ap.add_argument("--train-steps", type=int, default=1221,
                     help="learned workload: Adam steps of 8192 samples (default 1221, i.e. 1e7 samples)")
     ap.add_argument("--no-fuse", action="store_true", help="Z build as its own launch (mv_options.fuse_zbuild = 0)")
@@ -236,11 +239,48 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def sweep(args):
+    """Runtime against catalogue size and array size (the shape of the paper's
+    scaling tests, Sec. 4.3): HERA-like arrays of 2^3..2^8 antennas and uniform
+    skies of 2^10..2^19 sources, one LST x 16 channels, FP16x3 (or --precision),
+    CUDA events around warm simulate calls."""
+    import torch
+    from paper_2312_09763_gb300 import Simulator, synth
+    torch.cuda.set_device(0)
+    for lg_ant in range(3, 9):
+        for lg_src in range(10, 20, 3):
+            w = synth.hera_like(n_ant=2 ** lg_ant, n_src=2 ** lg_src, n_chan=16, n_times=1, n_za=46, n_az=120)
+            sim = Simulator(0)
+            sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
+            sim.set_beam(w.beam)
+            sim.set_antennas(w.enu, None, w.lat)
+            V = torch.empty((1, 16, w.n_ant, w.n_ant), dtype=torch.complex64, device="cuda")
+            for _ in range(3):
+                sim.simulate(w.lsts, w.freqs, args.precision, out=V)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 10
+            for _ in range(reps):
+                sim.simulate(w.lsts, w.freqs, args.precision, out=V)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps / 16
+            live = int(sim.last_live_counts(16)[0])
+            print(json.dumps({"sweep": True, "n_ant": w.n_ant, "n_src": w.n_src, "live": live,
+                              "precision": args.precision, "ms_per_instance": ms,
+                              "vis_per_s": w.n_ant * (w.n_ant + 1) / 2 / (ms / 1e3)}), flush=True)
+            sim.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sweep:
+        sweep(args)
         return
     import torch
     from paper_2312_09763_gb300 import Simulator
