@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Plain numpy in float64,
 written from the definitions below; it shares nothing with the CUDA library.
 
 The paper's beams are gridded (UVBeam) or analytic (Sec. 2.4); a learned
-surrogate of a per-antenna gridded beam is an extension of this build, so the
+surrogate of per-antenna gridded beams is not in the paper, so the
 definitions here are the surrogate's own:
 
   coordinates   x = (az / 2 pi, za / (pi/2), (nu - nu_mid) / nu_half)
