@@ -5,8 +5,8 @@ beam grids, LST and frequency lists.  It holds none of the simulator's
 arithmetic, imports nothing else from this package, and feeds the same arrays
 to the CUDA path and to the FP64 oracle.
 
-Every quantity draws from its own stream, keyed by (20231209 + workload id,
-quantity name), so that changing one quantity never shifts another.
+Every quantity draws from its own stream, keyed by (20231209 + a per-workload
+offset, quantity name), so that changing one quantity never shifts another.
 
 The paper's own inputs (a GLEAM-like catalogue, the GSM, the CST HERA beam;
 Sec. 5.1) are not available; these stand in for them with the counts, flux
@@ -14,11 +14,11 @@ distributions and beam widths of the workloads below.
 
 Workloads (all angles in radians, frequencies in Hz, lengths in metres):
 
-0. tiny: 10 antennas uniform in a 50 m square (Up = 0); 1000 sources uniform on
+* tiny: 10 antennas uniform in a 50 m square (Up = 0); 1000 sources uniform on
    the sphere, dN/dS ~ S^-1.6 on [0.1, 10] Jy, flat spectra; 1 channel at
    150 MHz; 4 LSTs spanning 10 min; latitude -30.7 deg; analytic Gaussian
    E-field beam, FWHM 10 deg.
-1. HERA-like: 350 antennas, the triangular-lattice points (14.6 m spacing)
+* HERA-like: 350 antennas, the triangular-lattice points (14.6 m spacing)
    nearest the origin; 1e5 sources uniform on the sphere, dN/dS ~ S^-1.6 on
    [0.01, 100] Jy, spectral index ~ N(-0.8, 0.2) about 150 MHz; 64 channels
    centred in 100-200 MHz; 60 LSTs one minute apart; scalar gridded beam on a
@@ -170,7 +170,7 @@ class Workload:
 
 
 def tiny(n_ant: int = 10, n_src: int = 1000, n_times: int = 4) -> Workload:
-    """Workload 0 (see module docstring)."""
+    """The tiny workload (module docstring)."""
     enu = square_array(n_ant, 50.0, rng(0, "antennas"))
     ra, dec = uniform_sphere(n_src, rng(0, "positions"))
     flux = powerlaw_flux(n_src, 0.1, 10.0, 1.6, rng(0, "flux"))
@@ -182,7 +182,7 @@ def tiny(n_ant: int = 10, n_src: int = 1000, n_times: int = 4) -> Workload:
 
 def hera_like(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times: int = 60,
               n_za: int = 91, n_az: int = 360) -> Workload:
-    """Workload 1 (see module docstring); smaller sizes give its test cases."""
+    """The HERA-like workload (module docstring); smaller sizes give its test cases."""
     enu = hex_array(n_ant, 14.6)
     ra, dec = uniform_sphere(n_src, rng(1, "positions"))
     flux = powerlaw_flux(n_src, 0.01, 100.0, 1.6, rng(1, "flux"))
@@ -198,11 +198,11 @@ def hera_like(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times:
 
 def batched_uneven(n_pairs: int = 256, n_ant: int = 350, n_src: int = 100_000, n_za: int = 91,
                    n_az: int = 360) -> Workload:
-    """Workload 3: n_pairs (LST, frequency) pairs, LST ~ U[0, 24 h) and
+    """Batched uneven instances: n_pairs (LST, frequency) pairs, LST ~ U[0, 24 h) and
     nu ~ U[50, 250] MHz, for the HERA-like array; the sky is 40 % uniform and
     60 % von Mises-Fisher clustered (kappa = 20) about RA 6 h, Dec = latitude,
     so the horizon cut leaves about 20k-80k live sources depending on LST;
-    fluxes and spectra as workload 1; the beam of workload 1 on 48-252 MHz.
+    fluxes and spectra as the HERA-like workload; its beam on 48-252 MHz.
     `lsts` and `freqs` hold the pairs (equal length)."""
     enu = hex_array(n_ant, 14.6)
     n_uni = int(round(0.4 * n_src))
@@ -249,7 +249,7 @@ def dipole_feed_offset_grids(n_ant: int, nu_grid: np.ndarray, n_za: int, n_az: i
 
 def learned_beam(n_ant: int = 350, n_src: int = 100_000, n_chan: int = 64, n_times: int = 60, n_za: int = 91,
                  n_az: int = 360, dnu: float = 1e6, nu_lo: float = 98e6, nu_hi: float = 202e6) -> Workload:
-    """Workload 4: the HERA-like array and sky of workload 1 with one beam per
+    """Learned-beam workload: the HERA-like array and sky with one beam per
     antenna (dipole_feed_offset_grids on a 1 deg x 1 deg x 1 MHz grid over
     98-202 MHz, or [nu_lo, nu_hi] for samples of it), the setting where a
     learned surrogate replaces n_ant grids."""
@@ -341,7 +341,7 @@ def gaussian_random_field(theta: np.ndarray, phi: np.ndarray, lmax: int, cl: np.
 
 def polarised_diffuse(n_ant: int = 350, nside: int = 128, n_chan: int = 32, n_times: int = 120,
                       n_za: int = 91, n_az: int = 360, lmax: int = None, full_stokes: bool = False) -> Workload:
-    """Workload 2: the HERA-like array, a diffuse sky of 12 nside^2 HEALPix
+    """Polarised diffuse workload: the HERA-like array, a diffuse sky of 12 nside^2 HEALPix
     pixel centres whose intensities are a log-normal Gaussian random field
     (C_l ~ l^-2.5 for l >= 1, C_0 = 0, field normalised to unit variance)
     turned into fluxes (intensity x pixel area, about 1e3 Jy in total, spectral
