@@ -113,3 +113,33 @@ def test_simulate_with_the_surrogate_matches_oracle_with_same_network(tmp_path):
     sim2 = simulator(w)
     sim2.surrogate_load(path, **sim._mlp)
     assert np.array_equal(sim2.surrogate_eval([0, 5], [0.3, 1.0], [0.2, 0.7], [150e6, 160e6]), y0)
+
+
+def test_surrogate_with_a_polarised_sky():
+    # the tensor-core forward pass applies the coherency square root to the
+    # network's Jones terms (eq. "fullz"); same network on both sides
+    w = workload(n_ant=12, n_src=3000)
+    g = np.random.default_rng(5)
+    d = g.normal(size=(3, w.n_src))
+    w.stokes_quv = d * (0.5 * g.uniform(0, 1, w.n_src) * w.flux_ref / np.linalg.norm(d, axis=0))
+    sim = simulator(w)
+    sim.surrogate_create()
+    sim.surrogate_train(steps=300, batch=8192, lr0=2e-3, lr1=1e-5, seed=3)
+    net = oracle_net(sim, *grid_meta(w))
+    sim.set_beam_surrogate(True)
+    V = sim.simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+    P = oracle_problem(w)
+    for ic, f in enumerate(w.freqs):
+        def beam_fn(az, za, nu):
+            n = az.size
+            out = np.empty((w.n_ant, 2, 2, n), dtype=np.complex128)
+            for b in range(w.n_ant):
+                y = mlp.forward(net, np.full(n, b), az, za, np.full(n, nu))
+                out[b] = (y[:, 0::2] + 1j * y[:, 1::2]).T.reshape(2, 2, n)
+            return out
+        Vo = oracle.vis_with_beam_fn(P, w.lsts[0], f, beam_fn)
+        assert rel_err(V[0, ic], Vo) <= 3e-2, ic
+    # and the polarisation matters at this level
+    P.stokes_quv = None
+    Vu = oracle.vis_with_beam_fn(P, w.lsts[0], w.freqs[0], beam_fn)
+    assert rel_err(V[0, 0], Vu) > 0.02
