@@ -66,6 +66,9 @@ struct mv_ctx {
     Buf wa[2], amax[2], u[2], ulo[2], aph[2];
     cudaStream_t zstream = nullptr;
     cudaEvent_t ev_prep = nullptr, ev_zdone[2] = {nullptr, nullptr}, ev_hdone[2] = {nullptr, nullptr};
+    // copies of each batch's V to pinned host memory, overlapping the next batches
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_vdone = nullptr, ev_cdone = nullptr;
     int n_sms = 148;
     long long model_version = 0;  // bumped by every set-up call (kernel arguments embed the model)
     // autotuned HERK configuration, valid for calls of the same shape
@@ -345,6 +348,7 @@ struct Prepared {
     long long pitch = 0, k_pitch = 0;
     LiveTables lt{};
     float2* Vout = nullptr;
+    float2* Vhost = nullptr;  // page-locked host V (copied per batch on cstream), or NULL
     size_t v_bytes = 0;
 };
 
@@ -489,9 +493,15 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
         return s;
     p.Vout = static_cast<float2*>(V);
     p.v_bytes = sizeof(float2) * (size_t)p.n_inst * p.N * p.N;
+    p.Vhost = nullptr;
     if (!V_on_device) {
         if ((s = ensure(c, c->vdev, p.v_bytes))) return s;
         p.Vout = static_cast<float2*>(c->vdev.p);
+        // page-locked host output: each batch's V is copied as soon as its HERK ends
+        cudaPointerAttributes pa{};
+        if (cudaPointerGetAttributes(&pa, V) == cudaSuccess && pa.type == cudaMemoryTypeHost)
+            p.Vhost = static_cast<float2*>(V);
+        cudaGetLastError();
     }
     LiveTables& lt = p.lt;
     lt.e = (double*)c->le.p;
@@ -588,6 +598,25 @@ mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int 
 mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStream_t st, long long* L) {
     mv_status s;
     const Model& m = c->model;
+    // page-locked host output: the batch's V (contiguous instances) goes to the
+    // host on cstream once the HERK queued before this point on st is done
+    auto copy_out = [&](const Plan::Batch& b) -> mv_status {
+        if (!p.Vhost) return MV_OK;
+        const long long off = P.inst[b.inst0].v_off;
+        const size_t bytes = sizeof(float2) * (size_t)b.n * p.N * p.N;
+        mv_status s2;
+        if ((s2 = cuda_check(cudaEventRecord(c->ev_vdone, st), "event"))) return s2;
+        if ((s2 = cuda_check(cudaStreamWaitEvent(c->cstream, c->ev_vdone, 0), "event wait"))) return s2;
+        return cuda_check(cudaMemcpyAsync(p.Vhost + off, p.Vout + off, bytes, cudaMemcpyDeviceToHost, c->cstream),
+                          "copy V to host");
+    };
+    // st waits for the copies (they also join a stream capture)
+    auto join_copies = [&]() -> mv_status {
+        if (!p.Vhost) return MV_OK;
+        mv_status s2;
+        if ((s2 = cuda_check(cudaEventRecord(c->ev_cdone, c->cstream), "event"))) return s2;
+        return cuda_check(cudaStreamWaitEvent(st, c->ev_cdone, 0), "event wait");
+    };
     Timed tc0(c, MV_KERNEL_CULL, st);
     cudaError_t e = launch_cull(m, (const double*)c->R.p, p.n_times, p.lt, (int*)c->counts.p, (int*)c->offsets.p,
                                 p.bpt, st, L);
@@ -626,8 +655,9 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
             e = enqueue_herk(c, p, P.batches[i], h, k, st, L, next ? &zj : nullptr);
             th.end();
             if ((s = launched(e, "HERK tc", st))) return s;
+            if ((s = copy_out(P.batches[i]))) return s;
         }
-        return MV_OK;
+        return join_copies();
     }
     if (p.nbuf == 1) {
         for (const auto& b : P.batches) {
@@ -636,8 +666,9 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
             e = enqueue_herk(c, p, b, h, 0, st, L);
             th.end();
             if ((s = launched(e, p.zprec == 0 ? "HERK fp32" : "HERK tc", st))) return s;
+            if ((s = copy_out(b))) return s;
         }
-        return MV_OK;
+        return join_copies();
     }
     // Two workspace sets: batch b builds Z into set b % 2 on zstream while the
     // HERK of batch b - 1 reads the other set on st.  zstream first waits for
@@ -658,14 +689,16 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
         th.end();
         if ((s = launched(e, p.zprec == 0 ? "HERK fp32" : "HERK tc", st))) return s;
         if ((s = cuda_check(cudaEventRecord(c->ev_hdone[k], st), "event"))) return s;
+        if ((s = copy_out(b))) return s;
     }
-    return MV_OK;
+    return join_copies();
 }
 
 // Key of a captured launch sequence: every value its kernel arguments depend on.
 std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, const HerkCfg& h) {
     std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch, p.nbuf,
-                                p.fuse, h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout, c->model_version};
+                                p.fuse, h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout,
+                                (long long)(uintptr_t)p.Vhost, c->model_version};
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
                          &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
                          &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err,
@@ -724,7 +757,8 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     c->last_inst_t.clear();
     for (auto& in : P.inst) c->last_inst_t.push_back(in.t);
     if (!V_on_device) {
-        if ((s = cuda_check(cudaMemcpyAsync(V, p.Vout, p.v_bytes, cudaMemcpyDeviceToHost, st), "copy V to host")))
+        if (!p.Vhost &&
+            (s = cuda_check(cudaMemcpyAsync(V, p.Vout, p.v_bytes, cudaMemcpyDeviceToHost, st), "copy V to host")))
             return s;
         if ((s = cuda_check(cudaStreamSynchronize(st), "synchronize"))) return s;
         int herr = 0;
@@ -871,6 +905,9 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
     }
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->zstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_vdone, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_cdone, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_zdone[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_zdone[1], cudaEventDisableTiming) != cudaSuccess ||
@@ -904,9 +941,11 @@ void mv_destroy(mv_ctx* c) {
     harvest(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    for (cudaEvent_t e : {c->ev_prep, c->ev_zdone[0], c->ev_zdone[1], c->ev_hdone[0], c->ev_hdone[1]})
+    for (cudaEvent_t e : {c->ev_prep, c->ev_zdone[0], c->ev_zdone[1], c->ev_hdone[0], c->ev_hdone[1], c->ev_vdone,
+                          c->ev_cdone})
         if (e) cudaEventDestroy(e);
     if (c->zstream) cudaStreamDestroy(c->zstream);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
