@@ -104,6 +104,14 @@ struct Unit {
     int part;  // index of the unit's partial tile: (slot n_tiles + tile) S + ks
 };
 
+// A diagonal tile's A rows [ti BM, ti BM + BM) lie inside its B rows
+// [tj BN, tj BN + BN): the tile loads B only and reads A from B's 128-row
+// half diag_half (-1: not a diagonal tile).
+template <int BN>
+__host__ __device__ __forceinline__ int diag_half(int ti, int tj) {
+    return (ti * BM) / BN == tj ? (ti * BM - tj * BN) / BM : -1;
+}
+
 template <int BN>
 __device__ __forceinline__ Unit decode_unit(int u, int n_tiles, int S, const int* __restrict__ order,
                                             const Inst* __restrict__ inst, int inst0, const LiveTables& lt,
@@ -206,16 +214,19 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 mbar_arrive(qfull(q));
                 if (u < 0) break;
                 const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+                const bool diag = diag_half<BN>(w.ti, w.tj) >= 0;
                 bool ok = true;
                 for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!wait_bounded(empty(s), ph ^ 1u, abort_flag, err)) { ok = false; break; }
-                    mbar_expect_tx(full(s), STAGE_BYTES);
+                    mbar_expect_tx(full(s), diag ? 2 * B_BYTES : STAGE_BYTES);
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     const int x = kb * BK;
-                    tma_load_3d(st, &map_hi, x, w.ti * BM, w.slot, full(s));
-                    tma_load_3d(st + A_BYTES, &map_lo, x, w.ti * BM, w.slot, full(s));
+                    if (!diag) {
+                        tma_load_3d(st, &map_hi, x, w.ti * BM, w.slot, full(s));
+                        tma_load_3d(st + A_BYTES, &map_lo, x, w.ti * BM, w.slot, full(s));
+                    }
 #pragma unroll
                     for (int h = 0; h < BN / 128; ++h) {
                         tma_load_3d(st + 2 * A_BYTES + h * 16384, &map_hi, x, w.tj * BN + h * 128, w.slot, full(s));
@@ -236,6 +247,10 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 mbar_arrive(qempty(q));
                 if (u < 0) break;
                 const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+                // A's offset in the stage: its own slot, or the matching half of B
+                const int dh = diag_half<BN>(w.ti, w.tj);
+                const uint32_t a_off = dh < 0 ? 0u : (uint32_t)(2 * A_BYTES + dh * 16384);
+                const uint32_t a_lo_off = dh < 0 ? (uint32_t)A_BYTES : a_off + (uint32_t)B_BYTES;
                 bool ok = true;
                 for (int kc = w.kb0; kc < w.kb1 && ok; kc += flush, ++cg) {
                     const int buf = cg & 1;
@@ -253,8 +268,8 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                         const uint32_t st = sbase + s * STAGE_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint64_t a_hi = sdesc(st + kk * 32);
-                            const uint64_t a_lo = sdesc(st + A_BYTES + kk * 32);
+                            const uint64_t a_hi = sdesc(st + a_off + kk * 32);
+                            const uint64_t a_lo = sdesc(st + a_lo_off + kk * 32);
                             const uint64_t b_hi = sdesc(st + 2 * A_BYTES + kk * 32);
                             const uint64_t b_lo = sdesc(st + 2 * A_BYTES + B_BYTES + kk * 32);
                             tc_mma(d, a_hi, b_hi, idesc, acc);

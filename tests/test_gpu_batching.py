@@ -120,15 +120,18 @@ def test_autotune_then_simulate():
 def test_page_locked_host_output_per_batch(prec):
     # a page-locked host output gets each batch's V copied on a side stream as
     # soon as that batch's HERK ends; a pageable one gets a single copy at the
-    # end.  Both hold exactly the device result, in every batching mode.
+    # end.  Both hold exactly the device result, in every batching mode (one
+    # HERK configuration: the split of the source axis decides the summation
+    # order).
     import torch
     w = synth.hera_like(n_ant=90, n_src=12_000, n_chan=6, n_times=3, n_za=46, n_az=120)
     shape = (3, 6, 90, 90)
-    ref = simulator(w, max_batch=4).simulate(w.lsts, w.freqs, prec).cpu().numpy()
+    kw = dict(max_batch=4, herk_tile_n=128, herk_split=2)
+    ref = simulator(w, **kw).simulate(w.lsts, w.freqs, prec).cpu().numpy()
     modes = [dict(), dict(fuse_zbuild=False), dict(fuse_zbuild=False, overlap_batches=True)]
     for mode in modes:
         for use_graph in (False, True):
-            sim = simulator(w, max_batch=4, use_graph=use_graph, **mode)
+            sim = simulator(w, use_graph=use_graph, **kw, **mode)
             for _ in range(2):
                 pinned = torch.full(shape, complex(np.nan, np.nan), dtype=torch.complex64).pin_memory()
                 sim.simulate(w.lsts, w.freqs, prec, out=pinned, host=True)
