@@ -49,7 +49,11 @@ constexpr int SMEM_BIAS = (MAXL + 1) * 256 * 4;  // every layer's biases
 constexpr int MAXF = 128;                         // Fourier frequencies at most
 constexpr int SMEM_FB = MAXF * 16;                // B as float4 rows
 constexpr int NEPI = 16;                          // epilogue warps: four per TMEM lane quadrant
-constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB + 256 + 1024;
+// per-row values gathered ahead of use with cp.async: the next tile's (az, za)
+// for every epilogue thread, and (m00, Re m10, Im m10, m11) or (flux, 0, 0, 0)
+// plus the spectral index of this tile's sources for the WA writers
+constexpr int SMEM_GATHER = NEPI * 32 * 8 + TILE * 16 + TILE * 4;
+constexpr int SMEM_BYTES = SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB + SMEM_GATHER + 256 + 1024;
 constexpr int THREADS = (2 + NEPI) * 32;
 
 struct Maps {
@@ -85,14 +89,20 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
 
 // Registers of a second tcgen05.ld: no use of them may move above the
 // tcgen05.wait::ld that precedes this point.
-__device__ __forceinline__ void keep_after_wait(uint32_t (&r)[32]) {
+__device__ __forceinline__ void keep_after_wait16(uint32_t (&r)[16]) {
     asm volatile(""
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+                   "+r"(r[15]));
 }
+
+// Ampere-style asynchronous global -> shared copies of 4, 8 or 16 bytes.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t saddr, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(saddr), "l"(g), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -110,7 +120,11 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     const uint32_t o_base = w_base + SMEM_W;
     float* sbias = reinterpret_cast<float*>(smem + SMEM_A + SMEM_W + SMEM_O);  // [layer][256]
     float4* sB = reinterpret_cast<float4*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS);  // [F] (B_f0, B_f1, B_f2, 0)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB);
+    uint8_t* sgather = smem + SMEM_A + SMEM_W + SMEM_O + SMEM_BIAS + SMEM_FB;
+    float2* g_azza = reinterpret_cast<float2*>(sgather);                         // [epilogue thread]
+    float4* g_m = reinterpret_cast<float4*>(sgather + NEPI * 32 * 8);            // [row of the tile]
+    float* g_alpha = reinterpret_cast<float*>(sgather + NEPI * 32 * 8 + TILE * 16);  // [row of the tile]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sgather + SMEM_GATHER);
     // wfull[NSLOT], wfree[NSLOT], afull, dfull, ofull
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT + 3);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -214,60 +228,96 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
         // epilogue warps: lane quadrant q, sub-tile u, column half h
         const int q = warp & 3, u = ((warp - 2) >> 2) & 1, h = (warp - 2) >> 3;
         const int r_loc = q * 32 + lane;  // row within the sub-tile
+        const int row = u * TM + r_loc;   // row within the tile
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * 256);
         const uint32_t ab = a_base + u * SUB_A;
         const int F = net.F, E = net.E;
+        const int ncomp = net.n_out / 2;
+        const uint32_t my_azza = smem_u32(&g_azza[threadIdx.x - 64]);
         int nd = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-            const long long r = (long long)tile * TILE + u * TM + r_loc;
-            const bool valid = r < R;
-            const int b = valid ? (int)(r / K) : 0, s = valid ? (int)(r % K) : 0;
-            // ---- input features of row r: chunks of 8 columns, chunk c by half c % 2
-            {
-                float2 azza = make_float2(0.f, 0.f);
-                if (valid) azza = lt.azza[(long long)t * lt.pitch + s];
-                const float x0 = azza.x * 0.15915494309189535f;   // az / 2 pi
-                const float x1 = azza.y * 0.63661977236758134f;   // za / (pi / 2)
-                const float x2 = (nu - net.nu_mid) / net.nu_half;
-                for (int c8 = 8 * h; c8 < F; c8 += 16) {
-                    float sv[8], cv[8];
+        // row of the network input in a tile: beam b, live source s
+        auto row_of = [&](int tile, bool& valid, int& b, int& s) {
+            const long long r = (long long)tile * TILE + row;
+            valid = r < R;
+            b = valid ? (int)(r / K) : 0;
+            s = valid ? (int)(r % K) : 0;
+        };
+        // input features of this thread's row: chunks of 8 columns, chunk c by half c % 2
+        auto features = [&](bool valid, int b, float2 azza) {
+            const float x0 = azza.x * 0.15915494309189535f;   // az / 2 pi
+            const float x1 = azza.y * 0.63661977236758134f;   // za / (pi / 2)
+            const float x2 = (nu - net.nu_mid) / net.nu_half;
+            for (int c8 = 8 * h; c8 < F; c8 += 16) {
+                float sv[8], cv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 bf = sB[c8 + i];
-                        float ph = bf.x * x0 + bf.y * x1 + bf.z * x2;
-                        ph -= rintf(ph);
-                        // |2 pi ph| <= pi: the fast sine and cosine are accurate to ~1e-6
-                        // there, far below the BF16 rounding of the features
-                        __sincosf(6.283185307179586f * ph, &sv[i], &cv[i]);
-                        if (!valid) sv[i] = cv[i] = 0.f;
-                    }
-                    st_shared_v4(a_chunk(ab, r_loc, c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
-                                 pack_bf16(sv[4], sv[5]), pack_bf16(sv[6], sv[7]));
-                    st_shared_v4(a_chunk(ab, r_loc, F + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
-                                 pack_bf16(cv[4], cv[5]), pack_bf16(cv[6], cv[7]));
+                for (int i = 0; i < 8; ++i) {
+                    const float4 bf = sB[c8 + i];
+                    float ph = bf.x * x0 + bf.y * x1 + bf.z * x2;
+                    ph -= rintf(ph);
+                    // |2 pi ph| <= pi: the fast sine and cosine are accurate to ~1e-6
+                    // there, far below the BF16 rounding of the features
+                    __sincosf(6.283185307179586f * ph, &sv[i], &cv[i]);
+                    if (!valid) sv[i] = cv[i] = 0.f;
                 }
-                const float* e = net.p + net.off_emb + (long long)b * E;
-                for (int c8 = 8 * h; c8 < net.d0p - 2 * F; c8 += 16) {
-                    float v[8];
+                st_shared_v4(a_chunk(ab, r_loc, c8), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
+                             pack_bf16(sv[4], sv[5]), pack_bf16(sv[6], sv[7]));
+                st_shared_v4(a_chunk(ab, r_loc, F + c8), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
+                             pack_bf16(cv[4], cv[5]), pack_bf16(cv[6], cv[7]));
+            }
+            const float* e = net.p + net.off_emb + (long long)b * E;
+            for (int c8 = 8 * h; c8 < net.d0p - 2 * F; c8 += 16) {
+                float v[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) v[i] = valid && c8 + i < E ? e[c8 + i] : 0.f;
-                    st_shared_v4(a_chunk(ab, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
-                                 pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-                }
+                for (int i = 0; i < 8; ++i) v[i] = valid && c8 + i < E ? e[c8 + i] : 0.f;
+                st_shared_v4(a_chunk(ab, r_loc, 2 * F + c8), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]),
+                             pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(afull);
+        };
+        // Per tile: the next tile's (az, za) and, for the WA writers (half 0),
+        // the source index are requested at the start, the index's flux,
+        // spectral index (and coherency root) once layer 0 is done; all land in
+        // shared memory while the layers run.  After the output layer the
+        // warps read its accumulator, hand the MMA warp the next tile's
+        // features, and then scale and store this tile's WA.
+        int tile = blockIdx.x;
+        if (tile < n_tiles) {
+            bool valid;
+            int b, s;
+            row_of(tile, valid, b, s);
+            features(valid, b, valid ? lt.azza[(long long)t * lt.pitch + s] : make_float2(0.f, 0.f));
+        }
+        for (; tile < n_tiles && ok; tile += gridDim.x) {
+            const int next = tile + gridDim.x;
+            bool valid;
+            int b, s;
+            row_of(tile, valid, b, s);
+            {
+                bool nvalid = false;
+                int nb = 0, ns = 0;
+                if (next < n_tiles) row_of(next, nvalid, nb, ns);
+                if (nvalid) cp_async<8>(my_azza, lt.azza + (long long)t * lt.pitch + ns);
+            }
+            const bool wa_row = h == 0 && valid;
+            const int src = wa_row ? lt.idx[(long long)t * lt.pitch + s] : 0;
             // ---- hidden layers: accumulator -> bias, ReLU -> BF16 activations
             for (int l = 0; l < D; ++l) {
                 if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
+                if (l == 0 && wa_row) {  // the source index has landed by now
+                    cp_async<4>(smem_u32(&g_alpha[row]), m.half_alpha + src);
+                    if (m.pol_m) cp_async<16>(smem_u32(&g_m[row]), m.pol_m + src);
+                    else cp_async<4>(smem_u32(&g_m[row]), m.sqrt_flux + src);
+                }
+                if (l == 0) cp_async_commit();
                 const float* bias = sbias + l * 256;
-                // this warp's H / 2 columns, two 32-column TMEM loads in flight at a time
-                auto drain = [&](const uint32_t (&a32)[32], int c0) {
+                // this warp's H / 2 columns, two 16-column TMEM loads in flight at a time
+                auto drain = [&](const uint32_t (&a32)[16], int c0) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < 2; ++j) {
                         const float4 b0 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j);
                         const float4 b1 = *reinterpret_cast<const float4*>(bias + c0 + 8 * j + 4);
                         st_shared_v4(a_chunk(ab, r_loc, c0 + 8 * j),
@@ -277,14 +327,14 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                                      relu_bf16x2(__uint_as_float(a32[8 * j + 6]) + b1.z, __uint_as_float(a32[8 * j + 7]) + b1.w));
                     }
                 };
-                for (int c00 = h * (H / 2); c00 < (h + 1) * (H / 2); c00 += 64) {
-                    uint32_t acc[2][32];
-                    tmem_ld32(trow + c00, acc[0]);
-                    tmem_ld32(trow + c00 + 32, acc[1]);
-                    tmem_wait_ld(acc[0]);
-                    keep_after_wait(acc[1]);
+                for (int c00 = h * (H / 2); c00 < (h + 1) * (H / 2); c00 += 32) {
+                    uint32_t acc[2][16];
+                    tmem_ld16(trow + c00, acc[0]);
+                    tmem_ld16(trow + c00 + 16, acc[1]);
+                    tmem_wait_ld16(acc[0]);
+                    keep_after_wait16(acc[1]);
                     drain(acc[0], c00);
-                    drain(acc[1], c00 + 32);
+                    drain(acc[1], c00 + 16);
                 }
                 tc_fence_before();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -292,26 +342,35 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                 if (lane == 0) mbar_arrive(afull);
             }
             if (!ok) break;
-            // ---- output layer -> WA
+            // ---- output layer: accumulator -> registers, then the next tile's
+            // features (the accumulator columns are free again), then WA
             if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
             tc_fence_after();
+            float y[8];
             if (h == 0) {
                 uint32_t acc[16];
                 tmem_ld16(trow, acc);
                 tmem_wait_ld16(acc);
+                const float* bo = sbias + D * 256;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) y[i] = __uint_as_float(acc[i]) + bo[i];
+            }
+            tc_fence_before();
+            cp_async_wait_all();
+            if (next < n_tiles) {
+                bool nvalid;
+                int nb, ns;
+                row_of(next, nvalid, nb, ns);
+                features(nvalid, nb, nvalid ? g_azza[threadIdx.x - 64] : make_float2(0.f, 0.f));
+            }
+            if (h == 0) {
                 float mx = 0.f;
                 if (valid) {
-                    const float* bo = sbias + D * 256;
-                    float y[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) y[i] = __uint_as_float(acc[i]) + bo[i];
-                    const long long o = (long long)t * lt.pitch + s;
-                    const int src = lt.idx[o];
-                    const float spec = expf(m.half_alpha[src] * ln_ratio);
-                    const int ncomp = net.n_out / 2;
+                    const float spec = expf(g_alpha[row] * ln_ratio);
+                    const float4 gm = g_m[row];
                     float2* wb = wa + (long long)b * ncomp * wa_pitch + s;
                     if (!m.pol_m) {
-                        const float w = m.sqrt_flux[src] * spec;
+                        const float w = gm.x * spec;
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
                             if (c < ncomp) {
@@ -320,13 +379,12 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                                 mx = fmaxf(mx, hypotf(v.x, v.y));
                             }
                     } else {  // two axes per feed: z = A M (eq. "fullz")
-                        const float4 M = m.pol_m[src];
 #pragma unroll
                         for (int c = 0; c < 4; c += 2)
                             if (c + 1 < ncomp) {
                                 float2 z0, z1;
                                 apply_sky_sqrt(make_float2(y[2 * c], y[2 * c + 1]),
-                                               make_float2(y[2 * c + 2], y[2 * c + 3]), M, spec, z0, z1);
+                                               make_float2(y[2 * c + 2], y[2 * c + 3]), gm, spec, z0, z1);
                                 wb[(long long)c * wa_pitch] = z0;
                                 wb[(long long)(c + 1) * wa_pitch] = z1;
                                 mx = fmaxf(mx, fmaxf(hypotf(z0.x, z0.y), hypotf(z1.x, z1.y)));
@@ -335,9 +393,9 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                 }
                 for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
                 if (lane == 0 && mx > 0.f) atomicMax(reinterpret_cast<int*>(amax), __float_as_int(mx));
-                tc_fence_before();
             }
         }
+        cp_async_wait_all();
     }
     __syncthreads();
     if (*abort_flag) {

@@ -143,3 +143,35 @@ def test_surrogate_with_a_polarised_sky():
     P.stokes_quv = None
     Vu = oracle.vis_with_beam_fn(P, w.lsts[0], w.freqs[0], beam_fn)
     assert rel_err(V[0, 0], Vu) > 0.02
+
+
+@pytest.mark.parametrize("polarised", [False, True])
+def test_surrogate_several_tiles_per_sm(polarised):
+    # 48 beams x ~3000 live sources: ~570 tiles of 256 network rows, several per
+    # persistent CTA, so each CTA carries a tile's gathered source data and the
+    # next tile's features across the tile boundary
+    w = workload(n_ant=48, n_src=6000)
+    if polarised:
+        g = np.random.default_rng(8)
+        d = g.normal(size=(3, w.n_src))
+        w.stokes_quv = d * (0.6 * g.uniform(0, 1, w.n_src) * w.flux_ref / np.linalg.norm(d, axis=0))
+    sim = simulator(w)
+    sim.surrogate_create()
+    sim.surrogate_train(steps=200, batch=8192, lr0=2e-3, lr1=1e-5, seed=4)
+    net = oracle_net(sim, *grid_meta(w))
+    sim.set_beam_surrogate(True)
+    V = sim.simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+    live = int(sim.last_live_counts(len(w.lsts) * len(w.freqs))[0])
+    assert w.n_ant * live > 3 * 152 * 256
+    P = oracle_problem(w)
+    f = w.freqs[1]
+
+    def beam_fn(az, za, nu):
+        n = az.size
+        out = np.empty((w.n_ant, 2, 2, n), dtype=np.complex128)
+        for b in range(w.n_ant):
+            y = mlp.forward(net, np.full(n, b), az, za, np.full(n, nu))
+            out[b] = (y[:, 0::2] + 1j * y[:, 1::2]).T.reshape(2, 2, n)
+        return out
+    Vo = oracle.vis_with_beam_fn(P, w.lsts[0], f, beam_fn)
+    assert rel_err(V[0, 1], Vo) <= 3e-2
