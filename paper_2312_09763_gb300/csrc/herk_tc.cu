@@ -81,10 +81,12 @@ struct Cfg {
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512 + Z_WARPS * 16 * 4;
 };
 
-// Z-build warps of a fused HERK: 14 (a sweep of 6 to 26 on the 350-antenna
-// workload was fastest at 14; more warps slow the tensor pipe's feed, fewer
-// leave the Z build behind).
-__host__ __device__ constexpr int zwarps(int zp, int za, int zf) { return zp == 0 || za * zf == 0 ? 0 : 14; }
+// Z-build warps of a fused HERK: 6, with 12 warps in all (3 per SM
+// sub-partition, up to 168 registers a thread, so the Z build keeps its WA
+// prefetch).  On the 350-antenna workload a sweep of 4 to 14 warps was
+// fastest at 6-7: more warps slow the tensor pipe's feed, fewer leave the Z
+// build behind.
+__host__ __device__ constexpr int zwarps(int zp, int za, int zf) { return zp == 0 || za * zf == 0 ? 0 : 6; }
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16 (format 1) or FP16
 // (format 0), both K-major, N = BN, M = 128.

@@ -126,7 +126,7 @@ template <> struct Plane<0> { using T = float; };
 // [by ant_per_block, +ant_per_block) and every instance of the group.
 // Sources past the live count (up to the k padding) are written as zeros
 // (their WA entries are zero).  scale[j]: the FP16 scale of instance j.
-template <int PREC, int NAX, int NFD, bool PREFETCH = true>
+template <int PREC, int NAX, int NFD>
 __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restrict__ inst, const ZGroup& g,
                                             const LiveTables& lt, const float2* __restrict__ wa,
                                             long long wa_pitch, const float* __restrict__ scale, void* u, void* ulo,
@@ -205,9 +205,8 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
             cos_sin_turns(Q0, rc0, rs0);
             cos_sin_turns(Q1, rc1, rs1);
             for (int j0 = 0; j0 < g.n; j0 += kAnchor) {
-                // one-component beams: the block's WA loads go out together (in the
-                // stand-alone kernel; inside the HERK the registers are scarcer)
-                constexpr int PF = (NC == 1 && PREFETCH) ? kAnchor : 1;
+                // one-component beams: the WA loads of the kAnchor channels go out together
+                constexpr int PF = NC == 1 ? kAnchor : 1;
                 float4 Apf[PF][NC];
                 if constexpr (PF > 1) {
 #pragma unroll
@@ -272,7 +271,7 @@ __device__ __forceinline__ void zjob_warp(const ZJob& z, int warp_id, int n_warp
         __syncwarp();
         if (PREC == 2 && lane < g.n) sw[lane] = ldexpf(1.f, fp16_scale_exp(z.amax[g.slot0 + lane]));
         __syncwarp();
-        zbuild_item<PREC, NAX, NFD, false>(z.m, z.inst, g, z.lt, z.wa, z.wa_pitch, sw, z.u, z.ulo, z.rows, z.k_pitch, apb,
+        zbuild_item<PREC, NAX, NFD>(z.m, z.inst, g, z.lt, z.wa, z.wa_pitch, sw, z.u, z.ulo, z.rows, z.k_pitch, apb,
                                     z.aph + (long long)bz * z.n_phase * z.m.n_ant, bx, by, 32, lane);
     }
 }
