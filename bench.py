@@ -34,13 +34,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) per instance of k_herk_tc<128> on the 350-antenna,
-# 1e5-source workload in FP16x3: one ncu capture of 16 instances (2.4454 GB),
+# 1e5-source workload in FP16x3: one ncu capture of 16 instances (2.4458 GB),
 # summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
-HERK_DRAM_BYTES_PER_INSTANCE = 2.4454e9 / 16
+HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0178e9) / 16
 # The same for the HERK launch that also builds the next batch's U planes
-# (k_herk_tc<128, 2, 1, 1>): 3.4525 GB read + 2.2655 GB written for 16 + 16
+# (k_herk_tc<128, 2, 1, 1>): 2.4974 GB read + 2.2658 GB written for 16 + 16
 # instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
-FUSED_DRAM_BYTES_PER_INSTANCE = (3.4525e9 + 2.2655e9) / 16
+FUSED_DRAM_BYTES_PER_INSTANCE = (2.4974e9 + 2.2658e9) / 16
+# k_mlp_wa on the learned-beam sample (one launch = one instance of 350 beams x
+# 50,013 live sources): 2.9 MB read + 501.5 MB written, summarised in
+# profiles/k_mlp_wa_learned_350beams_1e5src.txt.
+MLP_DRAM_BYTES_PER_LAUNCH = 2.920e6 + 501.452e6
 METRIC = "vis/s (bl·chan·time) at 350 ant×1e5 src; split-prec TC vs FP32 @1e-5 rel err"
 UNIT = "vis/s"
 
@@ -406,7 +410,9 @@ def main():
         learned.update({"network_rows_per_step": rows_step, "flop_per_row": 2 * macs,
                         "surrogate_vs_grid_rel_err": err})
         roof = {"bound": "tensor", "achieved": mlp_tf, "peak": sustained, "unit": "TFLOP/s",
-                "frac": mlp_tf / sustained, "traffic": None, "kernel": "k_mlp_wa (learned-beam forward + WA, tcgen05)",
+                "frac": mlp_tf / sustained,
+                "traffic": MLP_DRAM_BYTES_PER_LAUNCH, "traffic_unit": "B per launch",
+                "kernel": "k_mlp_wa (learned-beam forward + WA, tcgen05)",
                 "launches": n_b, "avg_launch_ms": ms_b / max(n_b, 1),
                 "peak_source": f"{src} bf16 sustained (kernels timed inside a long step)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
