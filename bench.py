@@ -374,9 +374,11 @@ def main():
         # triangle of the 2N x 2N real Gram matrix, for every instance
         flops_step = float(np.sum(3 * 2.0 * rows * (rows + 1) / 2 * K))
         achieved = flops_step * args.steps / (ms_h / 1e3) / 1e12
-        # with the fused Z build (the default for 128-column tiles) the timed
-        # HERK launches also write the next batch's U planes
-        fused = not args.no_fuse and tuning is not None and tuning.get("tile_n") == 128 and nf == nax
+        # with the fused Z build (the schedule the autotuner timed faster, or
+        # the default for a forced 128-column tile) the timed HERK launches
+        # also write the next batch's U planes
+        fused = not args.no_fuse and args.precision != "fp32" and nf == nax and \
+            (bool(tuning.get("fused")) if tuning is not None else hk.get("herk_tile_n") == 128)
         traffic = None
         if args.workload == "hera" and not args.small and args.precision == "fp16x3" and tuning \
                 and tuning.get("tile_n") == 128:

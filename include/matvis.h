@@ -103,7 +103,10 @@ typedef struct {
     int split;           /* source-axis split */
     int flush_kblocks;   /* 64-source k-blocks per TMEM flush */
     int candidates;      /* configurations timed */
-    double herk_ms;      /* best time of one HERK launch of the first batch */
+    double herk_ms;      /* best time of one batch: the HERK launch (with the next batch's Z build when
+                            fused), or the HERK and the batch's own Z-side launches */
+    int fused;           /* 1: the HERK launch of a batch builds the next batch's Z planes;
+                            0: every batch's Z build runs as its own launches */
 } mv_tuning;
 
 /* Fill *opt with defaults. */

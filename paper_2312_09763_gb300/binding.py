@@ -61,7 +61,7 @@ class _MlpConfig(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("tile_n", ctypes.c_int), ("split", ctypes.c_int), ("flush_kblocks", ctypes.c_int),
-                ("candidates", ctypes.c_int), ("herk_ms", ctypes.c_double)]
+                ("candidates", ctypes.c_int), ("herk_ms", ctypes.c_double), ("fused", ctypes.c_int)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -295,7 +295,7 @@ class Simulator:
         self._check(self._lib.mv_autotune(self._h, lst.size, _p(lst), nu.size, _p(nu), PRECISION[precision],
                                           1 if pairs else 0, ctypes.byref(t)))
         return {"tile_n": t.tile_n, "split": t.split, "flush_kblocks": t.flush_kblocks,
-                "candidates": t.candidates, "herk_ms": t.herk_ms}
+                "candidates": t.candidates, "herk_ms": t.herk_ms, "fused": bool(t.fused)}
 
     # --------------------------------------------------------- learned beam
     def surrogate_create(self, n_freq=64, emb_dim=16, width=256, depth=4, sigma_az=2.0, sigma_za=3.0, sigma_nu=1.0,

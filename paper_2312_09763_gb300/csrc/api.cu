@@ -76,6 +76,7 @@ struct mv_ctx {
         bool valid = false;
         int rows = 0, slots = 0, zprec = 0;
         HerkCfg cfg;
+        bool fuse = true;  // the timed schedule: fused Z build, or separate Z-side launches
         double ms = 0;
     } tuned;
     // captured launch sequence of the last call shape
@@ -368,9 +369,12 @@ HerkCfg heuristic_cfg(mv_ctx* c, const Prepared& p) {
     return h;
 }
 
+bool tuned_for(const mv_ctx* c, const Prepared& p) {
+    return c->tuned.valid && c->tuned.rows == p.rows && c->tuned.slots == p.max_slots && c->tuned.zprec == p.zprec;
+}
+
 HerkCfg chosen_cfg(mv_ctx* c, const Prepared& p) {
-    if (c->tuned.valid && c->tuned.rows == p.rows && c->tuned.slots == p.max_slots && c->tuned.zprec == p.zprec)
-        return c->tuned.cfg;
+    if (tuned_for(c, p)) return c->tuned.cfg;
     return heuristic_cfg(c, p);
 }
 
@@ -456,8 +460,10 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if ((s = ensure(c, c->lidx, sizeof(int) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->lazza, sizeof(float2) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
+    // the fused schedule unless the autotuner timed the separate one faster
+    // for calls of this shape
     p.fuse = c->opt.fuse_zbuild && p.zprec != 0 && P.batches.size() > 1 && c->opt.herk_tile_n != 256 &&
-             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed);
+             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed) && !(tuned_for(c, p) && !c->tuned.fuse);
     p.nbuf = (P.batches.size() > 1 && (c->opt.overlap_batches || p.fuse)) ? 2 : 1;
     // antenna phase factors: per batch, groups x wavenumbers per group x antennas
     p.n_phase = 2;
@@ -774,7 +780,13 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
 
 // Autotuner: run the first batch of the call once, then time the HERK of that
 // batch under each candidate (tile width, split, flush) with CUDA events and
-// keep the fastest for calls of the same shape.
+// keep the fastest for calls of the same shape.  Where the Z build can be
+// fused, both schedules are timed per batch -- the fused HERK launch (which
+// also builds a batch's Z planes) against the best separate HERK plus the
+// batch's own Z-side launches -- and the faster one is kept: the fused
+// kernel runs its Z build on a few warps beside the tensor-core roles, which
+// pays when the Z build is light (channels stepped within a group) and not
+// when every instance needs its own phase evaluation.
 mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tuning* out) {
     if (prec == MV_PREC_FP32) return fail(MV_ERR_ARG, "the autotuner tunes the tensor-core HERK");
     if (c->use_sur) return fail(MV_ERR_STATE, "autotune with the gridded beam (mv_set_beam_surrogate(ctx, 0))");
@@ -788,19 +800,21 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
     const Plan::Batch b0 = P.batches[0];
     std::vector<HerkCfg> cands;
     const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
-    // with the fused Z build the tile width is 128, and each trial carries the
-    // Z build of the first batch (into the second workspace set)
-    const std::vector<int> widths = p.fuse ? std::vector<int>{128} : std::vector<int>{128, 256};
-    for (int bn : widths)
-        for (int split : {1, 2, 4, 8, 16, 32, 64})
-            for (int flush : {4, 8, 16}) {
-                if (split > 1 && est_kb / split < 8) continue;
-                HerkCfg h;
-                h.bn = bn;
-                h.split = split;
-                h.flush = flush;
-                cands.push_back(h);
-            }
+    // fused trials (tile width 128) carry the Z build of the first batch into
+    // the second workspace set; separate trials run the HERK alone
+    std::vector<bool> fused_trial;
+    for (int fz = p.fuse ? 1 : 0; fz >= 0; --fz)
+        for (int bn : fz ? std::vector<int>{128} : std::vector<int>{128, 256})
+            for (int split : {1, 2, 4, 8, 16, 32, 64})
+                for (int flush : {4, 8, 16}) {
+                    if (split > 1 && est_kb / split < 8) continue;
+                    HerkCfg h;
+                    h.bn = bn;
+                    h.split = split;
+                    h.flush = flush;
+                    cands.push_back(h);
+                    fused_trial.push_back(fz == 1);
+                }
     size_t need = 0;
     for (auto& h : cands)
         need = std::max(need, sizeof(float) * 128 * h.bn * (size_t)herk_tc_units(p.rows, p.max_slots, h.split, h.bn));
@@ -822,23 +836,40 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
         if ((s = enqueue_ant_phase(c, p, b0, 1, st, &L))) return s;
         zj = make_zjob(c, p, b0, 1);
     }
-    const ZJob* zp = p.fuse ? &zj : nullptr;
     cudaEvent_t e0 = ev_get(c), e1 = ev_get(c);
+    const int reps = 2;
+    // the separate schedule's Z side of one batch (beam, phase table, Z build)
+    double zside_ms = 0;
+    if (p.fuse) {
+        if ((s = enqueue_zside(c, p, b0, 1, st, &L))) return s;  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+            if ((s = enqueue_zside(c, p, b0, 1, st, &L))) return s;
+        cudaEventRecord(e1, st);
+        if ((s = cuda_check(cudaEventSynchronize(e1), "trial timing"))) return s;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        zside_ms = ms / reps;
+    }
     HerkCfg best;
+    bool best_fused = false;
     double best_ms = 1e300;
-    for (const auto& h : cands) {
+    for (size_t i = 0; i < cands.size(); ++i) {
+        const HerkCfg& h = cands[i];
+        const ZJob* zp = fused_trial[i] ? &zj : nullptr;
         if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L, zp), "trial HERK"))) return s;  // warm-up
         cudaEventRecord(e0, st);
-        const int reps = 2;
         for (int r = 0; r < reps; ++r)
             if ((s = cuda_check(enqueue_herk(c, p, b0, h, 0, st, &L, zp), "trial HERK"))) return s;
         cudaEventRecord(e1, st);
         if ((s = cuda_check(cudaEventSynchronize(e1), "trial timing"))) return s;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms / reps < best_ms) {
-            best_ms = ms / reps;
+        const double per_batch = ms / reps + (p.fuse && !fused_trial[i] ? zside_ms : 0.0);
+        if (per_batch < best_ms) {
+            best_ms = per_batch;
             best = h;
+            best_fused = fused_trial[i];
         }
     }
     c->pool.push_back(e0);
@@ -849,6 +880,7 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
     c->tuned.slots = p.max_slots;
     c->tuned.zprec = p.zprec;
     c->tuned.cfg = best;
+    c->tuned.fuse = best_fused;
     c->tuned.ms = best_ms;
     if (out) {
         out->tile_n = best.bn;
@@ -856,6 +888,7 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
         out->flush_kblocks = best.flush;
         out->herk_ms = best_ms;
         out->candidates = (int)cands.size();
+        out->fused = best_fused ? 1 : 0;
     }
     return MV_OK;
 }

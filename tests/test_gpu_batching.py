@@ -109,6 +109,8 @@ def test_autotune_then_simulate():
     sim = simulator(w)
     t = sim.autotune(w.lsts, w.freqs, "bf16x3")
     assert t["tile_n"] in (128, 256) and t["split"] >= 1 and t["candidates"] > 4 and t["herk_ms"] > 0
+    # fused and separate schedules are both timed; the fused one needs 128-column tiles
+    assert t["fused"] in (True, False) and (t["tile_n"] == 128 or not t["fused"])
     V = sim.simulate(w.lsts, w.freqs, "bf16x3").cpu().numpy()
     P = oracle_problem(w)
     pa, pb = sample_pairs(w.n_ant, 200, seed=2)
