@@ -38,26 +38,65 @@ namespace {
 
 using namespace tc;
 
-constexpr int BM = 128, BK = 64;  // tile rows, k-block (64 sources = 128 B of BF16/FP16)
-// ------------------------------------------------------------------ tiling
-// Lower-triangle tiles of G: row tile ti (BM rows), column tile tj (BN rows of
-// U) with tj <= ti BM / BN; tile index runs over (ti, tj) in row order.
+constexpr int BM = 128;  // tile rows
+
+// k-block of a tile width: 64 sources (128-byte rows, 128-byte swizzle) for
+// 128-column tiles, 32 sources (64-byte rows, 64-byte swizzle) for 256-column
+// tiles, whose ring then holds four stages instead of two: the same 192 KB in
+// finer steps, so more of it is in flight while the MMAs read one stage.
 template <int BN>
-__host__ __device__ __forceinline__ int tiles_in_row(int ti) { return ti * BM / BN + 1; }
+__host__ __device__ constexpr int bk_for() { return BN == 256 ? 32 : 64; }
+
+// Shared-memory descriptor of a K-major operand tile with rows of BK 16-bit
+// elements: 8-row groups 8 BK 2 bytes apart, swizzle of the row width.
+template <int BK>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
+    static_assert(BK == 64 || BK == 32, "128- or 64-byte rows");
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * BK * 2) >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)(BK == 64 ? 2 : 4) << 61);
+}
+// ------------------------------------------------------------------ tiling
+// Lower-triangle tiles of G, row panel by row panel: panel ti (rows [ti BM,
+// ti BM + BM)) needs the columns [0, cmax), taken BN at a time.  With
+// 256-column tiles cmax = min(BM (ti + 1), rows rounded up to 16), so the last
+// chunk of a panel (the one holding the diagonal) is cmax - c0 wide, a
+// multiple of 16 (the MMA's N): at 700 rows 12 tiles, four of them 128 wide
+// and one 192 (336 K of executed area for the 245 K of the triangle, against
+// 393 K for full tiles).  128-column tiles stay full (cmax = BM (ti + 1)): a
+// 64-wide MMA tile costs as much as a full one.  Tile index runs over the
+// chunks in row order.
+template <int BN>
+__host__ __device__ __forceinline__ int panel_cmax(int ti, int rows) {
+    return BN == 128 ? BM * (ti + 1) : min(BM * (ti + 1), (rows + 15) / 16 * 16);
+}
 
 template <int BN>
-__host__ __device__ __forceinline__ void tile_of(int idx, int& ti, int& tj) {
-    int i = 0;
-    while (idx >= tiles_in_row<BN>(i)) { idx -= tiles_in_row<BN>(i); ++i; }
-    ti = i;
-    tj = idx;
+__host__ __device__ __forceinline__ void tile_at(int idx, int rows, int& ti, int& c0, int& ncol) {
+    if (BN == 128) {  // panel i holds i + 1 full tiles
+        int i = 0;
+        while (idx > i) idx -= ++i;
+        ti = i;
+        c0 = idx * BN;
+        ncol = BN;
+        return;
+    }
+    for (int i = 0;; ++i) {
+        const int cmax = panel_cmax<BN>(i, rows), nch = (cmax + BN - 1) / BN;
+        if (idx < nch) {
+            ti = i;
+            c0 = idx * BN;
+            ncol = min(BN, cmax - c0);
+            return;
+        }
+        idx -= nch;
+    }
 }
 
 template <int BN>
 int n_tiles_for(int rows) {
     const int T = (rows + BM - 1) / BM;
     int n = 0;
-    for (int i = 0; i < T; ++i) n += tiles_in_row<BN>(i);
+    for (int i = 0; i < T; ++i) n += (panel_cmax<BN>(i, rows) + BN - 1) / BN;
     return n;
 }
 
@@ -69,10 +108,12 @@ template <int BN, int ZW = 0>
 struct Cfg {
     static constexpr bool FZ = ZW > 0;
     static_assert(!FZ || BN == 128, "the fused Z build runs with 128-column tiles");
-    static constexpr int A_BYTES = BM * BK * 2;                    // 16 KB per plane
-    static constexpr int B_BYTES = BN * BK * 2;                    // 16 or 32 KB per plane
-    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 64 or 96 KB
-    static constexpr int STAGES = BN == 256 ? 2 : 3;               // 192 KB of ring either way
+    static constexpr int BK = bk_for<BN>();
+    static constexpr int SUB = BM * BK * 2;                        // one 128-row box of one plane
+    static constexpr int A_BYTES = SUB;                            // 16 or 8 KB per plane
+    static constexpr int B_BYTES = BN * BK * 2;                    // 16 KB per plane either way
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 64 or 48 KB
+    static constexpr int STAGES = BN == 256 ? 4 : 3;               // 192 KB of ring either way
     static constexpr int TMEM_COLS = (BN == 256 || FZ) ? 512 : 256;  // two accumulators (+ running sums)
     static constexpr int EPI_WARPS = BN / 32;                      // 128 columns per epilogue warp
     static constexpr int Z_WARPS = ZW;
@@ -102,31 +143,34 @@ constexpr uint32_t idesc_for(bool fp16, int bn) {
 // first, and the CTAs running at one time share k-ranges of one instance, so
 // each 64-column block of U is read from HBM about once and reused via L2.
 struct Unit {
-    int slot, ti, tj, kb0, kb1;
+    int slot, ti, c0, ncol, kb0, kb1;  // row panel, first column and width of the tile
     int part;  // index of the unit's partial tile: (slot n_tiles + tile) S + ks
 };
 
-// A diagonal tile's A rows [ti BM, ti BM + BM) lie inside its B rows
-// [tj BN, tj BN + BN): the tile loads B only and reads A from B's 128-row
-// half diag_half (-1: not a diagonal tile).
-template <int BN>
-__host__ __device__ __forceinline__ int diag_half(int ti, int tj) {
-    return (ti * BM) / BN == tj ? (ti * BM - tj * BN) / BM : -1;
+// 128-row boxes of U that hold a tile's B rows [c0, c0 + ncol).
+__host__ __device__ __forceinline__ int n_boxes(int ncol) { return (ncol + BM - 1) / BM; }
+
+// A diagonal tile's A rows [ti BM, ti BM + BM) are one of the 128-row boxes
+// of its B rows: the tile loads B only and reads A from B's box diag_box
+// (-1: not a diagonal tile).
+__host__ __device__ __forceinline__ int diag_box(int ti, int c0, int ncol) {
+    const int d = ti * BM - c0;
+    return d >= 0 && d < n_boxes(ncol) * BM ? d / BM : -1;
 }
 
 template <int BN>
 __device__ __forceinline__ Unit decode_unit(int u, int n_tiles, int S, const int* __restrict__ order,
                                             const Inst* __restrict__ inst, int inst0, const LiveTables& lt,
-                                            int n_ax) {
+                                            int n_ax, int rows) {
     Unit w;
     const int tile = u % n_tiles;
     const int rest = u / n_tiles;
     const int ks = rest % S;
     w.slot = order[rest / S];
     w.part = (w.slot * n_tiles + tile) * S + ks;
-    tile_of<BN>(tile, w.ti, w.tj);
+    tile_at<BN>(tile, rows, w.ti, w.c0, w.ncol);
     const long long K = (long long)lt.n_live[inst[inst0 + w.slot].t] * n_ax;
-    const long long KB = ((K + kKPad - 1) / kKPad * kKPad) / BK;
+    const long long KB = ((K + kKPad - 1) / kKPad * kKPad) / bk_for<BN>();
     w.kb0 = (int)(KB * ks / S);
     w.kb1 = (int)(KB * (ks + 1) / S);
     return w;
@@ -167,6 +211,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     constexpr bool FZ = ZP != 0;
     using C = Cfg<BN, zwarps(ZP, ZA, ZF)>;
     constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
+    constexpr int BK = C::BK, SUB = C::SUB;
     constexpr int QD = C::QDEPTH;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -215,25 +260,25 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 qslot[q] = u;
                 mbar_arrive(qfull(q));
                 if (u < 0) break;
-                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
-                const bool diag = diag_half<BN>(w.ti, w.tj) >= 0;
+                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N);
+                const bool diag = diag_box(w.ti, w.c0, w.ncol) >= 0;
+                const int nb = BN == 128 ? 1 : n_boxes(w.ncol);  // full tiles at 128 columns
+                const uint32_t bytes = (uint32_t)(2 * nb * SUB + (diag ? 0 : 2 * A_BYTES));
                 bool ok = true;
                 for (int kb = w.kb0; kb < w.kb1; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!wait_bounded(empty(s), ph ^ 1u, abort_flag, err)) { ok = false; break; }
-                    mbar_expect_tx(full(s), diag ? 2 * B_BYTES : STAGE_BYTES);
+                    mbar_expect_tx(full(s), bytes);
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     const int x = kb * BK;
                     if (!diag) {
                         tma_load_3d(st, &map_hi, x, w.ti * BM, w.slot, full(s));
                         tma_load_3d(st + A_BYTES, &map_lo, x, w.ti * BM, w.slot, full(s));
                     }
-#pragma unroll
-                    for (int h = 0; h < BN / 128; ++h) {
-                        tma_load_3d(st + 2 * A_BYTES + h * 16384, &map_hi, x, w.tj * BN + h * 128, w.slot, full(s));
-                        tma_load_3d(st + 2 * A_BYTES + B_BYTES + h * 16384, &map_lo, x, w.tj * BN + h * 128, w.slot,
-                                    full(s));
+                    for (int h = 0; h < nb; ++h) {
+                        tma_load_3d(st + 2 * A_BYTES + h * SUB, &map_hi, x, w.c0 + h * BM, w.slot, full(s));
+                        tma_load_3d(st + 2 * A_BYTES + B_BYTES + h * SUB, &map_lo, x, w.c0 + h * BM, w.slot, full(s));
                     }
                 }
                 if (!ok) break;
@@ -248,11 +293,13 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 const int u = qslot[q];
                 mbar_arrive(qempty(q));
                 if (u < 0) break;
-                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N);
                 // A's offset in the stage: its own slot, or the matching half of B
-                const int dh = diag_half<BN>(w.ti, w.tj);
-                const uint32_t a_off = dh < 0 ? 0u : (uint32_t)(2 * A_BYTES + dh * 16384);
+                const int dh = diag_box(w.ti, w.c0, w.ncol);
+                const uint32_t a_off = dh < 0 ? 0u : (uint32_t)(2 * A_BYTES + dh * SUB);
                 const uint32_t a_lo_off = dh < 0 ? (uint32_t)A_BYTES : a_off + (uint32_t)B_BYTES;
+                // N of the tile's MMAs: its width
+                const uint32_t id = BN == 128 ? idesc : (idesc & ~(0x3Fu << 17)) | ((uint32_t)(w.ncol >> 3) << 17);
                 bool ok = true;
                 for (int kc = w.kb0; kc < w.kb1 && ok; kc += flush, ++cg) {
                     const int buf = cg & 1;
@@ -270,14 +317,14 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                         const uint32_t st = sbase + s * STAGE_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint64_t a_hi = sdesc(st + a_off + kk * 32);
-                            const uint64_t a_lo = sdesc(st + a_lo_off + kk * 32);
-                            const uint64_t b_hi = sdesc(st + 2 * A_BYTES + kk * 32);
-                            const uint64_t b_lo = sdesc(st + 2 * A_BYTES + B_BYTES + kk * 32);
-                            tc_mma(d, a_hi, b_hi, idesc, acc);
+                            const uint64_t a_hi = sdesc_k<BK>(st + a_off + kk * 32);
+                            const uint64_t a_lo = sdesc_k<BK>(st + a_lo_off + kk * 32);
+                            const uint64_t b_hi = sdesc_k<BK>(st + 2 * A_BYTES + kk * 32);
+                            const uint64_t b_lo = sdesc_k<BK>(st + 2 * A_BYTES + B_BYTES + kk * 32);
+                            tc_mma(d, a_hi, b_hi, id, acc);
                             acc = 1;
-                            tc_mma(d, a_hi, b_lo, idesc, 1);
-                            tc_mma(d, a_lo, b_hi, idesc, 1);
+                            tc_mma(d, a_hi, b_lo, id, 1);
+                            tc_mma(d, a_lo, b_hi, id, 1);
                         }
                         tc_commit(empty(s));
                     }
@@ -298,13 +345,15 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             __syncwarp();
             if (lane == 0) mbar_arrive(qempty(qi));
             if (u < 0) break;
-            const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax);
+            const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N);
             const int rl = q4 * 32 + lane;  // row of the tile held by this thread
             const int r = w.ti * BM + rl;
             const int a = r >> 1;
             const bool even = (lane & 1) == 0;
             float2* Vb = V + inst[inst0 + w.slot].v_off;
-            const int c0 = w.tj * BN + h * 128;
+            const int c0 = w.c0 + h * 128;
+            // columns of this warp's 128 inside the tile (all of them at 128 columns)
+            const int ncv = BN == 128 ? 128 : w.ncol - h * 128;
             // undo the FP16 scaling 2^e of both operands: two exact power-of-two steps
             const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[w.slot])) : 1.f;
             // one 32-column chunk of the tile (columns c0 + 32 g ...): raw partial
@@ -350,6 +399,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                     const uint32_t ta = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * BN + h * 128);
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
+                        if (g * 32 >= ncv) break;
                         uint32_t rr[32];
                         tmem_ld32(ta + g * 32, rr);
                         tmem_wait_ld(rr);
@@ -362,7 +412,8 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 }
                 if (!ok || *abort_flag) break;
 #pragma unroll
-                for (int g = 0; g < 4; ++g) write_chunk(std::integral_constant<int, 32>{}, g, run + g * 32);
+                for (int g = 0; g < 4; ++g)
+                    if (g * 32 < ncv) write_chunk(std::integral_constant<int, 32>{}, g, run + g * 32);
             } else {
                 // running sums in TMEM columns [2 BN, 3 BN) of this warp's lanes,
                 // 16 columns at a time
@@ -376,7 +427,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                     tc_fence_after();
                     const uint32_t ta = tl + (uint32_t)(buf * BN);
 #pragma unroll 1
-                    for (int g = 0; g < 8; ++g) {
+                    for (int g = 0; g < 8 && g * 16 < ncv; ++g) {
                         uint32_t acc[16];
                         tmem_ld16(ta + g * 16, acc);
                         tmem_wait_ld16(acc);
@@ -398,7 +449,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 }
                 if (!ok || *abort_flag) break;
 #pragma unroll 1
-                for (int g = 0; g < 8; ++g) {
+                for (int g = 0; g < 8 && g * 16 < ncv; ++g) {
                     float x[16];
                     if (any) {
                         uint32_t sum[16];
@@ -441,13 +492,13 @@ k_herk_finalize(const Inst* __restrict__ inst, int inst0, int fp16, const float*
                 const float* __restrict__ partial, float2* __restrict__ V, int N, int n_tiles, int S) {
     const int st = blockIdx.x;
     const int slot = st / n_tiles, tile = st % n_tiles;
-    int ti, tj;
-    tile_of<BN>(tile, ti, tj);
+    int ti, c0, ncol;
+    tile_at<BN>(tile, 2 * N, ti, c0, ncol);
     const int q = blockIdx.y * 256 + threadIdx.x;  // 2 x 2 block index within the tile
     const int rp = q % (BM / 2), cp = q / (BM / 2);
     const int r = 2 * rp, c = 2 * cp;
-    const int a = (ti * BM + r) >> 1, b = (tj * BN + c) >> 1;
-    if (a >= N || b >= N || a < b) return;
+    const int a = (ti * BM + r) >> 1, b = (c0 + c) >> 1;
+    if (c >= ncol || a >= N || b >= N || a < b) return;
     float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
     for (int ks = 0; ks < S; ++ks) {
         const float* p = partial + ((long long)st * S + ks) * (BN * BM);
@@ -466,16 +517,16 @@ k_herk_finalize(const Inst* __restrict__ inst, int inst0, int fp16, const float*
     if (a != b) Vb[(long long)b * N + a] = make_float2(re, -im);
 }
 
-bool make_map(CUtensorMap* map, const void* base, long long k_pitch, int rows, int n_slots, bool fp16) {
+bool make_map(CUtensorMap* map, const void* base, long long k_pitch, int rows, int n_slots, bool fp16, int bk) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)k_pitch, (cuuint64_t)rows, (cuuint64_t)n_slots};
     cuuint64_t strides[2] = {(cuuint64_t)k_pitch * 2, (cuuint64_t)k_pitch * 2 * rows};
-    cuuint32_t box[3] = {BK, BM, 1};
+    cuuint32_t box[3] = {(cuuint32_t)bk, BM, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -486,6 +537,7 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
                       int flush, int split, int n_ctas, int* d_sched, float* d_partial, int* d_err,
                       const ZJob* zj, cudaStream_t st, long long* launches) {
     using C = Cfg<BN, zwarps(ZP, ZA, ZF)>;
+    flush *= 64 / C::BK;  // the option counts 64-source blocks
     const int n_tiles = n_tiles_for<BN>(rows);
     const int n_units = n_tiles * n_inst * split;
     int* order = d_sched;            // [n_inst]
@@ -546,7 +598,8 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                            int bn, int n_ctas, int* d_sched, float* d_partial, int* d_err, const ZJob* zj,
                            int zprec, cudaStream_t st, long long* launches) {
     CUtensorMap mh, ml;
-    if (!make_map(&mh, d_hi, k_pitch, rows, n_slots, fp16) || !make_map(&ml, d_lo, k_pitch, rows, n_slots, fp16))
+    const int bk = (zj || bn == 128) ? bk_for<128>() : bk_for<256>();
+    if (!make_map(&mh, d_hi, k_pitch, rows, n_slots, fp16, bk) || !make_map(&ml, d_lo, k_pitch, rows, n_slots, fp16, bk))
         return cudaErrorInvalidValue;
     if (flush < 1) flush = 4;
     if (split < 1) split = 1;
