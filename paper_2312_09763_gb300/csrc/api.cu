@@ -70,7 +70,6 @@ struct mv_ctx {
     cudaStream_t cstream = nullptr;
     cudaEvent_t ev_vdone = nullptr, ev_cdone = nullptr;
     int n_sms = 148;
-    long long model_version = 0;  // bumped by every set-up call (kernel arguments embed the model)
     // autotuned HERK configuration, valid for calls of the same shape
     struct Tuned {
         bool valid = false;
@@ -701,10 +700,25 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
 }
 
 // Key of a captured launch sequence: every value its kernel arguments depend on.
+// The model goes in by value (its pointers, sizes and beam scalars): set-up
+// calls that refill the same buffers with data of the same shape keep the
+// captured sequence, which reads the new data.
 std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, const HerkCfg& h) {
+    const Model& m = c->model;
+    auto bits = [](float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, sizeof u);
+        return (long long)u;
+    };
     std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch, p.nbuf,
                                 p.fuse, h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout,
-                                (long long)(uintptr_t)p.Vhost, c->model_version};
+                                (long long)(uintptr_t)p.Vhost,
+                                m.n_src, (long long)(uintptr_t)m.xeq, (long long)(uintptr_t)m.sqrt_flux,
+                                (long long)(uintptr_t)m.half_alpha, (long long)(uintptr_t)m.pol_m, m.n_ant,
+                                (long long)(uintptr_t)m.ant_e, (long long)(uintptr_t)m.ant_n,
+                                (long long)(uintptr_t)m.ant_u, (long long)(uintptr_t)m.beam_idx, m.beam_kind,
+                                bits(m.gauss_c), m.n_beam, m.n_feed, m.n_ax, m.n_nu, m.n_za, m.n_az, bits(m.dza),
+                                bits(m.daz), m.interp};
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
                          &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
                          &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err,
@@ -1020,7 +1034,6 @@ mv_status mv_init_sky(mv_ctx* c, int64_t n_src, const double* ra, const double* 
     c->h_flux.assign(flux_ref, flux_ref + n_src);
     c->nu_ref = nu_ref;
     c->have_sky = true;
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1030,8 +1043,7 @@ mv_status mv_set_sky_polarisation(mv_ctx* c, int64_t n_src, const double* q, con
     if (!c->have_sky) return fail(MV_ERR_STATE, "call mv_init_sky first");
     if (!q && !u && !v) {
         c->model.pol_m = nullptr;
-        ++c->model_version;
-        return MV_OK;
+            return MV_OK;
     }
     if (!q || !u || !v) return fail(MV_ERR_ARG, "stokes_q, stokes_u and stokes_v go together");
     if (n_src != c->model.n_src) return fail(MV_ERR_ARG, "n_src %lld != the sky's %lld", (long long)n_src,
@@ -1057,7 +1069,6 @@ mv_status mv_set_sky_polarisation(mv_ctx* c, int64_t n_src, const double* q, con
     if ((s = upload(c, c->pol_m, M.data(), M.size() * sizeof(float4), c->stream))) return s;
     if ((s = cuda_check(cudaStreamSynchronize(c->stream), "set_sky_polarisation"))) return s;
     c->model.pol_m = (const float4*)c->pol_m.p;
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1069,7 +1080,6 @@ mv_status mv_set_beam_gaussian(mv_ctx* c, double fwhm) {
     c->model.gauss_c = (float)(4.0 * std::log(2.0) / (fwhm * fwhm));
     c->model.n_beam = c->model.n_feed = c->model.n_ax = 1;
     c->have_beam = true;
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1107,7 +1117,6 @@ mv_status mv_set_beam_grid(mv_ctx* c, int n_beam, int n_feed, int n_ax, int n_nu
     c->grid_nu0 = nu0;
     c->grid_dnu = dnu;
     c->have_beam = true;
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1144,7 +1153,6 @@ mv_status mv_set_antennas(mv_ctx* c, int n_ant, const double* enu, const int32_t
     c->h_bidx = b;
     c->lat = lat;
     c->have_ant = true;
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1278,7 +1286,6 @@ mv_status mv_surrogate_create(mv_ctx* c, const mv_mlp_config* cfg) {
     surrogate_destroy(c->sur);
     c->sur = S;
     c->sur_cfg = k;
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1336,7 +1343,6 @@ mv_status mv_surrogate_set_params(mv_ctx* c, const float* host) {
     DeviceGuard g(c->device);
     cudaError_t e = surrogate_set_params(c->sur, host);
     if (e != cudaSuccess) return fail(MV_ERR_CUDA, "parameter copy: %s", cudaGetErrorString(e));
-    ++c->model_version;
     return MV_OK;
 }
 
@@ -1444,7 +1450,6 @@ mv_status mv_set_beam_surrogate(mv_ctx* c, int enable) {
     if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
     if (enable && !c->sur) return fail(MV_ERR_STATE, "no surrogate");
     c->use_sur = enable != 0;
-    ++c->model_version;
     return MV_OK;
 }
 
