@@ -430,14 +430,26 @@ def main():
     if rank == 0 and not args.no_e2e:
         # end to end through the public API: model inputs from pinned host
         # memory each step (sky, beam, antennas), V back to pinned host memory
-        ra, dec, fl = (torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (w.ra, w.dec, w.flux_ref))
+        pinned_keep = []
+
+        def pinned(x):  # a page-locked copy, as a numpy view
+            t = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+            pinned_keep.append(t)
+            return t.numpy()
+        ra, dec, fl = (pinned(np.asarray(x, dtype=np.float64)) for x in (w.ra, w.dec, w.flux_ref))
+        si = None if w.spec_idx is None else pinned(np.asarray(w.spec_idx, dtype=np.float64))
+        beam = w.beam
+        if beam[0] == "grid":
+            beam = (beam[0], pinned(np.asarray(beam[1], dtype=np.complex64))) + tuple(beam[2:])
+        enu = pinned(w.enu)
         Vh = torch.empty(tuple(V.shape), dtype=torch.complex64).pin_memory()
-        h2d = 8 * (w.ra.size * 4) + np.asarray(w.beam[1]).nbytes + w.enu.nbytes
+        h2d = sum(x.nbytes for x in (ra, dec, fl, enu)) + (0 if si is None else si.nbytes) + \
+            (beam[1].nbytes if beam[0] == "grid" else 0)
         d2h = Vh.numel() * 8
         def e2e_step():
-            sim.init_sky(ra.numpy(), dec.numpy(), fl.numpy(), w.spec_idx, w.nu_ref)
-            sim.set_beam(w.beam)
-            sim.set_antennas(w.enu, None, w.lat)
+            sim.init_sky(ra, dec, fl, si, w.nu_ref)
+            sim.set_beam(beam)
+            sim.set_antennas(enu, None, w.lat)
             run(w.lsts, w.freqs, args.precision, out=Vh, host=True)
         e2e_step()  # warm-up: the host-output staging buffer and its captured launch sequence
         e2e_steps = max(1, min(args.steps, 3))

@@ -218,6 +218,39 @@ typedef enum {
     MV_KERNEL_KINDS = 4
 } mv_kernel_kind;
 
+/* ------------------------------------------------------------- redundancy
+ * Baseline redundancy (Appendix A of the paper, "Utilising baseline
+ * redundancies").  Baselines (a, b), a <= b, whose vectors x_a - x_b agree on a
+ * tol_m grid (each component rounded to a multiple of tol_m) and whose beams
+ * agree have equal visibilities; a baseline whose vector is the reverse of
+ * another's (beams swapped) has the conjugate visibility.  Each group has one
+ * representative, its first member in lexicographic order; groups are
+ * numbered in the order of their representatives.
+ *
+ * mv_redundancy_plan (host only: no context, no device) groups the baselines
+ * of n_ant antennas (enu [n_ant][3] metres, beam_idx [n_ant] or NULL = all 0)
+ * and plans the cover of the representatives the HERK computes: Appendix A's
+ * sub-matrix heuristic (first antennas sorted by multiplicity, cut into 1-3
+ * slices at a density threshold), in both orientations, each sub-matrix a block
+ * of contiguous rows and columns of V in a permuted antenna order, costed in
+ * 128-row x tile_n-column (128 or 256) tiles of the 2 n_feed-row real Gram
+ * matrix; the whole lower triangle is kept when no cover is cheaper.
+ * Outputs (each may be NULL; sizes: n_bl = n_ant (n_ant + 1) / 2):
+ *   n_unique          number of groups
+ *   rep_a, rep_b      [n_bl] (only the first n_unique written) representatives
+ *   group_of          [n_bl] group of baseline (a, b), a <= b, row-major over a then b
+ *   conj_of           [n_bl] 1 where V_ab is the conjugate of the representative's
+ *   perm              [n_ant] position of antenna a in the cover's order
+ *   kind              0 whole triangle, 1 blocks hold (rep_a, rep_b) as (row, column),
+ *                     2 as (rep_b, rep_a)
+ *   n_blocks, blocks  [4][4] int32: row0, row1, col0, col1 (positions) per block
+ *   tiles             [2]: tiles of the chosen cover, tiles of the whole triangle
+ * MV_ERR_ARG for bad sizes, non-finite positions, tol_m <= 0 or n_feed < 1. */
+mv_status mv_redundancy_plan(int n_ant, const double *enu, const int32_t *beam_idx, double tol_m, int n_feed,
+                             int tile_n, int64_t *n_unique, int32_t *rep_a, int32_t *rep_b, int32_t *group_of,
+                             int8_t *conj_of, int32_t *perm, int32_t *kind, int32_t *n_blocks, int32_t *blocks,
+                             int64_t *tiles);
+
 /* Rotation and horizon cut of one LST without any device allocation.
  *
  * The paper has no counterpart: this exists for callers that cannot allocate

@@ -29,7 +29,7 @@ EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv
            "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static", "mv_autotune",
            "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
            "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
-           "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation"]
+           "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation", "mv_redundancy_plan"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -112,6 +112,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_surrogate_save.argtypes = [vp, ctypes.c_char_p]
     lib.mv_surrogate_load.argtypes = [vp, ctypes.c_char_p]
     lib.mv_set_beam_surrogate.argtypes = [vp, i32]
+    lib.mv_redundancy_plan.argtypes = [i32, vp, vp, dp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.mv_redundancy_plan.restype = i32
     for name in ("mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params", "mv_surrogate_set_params",
                  "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save", "mv_surrogate_load",
                  "mv_set_beam_surrogate"):
@@ -130,6 +132,30 @@ def _f64(a) -> np.ndarray:
 
 def _p(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def redundancy_plan(enu, beam_idx=None, tol_m: float = 1e-3, n_feed: int = 1, tile_n: int = 256) -> dict:
+    """Redundant-baseline groups of an array and the cover of their
+    representatives (mv_redundancy_plan; host only, no GPU needed)."""
+    lib = load_library()
+    enu = _f64(enu).reshape(-1, 3)
+    n = enu.shape[0]
+    nbl = n * (n + 1) // 2
+    bi = None if beam_idx is None else np.ascontiguousarray(np.asarray(beam_idx, dtype=np.int32))
+    nu, kind, nb = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    ra, rb, go = (np.zeros(nbl, np.int32) for _ in range(3))
+    co = np.zeros(nbl, np.int8)
+    perm = np.zeros(n, np.int32)
+    blocks = np.zeros(16, np.int32)
+    tiles = np.zeros(2, np.int64)
+    st = lib.mv_redundancy_plan(n, _p(enu), _p(bi), float(tol_m), n_feed, tile_n, ctypes.byref(nu), _p(ra), _p(rb),
+                                _p(go), _p(co), _p(perm), ctypes.byref(kind), ctypes.byref(nb), _p(blocks), _p(tiles))
+    if st != 0:
+        raise MatvisError(st, lib.mv_last_error().decode())
+    k = nu.value
+    return {"n_unique": k, "rep_a": ra[:k].copy(), "rep_b": rb[:k].copy(), "group_of": go, "conj_of": co,
+            "perm": perm, "kind": kind.value, "blocks": blocks[:4 * nb.value].reshape(-1, 4).copy(),
+            "tiles": int(tiles[0]), "tiles_full": int(tiles[1])}
 
 
 class Simulator:

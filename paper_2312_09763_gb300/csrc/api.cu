@@ -13,6 +13,7 @@
 
 #include "matvis.h"
 #include "common.cuh"
+#include "redund.h"
 
 using namespace mv;
 
@@ -1153,6 +1154,42 @@ mv_status mv_set_antennas(mv_ctx* c, int n_ant, const double* enu, const int32_t
     c->h_bidx = b;
     c->lat = lat;
     c->have_ant = true;
+    return MV_OK;
+}
+
+mv_status mv_redundancy_plan(int n_ant, const double* enu, const int32_t* beam_idx, double tol_m, int n_feed,
+                             int tile_n, int64_t* n_unique, int32_t* rep_a, int32_t* rep_b, int32_t* group_of,
+                             int8_t* conj_of, int32_t* perm, int32_t* kind, int32_t* n_blocks, int32_t* blocks,
+                             int64_t* tiles) {
+    g_err.clear();
+    if (n_ant < 1 || n_ant > 16384) return fail(MV_ERR_ARG, "n_ant %d out of range", n_ant);
+    if (!enu || !finite_all(enu, 3 * (int64_t)n_ant)) return fail(MV_ERR_ARG, "enu missing or not finite");
+    if (beam_idx)
+        for (int a = 0; a < n_ant; ++a)
+            if (beam_idx[a] < 0) return fail(MV_ERR_ARG, "beam_idx[%d] < 0", a);
+    RedPlan p;
+    const char* why = nullptr;
+    if (!plan_redundancy(n_ant, enu, beam_idx, tol_m, n_feed, tile_n, p, &why)) return fail(MV_ERR_ARG, "%s", why);
+    const long long n_bl = (long long)n_ant * (n_ant + 1) / 2;
+    if (n_unique) *n_unique = (int64_t)p.rep_a.size();
+    if (rep_a) std::memcpy(rep_a, p.rep_a.data(), sizeof(int32_t) * p.rep_a.size());
+    if (rep_b) std::memcpy(rep_b, p.rep_b.data(), sizeof(int32_t) * p.rep_b.size());
+    if (group_of) std::memcpy(group_of, p.group_of.data(), sizeof(int32_t) * n_bl);
+    if (conj_of) std::memcpy(conj_of, p.conj_of.data(), (size_t)n_bl);
+    if (perm) std::memcpy(perm, p.perm.data(), sizeof(int32_t) * n_ant);
+    if (kind) *kind = p.kind;
+    if (n_blocks) *n_blocks = (int32_t)p.blocks.size();
+    if (blocks)
+        for (size_t i = 0; i < p.blocks.size(); ++i) {
+            blocks[4 * i] = p.blocks[i].r0;
+            blocks[4 * i + 1] = p.blocks[i].r1;
+            blocks[4 * i + 2] = p.blocks[i].c0;
+            blocks[4 * i + 3] = p.blocks[i].c1;
+        }
+    if (tiles) {
+        tiles[0] = p.tiles;
+        tiles[1] = p.tiles_full;
+    }
     return MV_OK;
 }
 
