@@ -239,7 +239,8 @@ typedef enum {
  *   n_unique          number of groups
  *   rep_a, rep_b      [n_bl] (only the first n_unique written) representatives
  *   group_of          [n_bl] group of baseline (a, b), a <= b, row-major over a then b
- *   conj_of           [n_bl] 1 where V_ab is the conjugate of the representative's
+ *   conj_of           [n_bl] 1 where (a, b) is a reversed baseline of its group:
+ *                     V_ab^{pq} = conj(V_rep^{qp}) (feeds swapped), else V_ab = V_rep
  *   perm              [n_ant] position of antenna a in the cover's order
  *   kind              0 whole triangle, 1 blocks hold (rep_a, rep_b) as (row, column),
  *                     2 as (rep_b, rep_a)
@@ -250,6 +251,23 @@ mv_status mv_redundancy_plan(int n_ant, const double *enu, const int32_t *beam_i
                              int tile_n, int64_t *n_unique, int32_t *rep_a, int32_t *rep_b, int32_t *group_of,
                              int8_t *conj_of, int32_t *perm, int32_t *kind, int32_t *n_blocks, int32_t *blocks,
                              int64_t *tiles);
+
+/* Plan the redundant-group output for the context's antennas and beam (as
+ * mv_redundancy_plan with tile_n = 256): the Z planes of mv_simulate_unique
+ * are then built in the cover's antenna order and the HERK computes only the
+ * tiles of the cover.  tol_m <= 0 turns it off.  *n_unique (may be NULL)
+ * receives the number of groups.  MV_ERR_STATE before set_antennas and a
+ * beam; a later set_antennas (or a beam with another feed count) drops the
+ * plan. */
+mv_status mv_set_redundancy(mv_ctx *ctx, double tol_m, int64_t *n_unique);
+
+/* As mv_simulate, but one value per redundant group: V [n_t][n_nu][n_unique]
+ * [n_feed][n_feed] complex64, entry [g][p][q] = V^{pq} of the group's
+ * representative (rep_a, rep_b) of mv_redundancy_plan (every baseline of the
+ * group has this value, or where conj_of says so V_ab^{pq} = conj(V^{qp})).  Needs
+ * mv_set_redundancy and a tensor-core precision (MV_ERR_ARG for FP32). */
+mv_status mv_simulate_unique(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const double *nu,
+                             mv_precision prec, void *V, int V_on_device, void *stream);
 
 /* Rotation and horizon cut of one LST without any device allocation.
  *

@@ -29,7 +29,8 @@ EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv
            "mv_profile_enable", "mv_profile_read", "mv_horizon_cull_static", "mv_autotune",
            "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
            "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
-           "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation", "mv_redundancy_plan"]
+           "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation", "mv_redundancy_plan",
+           "mv_set_redundancy", "mv_simulate_unique"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -114,6 +115,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_set_beam_surrogate.argtypes = [vp, i32]
     lib.mv_redundancy_plan.argtypes = [i32, vp, vp, dp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mv_redundancy_plan.restype = i32
+    lib.mv_set_redundancy.argtypes = [vp, dp, vp]
+    lib.mv_set_redundancy.restype = i32
+    lib.mv_simulate_unique.argtypes = [vp, i32, vp, i32, vp, i32, vp, i32, vp]
+    lib.mv_simulate_unique.restype = i32
     for name in ("mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params", "mv_surrogate_set_params",
                  "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save", "mv_surrogate_load",
                  "mv_set_beam_surrogate"):
@@ -300,6 +305,23 @@ class Simulator:
         arr, ptr, on_dev = self._out((lst.size, N, N), out, host)
         self._check(self._lib.mv_simulate_pairs(self._h, lst.size, _p(lst), _p(nu), PRECISION[precision], ptr,
                                                 on_dev, None if host else self._stream(stream)))
+        return arr
+
+    def set_redundancy(self, tol_m: float = 1e-3) -> int:
+        """Plan the redundant-group output for the current antennas and beam
+        (mv_set_redundancy); returns the number of groups.  tol_m <= 0: off."""
+        n = ctypes.c_int64(0)
+        self._check(self._lib.mv_set_redundancy(self._h, float(tol_m), ctypes.byref(n)))
+        self.n_unique = int(n.value)
+        return self.n_unique
+
+    def simulate_unique(self, lsts, freqs, precision: str = "fp16x3", out=None, host: bool = False, stream=None):
+        """One value per redundant group: complex64 [n_t, n_nu, n_unique, n_feed, n_feed]."""
+        lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()
+        shape = (lst.size, nu.size, self.n_unique, self.n_feed, self.n_feed)
+        arr, ptr, on_dev = self._out(shape, out, host)
+        self._check(self._lib.mv_simulate_unique(self._h, lst.size, _p(lst), nu.size, _p(nu), PRECISION[precision],
+                                                 ptr, on_dev, None if host else self._stream(stream)))
         return arr
 
     def check_device_status(self, stream=None):

@@ -56,7 +56,15 @@ struct mv_ctx {
     double nu_ref = 150e6;
     double lat = 0.0;
     std::vector<int> h_bidx;
+    std::vector<double> h_enu;  // [n_ant][3] (host copy, for the redundancy plan)
     double grid_nu0 = 0, grid_dnu = 0;
+    // redundant-baseline expansion (mv_set_redundancy): the plan, the antenna
+    // arrays in the cover's order, the group lookup and the tile lists
+    RedPlan red;
+    bool have_red = false;
+    int red_nf = 0;  // feeds the plan was made for
+    Buf red_e, red_n, red_u, red_b, red_uidx, red_tl[2];  // red_tl: 128- and 256-column tiles
+    int red_ntl[2] = {0, 0};
     // model buffers
     std::vector<double> h_flux;  // I at nu_ref (host copy, for the polarised sky's coherency)
     Buf xeq, sqrt_flux, half_alpha, pol_m, ant_e, ant_n, ant_u, bidx, grid;
@@ -249,6 +257,7 @@ struct Plan {
     std::vector<ZGroup> groups;
     struct Batch { int inst0, n, g0, ng; };
     std::vector<Batch> batches;
+    bool unique = false;  // one value per redundant group instead of the full V
 };
 
 // A group of consecutive instances [i0, i0+n) of one time: equally spaced
@@ -351,6 +360,8 @@ struct Prepared {
     float2* Vout = nullptr;
     float2* Vhost = nullptr;  // page-locked host V (copied per batch on cstream), or NULL
     size_t v_bytes = 0;
+    long long per_inst = 0;  // output values per instance: N^2, or n_unique n_feed^2
+    HerkOut ho{};             // unique output: group lookup and tile lists (ho.tl set per tile width)
 };
 
 // Heuristic HERK configuration: wide tiles unless the matrix is narrow; a
@@ -374,6 +385,19 @@ bool tuned_for(const mv_ctx* c, const Prepared& p) {
 }
 
 HerkCfg chosen_cfg(mv_ctx* c, const Prepared& p) {
+    if (p.ho.uidx) {
+        // the redundant-group cover: its own tile count, 256 columns unless forced
+        HerkCfg h;
+        h.bn = c->opt.herk_tile_n == 128 ? 128 : 256;
+        h.flush = c->opt.herk_flush_kblocks > 0 ? c->opt.herk_flush_kblocks : 16;
+        const int n_tl = c->red.kind == 0 ? herk_tc_units(p.rows, 1, 1, h.bn) : c->red_ntl[h.bn == 128 ? 0 : 1];
+        const long long base = std::max(1ll, (long long)n_tl * p.max_slots);
+        const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
+        h.split = c->opt.herk_split > 0
+                      ? c->opt.herk_split
+                      : (int)std::max(1ll, std::min((4ll * c->n_sms + base - 1) / base, est_kb / 32));
+        return h;
+    }
     if (tuned_for(c, p)) return c->tuned.cfg;
     return heuristic_cfg(c, p);
 }
@@ -442,6 +466,15 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     p.ncomp = m.n_beam * m.n_feed * m.n_ax;
     p.max_slots = 0;
     for (auto& b : P.batches) p.max_slots = std::max(p.max_slots, b.n);
+    p.per_inst = P.unique ? (long long)c->red.rep_a.size() * m.n_feed * m.n_feed : (long long)p.N * p.N;
+    p.ho = HerkOut{};
+    if (P.unique) {
+        if (!c->have_red) return fail(MV_ERR_STATE, "no redundancy plan (mv_set_redundancy)");
+        if (p.zprec == 0) return fail(MV_ERR_ARG, "the redundant-group output needs a tensor-core precision");
+        p.ho.uidx = (const int*)c->red_uidx.p;
+        p.ho.n_ant = m.n_ant;
+        p.ho.n_feed = m.n_feed;
+    }
     const int n_times = p.n_times, max_slots = p.max_slots;
     const long long pitch = p.pitch;
 
@@ -463,7 +496,7 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     // the fused schedule unless the autotuner timed the separate one faster
     // for calls of this shape
     p.fuse = c->opt.fuse_zbuild && p.zprec != 0 && P.batches.size() > 1 && c->opt.herk_tile_n != 256 &&
-             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed) && !(tuned_for(c, p) && !c->tuned.fuse);
+             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed) && !(tuned_for(c, p) && !c->tuned.fuse) && !P.unique;
     p.nbuf = (P.batches.size() > 1 && (c->opt.overlap_batches || p.fuse)) ? 2 : 1;
     // antenna phase factors: per batch, groups x wavenumbers per group x antennas
     p.n_phase = 2;
@@ -491,14 +524,16 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if (p.zprec != 0) {
         // partial tiles for the largest split any configuration may use
         const HerkCfg h = chosen_cfg(c, p);
-        const size_t need = sizeof(float) * 128 * h.bn * (size_t)herk_tc_units(p.rows, max_slots, h.split, h.bn);
+        size_t units = (size_t)herk_tc_units(p.rows, max_slots, h.split, h.bn);
+        if (P.unique) units = std::max(units, (size_t)c->red_ntl[h.bn == 128 ? 0 : 1] * max_slots * h.split);
+        const size_t need = sizeof(float) * 128 * h.bn * units;
         if (h.split > 1 && (s = ensure(c, c->partial, need))) return s;
     }
     if (m.beam_kind == 2 &&
         (s = ensure(c, c->planes, sizeof(float2) * (size_t)p.n_chan * p.ncomp * m.n_za * m.n_az)))
         return s;
     p.Vout = static_cast<float2*>(V);
-    p.v_bytes = sizeof(float2) * (size_t)p.n_inst * p.N * p.N;
+    p.v_bytes = sizeof(float2) * (size_t)p.n_inst * p.per_inst;
     p.Vhost = nullptr;
     if (!V_on_device) {
         if ((s = ensure(c, c->vdev, p.v_bytes))) return s;
@@ -526,13 +561,19 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
 cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, const HerkCfg& h, int k,
                          cudaStream_t st, long long* L, const ZJob* zj = nullptr) {
     const Inst* d_inst = (const Inst*)c->inst.p;
+    HerkOut ho = p.ho;
+    if (ho.uidx) {
+        const int w = h.bn == 128 ? 0 : 1;
+        ho.tl = c->red.kind == 0 ? nullptr : (const TileDesc*)c->red_tl[w].p;
+        ho.n_tl = c->red.kind == 0 ? 0 : c->red_ntl[w];
+    }
     if (p.zprec == 0)
         return launch_herk_fp32(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const float*)c->u[k].p, p.rows,
                                 p.k_pitch, p.Vout, p.N, 256, st, L);
     return launch_herk_tc(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const __nv_bfloat16*)c->u[k].p,
                           (const __nv_bfloat16*)c->ulo[k].p, p.rows, p.k_pitch, p.max_slots, p.zprec == 2 ? 1 : 0,
                           (const float*)c->amax[k].p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
-                          (float*)c->partial.p, (int*)c->err.p, zj, p.zprec, st, L);
+                          (float*)c->partial.p, (int*)c->err.p, zj, p.zprec, p.ho.uidx ? &ho : nullptr, st, L);
 }
 
 // The Z build of batch b into workspace set k, for the HERK of the batch before.
@@ -609,7 +650,7 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
     auto copy_out = [&](const Plan::Batch& b) -> mv_status {
         if (!p.Vhost) return MV_OK;
         const long long off = P.inst[b.inst0].v_off;
-        const size_t bytes = sizeof(float2) * (size_t)b.n * p.N * p.N;
+        const size_t bytes = sizeof(float2) * (size_t)b.n * p.per_inst;
         mv_status s2;
         if ((s2 = cuda_check(cudaEventRecord(c->ev_vdone, st), "event"))) return s2;
         if ((s2 = cuda_check(cudaStreamWaitEvent(c->cstream, c->ev_vdone, 0), "event wait"))) return s2;
@@ -713,7 +754,8 @@ std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, co
     };
     std::vector<long long> k = {p.n_times, p.n_chan, p.n_inst, p.zprec, p.rows, p.max_slots, p.pitch, p.k_pitch, p.nbuf,
                                 p.fuse, h.bn, h.split, h.flush, (long long)(uintptr_t)p.Vout,
-                                (long long)(uintptr_t)p.Vhost,
+                                (long long)(uintptr_t)p.Vhost, P.unique ? 1 : 0, p.per_inst, c->red.kind,
+                                c->red_ntl[0], c->red_ntl[1],
                                 m.n_src, (long long)(uintptr_t)m.xeq, (long long)(uintptr_t)m.sqrt_flux,
                                 (long long)(uintptr_t)m.half_alpha, (long long)(uintptr_t)m.pol_m, m.n_ant,
                                 (long long)(uintptr_t)m.ant_e, (long long)(uintptr_t)m.ant_n,
@@ -723,7 +765,8 @@ std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, co
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
                          &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
                          &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err,
-                         &c->lsfix, &c->lseps, &c->aph[0], &c->aph[1], &c->pol_m};
+                         &c->lsfix, &c->lseps, &c->aph[0], &c->aph[1], &c->pol_m, &c->red_uidx, &c->red_tl[0],
+                         &c->red_tl[1]};
     for (const Buf* b : bufs) k.push_back((long long)(uintptr_t)b->p);
     for (const auto& b : P.batches) {
         k.push_back(b.inst0);
@@ -734,8 +777,38 @@ std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, co
     return k;
 }
 
+// For the redundant-group output the model's antennas are the cover's order
+// (the Z planes are built in that order) for the duration of the call.
+struct ModelSwap {
+    mv_ctx* c;
+    bool on;
+    const double *e, *n, *u;
+    const int* b;
+    ModelSwap(mv_ctx* c_, bool on_) : c(c_), on(on_) {
+        Model& m = c->model;
+        e = m.ant_e;
+        n = m.ant_n;
+        u = m.ant_u;
+        b = m.beam_idx;
+        if (on) {
+            m.ant_e = (const double*)c->red_e.p;
+            m.ant_n = (const double*)c->red_n.p;
+            m.ant_u = (const double*)c->red_u.p;
+            m.beam_idx = (const int*)c->red_b.p;
+        }
+    }
+    ~ModelSwap() {
+        Model& m = c->model;
+        m.ant_e = e;
+        m.ant_n = n;
+        m.ant_u = u;
+        m.beam_idx = b;
+    }
+};
+
 mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, cudaStream_t st) {
     c->launches = 0;
+    ModelSwap swap(c, P.unique);
     Prepared p;
     mv_status s = prepare(c, P, prec, V, V_on_device, st, p);
     if (s || p.n_inst == 0) return s;
@@ -1081,6 +1154,7 @@ mv_status mv_set_beam_gaussian(mv_ctx* c, double fwhm) {
     c->model.gauss_c = (float)(4.0 * std::log(2.0) / (fwhm * fwhm));
     c->model.n_beam = c->model.n_feed = c->model.n_ax = 1;
     c->have_beam = true;
+    if (c->have_red && c->red_nf != c->model.n_feed) c->have_red = false;  // the plan's rows per antenna changed
     return MV_OK;
 }
 
@@ -1118,6 +1192,7 @@ mv_status mv_set_beam_grid(mv_ctx* c, int n_beam, int n_feed, int n_ax, int n_nu
     c->grid_nu0 = nu0;
     c->grid_dnu = dnu;
     c->have_beam = true;
+    if (c->have_red && c->red_nf != c->model.n_feed) c->have_red = false;  // the plan's rows per antenna changed
     return MV_OK;
 }
 
@@ -1152,9 +1227,94 @@ mv_status mv_set_antennas(mv_ctx* c, int n_ant, const double* enu, const int32_t
     m.ant_u = (const double*)c->ant_u.p;
     m.beam_idx = (const int*)c->bidx.p;
     c->h_bidx = b;
+    c->h_enu.assign(enu, enu + 3 * (size_t)n_ant);
     c->lat = lat;
     c->have_ant = true;
+    c->have_red = false;  // a redundancy plan belongs to the antennas it was made for
     return MV_OK;
+}
+
+mv_status mv_set_redundancy(mv_ctx* c, double tol_m, int64_t* n_unique) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    c->have_red = false;
+    if (tol_m <= 0) return MV_OK;  // off
+    if (!c->have_ant || !c->have_beam) return fail(MV_ERR_STATE, "set_antennas and a beam first");
+    const Model& m = c->model;
+    const int n = m.n_ant, nf = m.n_feed;
+    RedPlan& r = c->red;
+    const char* why = nullptr;
+    if (!plan_redundancy(n, c->h_enu.data(), c->h_bidx.data(), tol_m, nf, 256, r, &why))
+        return fail(MV_ERR_ARG, "%s", why);
+    // antennas in the cover's order
+    std::vector<double> e(n), no(n), u(n);
+    std::vector<int> b(n);
+    for (int a = 0; a < n; ++a) {
+        const int q = r.perm[a];
+        e[q] = c->h_enu[3 * a];
+        no[q] = c->h_enu[3 * a + 1];
+        u[q] = c->h_enu[3 * a + 2];
+        b[q] = c->h_bidx[a];
+    }
+    // group lookup: the entry of V (cover's order) that computes each
+    // representative, and whether it is the representative's conjugate
+    std::vector<int> uidx((size_t)n * n, -1);
+    for (size_t g = 0; g < r.rep_a.size(); ++g) {
+        const int a = r.rep_a[g], bb = r.rep_b[g];
+        int row, col, cj;
+        if (r.kind == 1) { row = r.perm[a]; col = r.perm[bb]; cj = 0; }
+        else { row = r.perm[bb]; col = r.perm[a]; cj = 1; }  // kind 2, or the lower triangle
+        uidx[(size_t)row * n + col] = 2 * (int)g + cj;
+    }
+    // tiles of the blocks (rows of U: 2 n_feed per antenna), for 128- and
+    // 256-column tiles; at 128 columns every tile is full width
+    std::vector<TileDesc> tl[2];
+    if (r.kind != 0)
+        for (int w = 0; w < 2; ++w) {
+            const int BN = w ? 256 : 128;
+            for (const RedBlock& k : r.blocks) {
+                const int R0 = 2 * nf * k.r0, R1 = 2 * nf * k.r1, C0 = 2 * nf * k.c0, C1 = 2 * nf * k.c1;
+                for (int rr = R0; rr < R1; rr += 128)
+                    for (int cc = C0; cc < C1; cc += BN) {
+                        const int ncol = BN == 128 ? 128 : std::min(256, (C1 - cc + 15) / 16 * 16);
+                        tl[w].push_back(TileDesc{rr, cc, ncol, R1, C1, 0, 0, 0});
+                    }
+            }
+        }
+    DeviceGuard g(c->device);
+    mv_status s;
+    if ((s = upload(c, c->red_e, e.data(), n * sizeof(double), c->stream))) return s;
+    if ((s = upload(c, c->red_n, no.data(), n * sizeof(double), c->stream))) return s;
+    if ((s = upload(c, c->red_u, u.data(), n * sizeof(double), c->stream))) return s;
+    if ((s = upload(c, c->red_b, b.data(), n * sizeof(int), c->stream))) return s;
+    if ((s = upload(c, c->red_uidx, uidx.data(), uidx.size() * sizeof(int), c->stream))) return s;
+    for (int w = 0; w < 2; ++w) {
+        c->red_ntl[w] = (int)tl[w].size();
+        if (!tl[w].empty() &&
+            (s = upload(c, c->red_tl[w], tl[w].data(), tl[w].size() * sizeof(TileDesc), c->stream)))
+            return s;
+    }
+    if ((s = cuda_check(cudaStreamSynchronize(c->stream), "set_redundancy"))) return s;
+    c->have_red = true;
+    c->red_nf = nf;
+    if (n_unique) *n_unique = (int64_t)r.rep_a.size();
+    return MV_OK;
+}
+
+mv_status mv_simulate_unique(mv_ctx* c, int n_t, const double* lst, int n_nu, const double* nu, mv_precision prec,
+                             void* V, int V_on_device, void* stream) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (n_t < 0 || n_nu < 0 || (n_t > 0 && !lst) || (n_nu > 0 && !nu)) return fail(MV_ERR_ARG, "bad time/frequency lists");
+    if (!c->have_red) return fail(MV_ERR_STATE, "no redundancy plan (mv_set_redundancy)");
+    DeviceGuard g(c->device);
+    Plan P;
+    plan_grid(c, n_t, lst, n_nu, nu, P);
+    P.unique = true;
+    const long long per = (long long)c->red.rep_a.size() * c->model.n_feed * c->model.n_feed;
+    for (size_t i = 0; i < P.inst.size(); ++i) P.inst[i].v_off = (long long)i * per;
+    cudaStream_t st = stream ? (cudaStream_t)stream : c->stream;
+    return run(c, P, prec, V, V_on_device, st);
 }
 
 mv_status mv_redundancy_plan(int n_ant, const double* enu, const int32_t* beam_idx, double tol_m, int n_feed,

@@ -76,6 +76,25 @@ struct Model {
     int interp;              // 0 cubic, 1 bilinear
 };
 
+// A tile of a listed cover (the redundant-baseline expansion): A rows [r0,
+// r0 + 128) and B rows [c0, c0 + ncol) of U; its entries with a row >= rlim
+// or a column >= clim belong to no block of the cover.
+struct TileDesc {
+    int r0, c0, ncol, rlim, clim, pad0, pad1, pad2;
+};
+
+// What the tensor-core HERK writes: the full V (uidx NULL), or one value per
+// redundant group, V_u[inst][g][p][q]: uidx[a * n_ant + b] (antennas in the
+// cover's order) = 2 g + conj where entry (a, b) of V computes group g's
+// representative (conj: the representative is its conjugate), else -1.  tl:
+// the tiles of the cover (NULL: the lower triangle), n_tl of them.
+struct HerkOut {
+    const TileDesc* tl;
+    int n_tl;
+    const int* uidx;
+    int n_ant, n_feed;
+};
+
 // ------------------------------------------------------------ host launchers
 // (defined in the .cu files; all enqueue on `st` and return the CUDA error)
 cudaError_t launch_cull(const Model& m, const double* d_R, int n_times, LiveTables lt,
@@ -170,8 +189,8 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                            const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows,
                            long long k_pitch, int n_slots, int fp16, const float* d_amax, float2* d_v,
                            int N, int flush_kblocks, int split, int bn, int n_ctas, int* d_sched,
-                           float* d_partial, int* d_err, const ZJob* zj, int zprec, cudaStream_t st,
-                           long long* launches);
+                           float* d_partial, int* d_err, const ZJob* zj, int zprec, const HerkOut* out,
+                           cudaStream_t st, long long* launches);
 // Whether the HERK can carry the Z build (tile width 128; one feed and one
 // axis, or two and two; BF16x3 or FP16x3).
 bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed);

@@ -143,32 +143,60 @@ constexpr uint32_t idesc_for(bool fp16, int bn) {
 // first, and the CTAs running at one time share k-ranges of one instance, so
 // each 64-column block of U is read from HBM about once and reused via L2.
 struct Unit {
-    int slot, ti, c0, ncol, kb0, kb1;  // row panel, first column and width of the tile
+    int slot, r0, c0, ncol, kb0, kb1;  // first A row, first B row and width of the tile
+    int rlim, clim;                    // rows / columns past these belong to no block
     int part;  // index of the unit's partial tile: (slot n_tiles + tile) S + ks
 };
 
 // 128-row boxes of U that hold a tile's B rows [c0, c0 + ncol).
 __host__ __device__ __forceinline__ int n_boxes(int ncol) { return (ncol + BM - 1) / BM; }
 
-// A diagonal tile's A rows [ti BM, ti BM + BM) are one of the 128-row boxes
-// of its B rows: the tile loads B only and reads A from B's box diag_box
-// (-1: not a diagonal tile).
-__host__ __device__ __forceinline__ int diag_box(int ti, int c0, int ncol) {
-    const int d = ti * BM - c0;
-    return d >= 0 && d < n_boxes(ncol) * BM ? d / BM : -1;
+// A diagonal tile's A rows [r0, r0 + BM) are one of the 128-row boxes of its
+// B rows: the tile loads B only and reads A from B's box diag_box (-1: not a
+// diagonal tile).
+__host__ __device__ __forceinline__ int diag_box(int r0, int c0, int ncol) {
+    const int d = r0 - c0;
+    return d >= 0 && d % BM == 0 && d < n_boxes(ncol) * BM ? d / BM : -1;
+}
+
+// Entry (a, b) of V (antenna-feed indices in the cover's order) from the 2 x 2
+// block g of G, written to its redundant group's slot if it computes one.
+__device__ __forceinline__ void put_unique(const HerkOut& ho, float2* Vb, int a, int b, float g00, float g01,
+                                           float g10, float g11, float unscale) {
+    const int nf = ho.n_feed;
+    const int aa = a / nf, pa = a - aa * nf, bb = b / nf, pb = b - bb * nf;
+    const int e = ho.uidx[aa * ho.n_ant + bb];
+    if (e < 0) return;
+    const int grp = e >> 1;
+    const bool cj = (e & 1) != 0;
+    const float re = ((g00 + g11) * unscale) * unscale;
+    const float im = a == b ? 0.f : ((g10 - g01) * unscale) * unscale;
+    Vb[((long long)grp * nf + (cj ? pb : pa)) * nf + (cj ? pa : pb)] = make_float2(re, cj ? -im : im);
 }
 
 template <int BN>
 __device__ __forceinline__ Unit decode_unit(int u, int n_tiles, int S, const int* __restrict__ order,
                                             const Inst* __restrict__ inst, int inst0, const LiveTables& lt,
-                                            int n_ax, int rows) {
+                                            int n_ax, int rows, const HerkOut& ho) {
     Unit w;
     const int tile = u % n_tiles;
     const int rest = u / n_tiles;
     const int ks = rest % S;
     w.slot = order[rest / S];
     w.part = (w.slot * n_tiles + tile) * S + ks;
-    tile_at<BN>(tile, rows, w.ti, w.c0, w.ncol);
+    if (ho.tl) {
+        const TileDesc d = ho.tl[tile];
+        w.r0 = d.r0;
+        w.c0 = d.c0;
+        w.ncol = d.ncol;
+        w.rlim = d.rlim;
+        w.clim = d.clim;
+    } else {
+        int ti;
+        tile_at<BN>(tile, rows, ti, w.c0, w.ncol);
+        w.r0 = ti * BM;
+        w.rlim = w.clim = rows;
+    }
     const long long K = (long long)lt.n_live[inst[inst0 + w.slot].t] * n_ax;
     const long long KB = ((K + kKPad - 1) / kKPad * kKPad) / bk_for<BN>();
     w.kb0 = (int)(KB * ks / S);
@@ -207,7 +235,7 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
           const Inst* __restrict__ inst, int inst0, LiveTables lt, int n_ax, uint32_t idesc, int fp16,
           const float* __restrict__ amax, float2* __restrict__ V, int N, int n_tiles, int n_units, int S,
           int flush, const int* __restrict__ order, int* __restrict__ counter, float* __restrict__ partial,
-          int* __restrict__ err, const __grid_constant__ ZJob zj) {
+          int* __restrict__ err, const __grid_constant__ ZJob zj, const HerkOut ho) {
     constexpr bool FZ = ZP != 0;
     using C = Cfg<BN, zwarps(ZP, ZA, ZF)>;
     constexpr int STAGES = C::STAGES, STAGE_BYTES = C::STAGE_BYTES, A_BYTES = C::A_BYTES, B_BYTES = C::B_BYTES;
@@ -260,8 +288,8 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 qslot[q] = u;
                 mbar_arrive(qfull(q));
                 if (u < 0) break;
-                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N);
-                const bool diag = diag_box(w.ti, w.c0, w.ncol) >= 0;
+                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N, ho);
+                const bool diag = diag_box(w.r0, w.c0, w.ncol) >= 0;
                 const int nb = BN == 128 ? 1 : n_boxes(w.ncol);  // full tiles at 128 columns
                 const uint32_t bytes = (uint32_t)(2 * nb * SUB + (diag ? 0 : 2 * A_BYTES));
                 bool ok = true;
@@ -273,8 +301,8 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                     const uint32_t st = sbase + s * STAGE_BYTES;
                     const int x = kb * BK;
                     if (!diag) {
-                        tma_load_3d(st, &map_hi, x, w.ti * BM, w.slot, full(s));
-                        tma_load_3d(st + A_BYTES, &map_lo, x, w.ti * BM, w.slot, full(s));
+                        tma_load_3d(st, &map_hi, x, w.r0, w.slot, full(s));
+                        tma_load_3d(st + A_BYTES, &map_lo, x, w.r0, w.slot, full(s));
                     }
                     for (int h = 0; h < nb; ++h) {
                         tma_load_3d(st + 2 * A_BYTES + h * SUB, &map_hi, x, w.c0 + h * BM, w.slot, full(s));
@@ -293,9 +321,9 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 const int u = qslot[q];
                 mbar_arrive(qempty(q));
                 if (u < 0) break;
-                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N);
+                const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N, ho);
                 // A's offset in the stage: its own slot, or the matching half of B
-                const int dh = diag_box(w.ti, w.c0, w.ncol);
+                const int dh = diag_box(w.r0, w.c0, w.ncol);
                 const uint32_t a_off = dh < 0 ? 0u : (uint32_t)(2 * A_BYTES + dh * SUB);
                 const uint32_t a_lo_off = dh < 0 ? (uint32_t)A_BYTES : a_off + (uint32_t)B_BYTES;
                 // N of the tile's MMAs: its width
@@ -345,9 +373,9 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             __syncwarp();
             if (lane == 0) mbar_arrive(qempty(qi));
             if (u < 0) break;
-            const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N);
+            const Unit w = decode_unit<BN>(u, n_tiles, S, order, inst, inst0, lt, n_ax, 2 * N, ho);
             const int rl = q4 * 32 + lane;  // row of the tile held by this thread
-            const int r = w.ti * BM + rl;
+            const int r = w.r0 + rl;
             const int a = r >> 1;
             const bool even = (lane & 1) == 0;
             float2* Vb = V + inst[inst0 + w.slot].v_off;
@@ -375,6 +403,11 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                     const float g00 = even ? x0 : y0, g01 = even ? x1 : y1;
                     const float g10 = even ? y0 : x0, g11 = even ? y1 : x1;
                     const int b = (c0 + g * NCOL + 2 * jj) >> 1;
+                    if (ho.uidx) {  // one value per redundant group
+                        if ((jj & 1) == (lane & 1) && r < w.rlim && 2 * b < w.clim && a < N && b < N)
+                            put_unique(ho, Vb, a, b, g00, g01, g10, g11, unscale);
+                        continue;
+                    }
                     if ((jj & 1) == (lane & 1) && a < N && b < N && a >= b) {
                         const float re = ((g00 + g11) * unscale) * unscale;
                         // autocorrelations are real: the tensor core rounds the two
@@ -489,16 +522,29 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
 template <int BN>
 __global__ void __launch_bounds__(256)
 k_herk_finalize(const Inst* __restrict__ inst, int inst0, int fp16, const float* __restrict__ amax,
-                const float* __restrict__ partial, float2* __restrict__ V, int N, int n_tiles, int S) {
+                const float* __restrict__ partial, float2* __restrict__ V, int N, int n_tiles, int S,
+                const HerkOut ho) {
     const int st = blockIdx.x;
     const int slot = st / n_tiles, tile = st % n_tiles;
-    int ti, c0, ncol;
-    tile_at<BN>(tile, 2 * N, ti, c0, ncol);
+    int r0, c0, ncol, rlim = 2 * N, clim = 2 * N;
+    if (ho.tl) {
+        const TileDesc d = ho.tl[tile];
+        r0 = d.r0;
+        c0 = d.c0;
+        ncol = d.ncol;
+        rlim = d.rlim;
+        clim = d.clim;
+    } else {
+        int ti;
+        tile_at<BN>(tile, 2 * N, ti, c0, ncol);
+        r0 = ti * BM;
+    }
     const int q = blockIdx.y * 256 + threadIdx.x;  // 2 x 2 block index within the tile
     const int rp = q % (BM / 2), cp = q / (BM / 2);
     const int r = 2 * rp, c = 2 * cp;
-    const int a = (ti * BM + r) >> 1, b = (c0 + c) >> 1;
-    if (c >= ncol || a >= N || b >= N || a < b) return;
+    const int a = (r0 + r) >> 1, b = (c0 + c) >> 1;
+    if (c >= ncol || a >= N || b >= N || r0 + r >= rlim || c0 + c >= clim) return;
+    if (!ho.uidx && a < b) return;
     float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
     for (int ks = 0; ks < S; ++ks) {
         const float* p = partial + ((long long)st * S + ks) * (BN * BM);
@@ -510,9 +556,13 @@ k_herk_finalize(const Inst* __restrict__ inst, int inst0, int fp16, const float*
         g11 += v1.y;
     }
     const float unscale = fp16 ? ldexpf(1.f, -fp16_scale_exp(amax[slot])) : 1.f;
+    float2* Vb = V + inst[inst0 + slot].v_off;
+    if (ho.uidx) {
+        put_unique(ho, Vb, a, b, g00, g01, g10, g11, unscale);
+        return;
+    }
     const float re = ((g00 + g11) * unscale) * unscale;
     const float im = a == b ? 0.f : ((g10 - g01) * unscale) * unscale;
-    float2* Vb = V + inst[inst0 + slot].v_off;
     Vb[(long long)a * N + b] = make_float2(re, im);
     if (a != b) Vb[(long long)b * N + a] = make_float2(re, -im);
 }
@@ -535,10 +585,10 @@ template <int BN, int ZP = 0, int ZA = 1, int ZF = 1>
 cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* d_inst, int inst0, int n_inst,
                       LiveTables lt, int n_ax, int fp16, const float* d_amax, float2* d_v, int N, int rows,
                       int flush, int split, int n_ctas, int* d_sched, float* d_partial, int* d_err,
-                      const ZJob* zj, cudaStream_t st, long long* launches) {
+                      const ZJob* zj, const HerkOut& ho, cudaStream_t st, long long* launches) {
     using C = Cfg<BN, zwarps(ZP, ZA, ZF)>;
     flush *= 64 / C::BK;  // the option counts 64-source blocks
-    const int n_tiles = n_tiles_for<BN>(rows);
+    const int n_tiles = ho.tl ? ho.n_tl : n_tiles_for<BN>(rows);
     const int n_units = n_tiles * n_inst * split;
     int* order = d_sched;            // [n_inst]
     int* counter = d_sched + n_inst;  // one int
@@ -552,13 +602,13 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
     k_herk_tc<BN, ZP, ZA, ZF><<<grid, C::THREADS, C::SMEM, st>>>(mh, ml, d_inst, inst0, lt, n_ax,
                                                                  idesc_for(fp16 != 0, BN), fp16, d_amax, d_v, N,
                                                                  n_tiles, n_units, split, flush, order, counter,
-                                                                 d_partial, d_err, z);
+                                                                 d_partial, d_err, z, ho);
     *launches += 2;
     if (split > 1) {
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         dim3 g2(n_tiles * n_inst, (BM / 2) * (BN / 2) / 256);
-        k_herk_finalize<BN><<<g2, 256, 0, st>>>(d_inst, inst0, fp16, d_amax, d_partial, d_v, N, n_tiles, split);
+        k_herk_finalize<BN><<<g2, 256, 0, st>>>(d_inst, inst0, fp16, d_amax, d_partial, d_v, N, n_tiles, split, ho);
         *launches += 1;
     }
     return cudaGetLastError();
@@ -596,7 +646,7 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                            const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, int rows, long long k_pitch,
                            int n_slots, int fp16, const float* d_amax, float2* d_v, int N, int flush, int split,
                            int bn, int n_ctas, int* d_sched, float* d_partial, int* d_err, const ZJob* zj,
-                           int zprec, cudaStream_t st, long long* launches) {
+                           int zprec, const HerkOut* out, cudaStream_t st, long long* launches) {
     CUtensorMap mh, ml;
     const int bk = (zj || bn == 128) ? bk_for<128>() : bk_for<256>();
     if (!make_map(&mh, d_hi, k_pitch, rows, n_slots, fp16, bk) || !make_map(&ml, d_lo, k_pitch, rows, n_slots, fp16, bk))
@@ -604,9 +654,15 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
     if (flush < 1) flush = 4;
     if (split < 1) split = 1;
     if ((split > 1 && !d_partial) || !d_sched || n_inst > 4096) return cudaErrorInvalidValue;
+    HerkOut ho{};
+    if (out) {
+        ho = *out;
+        // a listed cover at 128 columns holds full-width tiles only
+        if (ho.n_feed < 1 || ho.n_ant < 1 || !ho.uidx || (ho.tl && ho.n_tl < 1)) return cudaErrorInvalidValue;
+    }
 #define MV_LB(BN_, ZP_, ZA_, ZF_)                                                                                \
     return launch_bn<BN_, ZP_, ZA_, ZF_>(mh, ml, d_inst, inst0, n_inst, lt, n_ax, fp16, d_amax, d_v, N, rows, flush, \
-                                         split, n_ctas, d_sched, d_partial, d_err, zj, st, launches)
+                                         split, n_ctas, d_sched, d_partial, d_err, zj, ho, st, launches)
     if (zj) {
         if (!herk_tc_fusable(bn, zprec, zj->m.n_ax, zj->m.n_feed)) return cudaErrorInvalidValue;
         if (zj->m.n_ax == 1) {

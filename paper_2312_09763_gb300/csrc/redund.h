@@ -18,7 +18,7 @@ struct RedPlan {
     // each, the first member in lexicographic order
     std::vector<int> rep_a, rep_b;
     // per baseline (a <= b, row-major over a then b): its group, and whether
-    // V_ab is the conjugate of the representative's visibility
+    // it is a reversed baseline of the group (V_ab^{pq} = conj(V_rep^{qp}))
     std::vector<int> group_of;
     std::vector<int8_t> conj_of;
     // the cover: kind 0 = the whole lower triangle (no sub-matrices), 1 =
