@@ -67,6 +67,9 @@ def parse():
                          "beams replaced by the trained surrogate)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="Z build / HERK overlap (mv_options.overlap_batches)")
+    ap.add_argument("--unique", action="store_true",
+                    help="one value per redundant baseline group (mv_simulate_unique, Appendix A); value counts "
+                         "the baselines the groups represent")
     ap.add_argument("--max-batch", type=int, default=0, help="instances per launch (mv_options.max_batch; 0 = auto)")
     ap.add_argument("--sweep", action="store_true",
                     help="scaling sweep instead of the benchmark line: time per instance over sources 2^10..2^19 "
@@ -305,6 +308,12 @@ def main():
     sim.init_sky(w.ra, w.dec, w.flux_ref, w.spec_idx, w.nu_ref)
     sim.set_beam(w.beam)
     sim.set_antennas(w.enu, w.beam_idx, w.lat)
+    n_unique = None
+    if args.unique:
+        if args.workload in ("uneven", "learned"):
+            raise SystemExit("--unique: hera or diffuse workload")
+        n_unique = sim.set_redundancy(1e-3)
+        args.no_autotune = True  # the cover has its own tile list and configuration
     learned = None
     if args.workload == "learned":
         # no host round trip of the 5.5 GB of per-antenna grids each step, and
@@ -328,8 +337,10 @@ def main():
     N = w.n_ant
     nf, nax = sim.n_feed, sim._n_ax()
     shape = (len(w.lsts), N * nf, N * nf) if pairs else (len(w.lsts), len(w.freqs), N * nf, N * nf)
+    if n_unique is not None:
+        shape = (len(w.lsts), len(w.freqs), n_unique, nf, nf)
     V = torch.empty(shape, dtype=torch.complex64, device=f"cuda:{local}")
-    run = sim.simulate_pairs if pairs else sim.simulate
+    run = sim.simulate_pairs if pairs else (sim.simulate_unique if n_unique is not None else sim.simulate)
     stream = torch.cuda.current_stream()
     if learned is None:
         tuning = None
@@ -398,6 +409,24 @@ def main():
             roof["hbm_achieved_gbs"] = 2 * z_bytes * args.steps / (ms_h / 1e3) / 1e9
             roof["hbm_frac"] = roof["hbm_achieved_gbs"] / hbm
             roof["hbm_peak_gbs"] = hbm
+    unique_info = None
+    if n_unique is not None and roof is not None:
+        # the redundant-group output: the HERK computes the cover's blocks only;
+        # algorithmic work = the sub-matrix area (real rows) of Appendix A
+        from paper_2312_09763_gb300 import redundancy_plan
+        plan = redundancy_plan(w.enu, w.beam_idx, 1e-3, nf, 256)
+        if plan["kind"] == 0:
+            area = rows * (rows + 1) / 2
+        else:
+            area = float(sum(4 * nf * nf * (r1 - r0) * (c1 - c0) for r0, r1, c0, c1 in plan["blocks"]))
+        flops_u = float(np.sum(3 * 2.0 * area * K))
+        roof.update({"achieved": flops_u * args.steps / (ms_h / 1e3) / 1e12,
+                     "kernel": "k_herk_tc over the redundant-group cover", "traffic": None})
+        roof["frac"] = roof["achieved"] / sustained
+        unique_info = {"n_unique": n_unique, "cover_kind": plan["kind"], "cover_blocks": plan["blocks"].tolist(),
+                       "cover_tiles": plan["tiles"], "triangle_tiles": plan["tiles_full"],
+                       "unique_vis_per_s": world * n_unique * nf * nf * n_instances(w, pairs) * args.steps
+                       / (ms_max / 1e3)}
     if learned is not None:
         # the surrogate's forward pass dominates: 2 x multiply-adds per row of
         # the network, one row per (antenna beam, live source) of each instance
@@ -417,7 +446,9 @@ def main():
                 "kernel": "k_mlp_wa (learned-beam forward + WA, tcgen05)",
                 "launches": n_b, "avg_launch_ms": ms_b / max(n_b, 1),
                 "peak_source": f"{src} bf16 sustained (kernels timed inside a long step)"}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    metric = METRIC if n_unique is None else \
+        "vis/s (bl·chan·time) represented by one value per redundant baseline group (Appendix A)"
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": w.name, "instances_per_step": n_instances(w, pairs),
@@ -425,6 +456,7 @@ def main():
                        "l2": "inputs larger than L2: Z planes of one batch ~4.5 GB, re-streamed each step",
                        "parallelism": f"{world} replica(s), instances simulated independently"},
             "gpu_launches": launches, "roofline": roof, "clocks": clk, "herk_tuning": tuning, "learned_beam": learned,
+            "redundant_groups": unique_info,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
     if rank == 0 and not args.no_e2e:
@@ -450,6 +482,8 @@ def main():
             sim.init_sky(ra, dec, fl, si, w.nu_ref)
             sim.set_beam(beam)
             sim.set_antennas(enu, None, w.lat)
+            if n_unique is not None:
+                sim.set_redundancy(1e-3)  # the plan belongs to the antennas just set
             run(w.lsts, w.freqs, args.precision, out=Vh, host=True)
         e2e_step()  # warm-up: the host-output staging buffer and its captured launch sequence
         e2e_steps = max(1, min(args.steps, 3))

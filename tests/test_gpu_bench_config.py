@@ -55,3 +55,23 @@ def test_diffuse_workload_as_benchmarked():
     sim.simulate(w.lsts, w.freqs, "fp16x3", out=V)
     torch.cuda.synchronize()
     check(sim, w, P, V, [(0, 0), (119, 31), (60, 15), (7, 28)], 100, 2, seed=12)
+
+
+def test_hera_redundant_groups_as_benchmarked():
+    # bench.py --unique: one value per redundant group over the whole workload
+    # (cover of the representatives, 256-column tiles, CUDA graph); every
+    # group of four instances against the oracle at its representative
+    from paper_2312_09763_gb300 import redundancy_plan
+    w = synth.hera_like()
+    P = oracle_problem(w)
+    sim = simulator(w)
+    n_u = sim.set_redundancy(1e-3)
+    plan = redundancy_plan(w.enu, None, 1e-3, 1, 256)
+    assert plan["kind"] in (1, 2) and plan["tiles"] < plan["tiles_full"]
+    V = torch.empty((60, 64, n_u, 1, 1), dtype=torch.complex64, device="cuda")
+    for _ in range(2):  # capture, then replay
+        sim.simulate_unique(w.lsts, w.freqs, "fp16x3", out=V)
+    torch.cuda.synchronize()
+    for it, ic in [(0, 0), (59, 63), (30, 17), (11, 50)]:
+        vo = oracle.vis(P, w.lsts[it], w.freqs[ic], pairs=(plan["rep_a"], plan["rep_b"]))
+        assert rel_err(V[it, ic].cpu().numpy(), vo) <= 1e-5, (it, ic)
