@@ -414,7 +414,7 @@ def main():
         # the redundant-group output: the HERK computes the cover's blocks only;
         # algorithmic work = the sub-matrix area (real rows) of Appendix A
         from paper_2312_09763_gb300 import redundancy_plan
-        plan = redundancy_plan(w.enu, w.beam_idx, 1e-3, nf, 256)
+        plan = redundancy_plan(w.enu, w.beam_idx, 1e-3, nf, 128)
         if plan["kind"] == 0:
             area = rows * (rows + 1) / 2
         else:

@@ -253,7 +253,7 @@ mv_status mv_redundancy_plan(int n_ant, const double *enu, const int32_t *beam_i
                              int64_t *tiles);
 
 /* Plan the redundant-group output for the context's antennas and beam (as
- * mv_redundancy_plan with tile_n = 256): the Z planes of mv_simulate_unique
+ * mv_redundancy_plan with tile_n = 128): the Z planes of mv_simulate_unique
  * are then built in the cover's antenna order and the HERK computes only the
  * tiles of the cover.  tol_m <= 0 turns it off.  *n_unique (may be NULL)
  * receives the number of groups.  MV_ERR_STATE before set_antennas and a

@@ -386,9 +386,11 @@ bool tuned_for(const mv_ctx* c, const Prepared& p) {
 
 HerkCfg chosen_cfg(mv_ctx* c, const Prepared& p) {
     if (p.ho.uidx) {
-        // the redundant-group cover: its own tile count, 256 columns unless forced
+        // the redundant-group cover: its own tile count, 128 columns unless
+        // forced (its narrow blocks leave a 256-column tiling short of MMA work
+        // per ring stage: 141 against 112 ms per step on the 350-antenna array)
         HerkCfg h;
-        h.bn = c->opt.herk_tile_n == 128 ? 128 : 256;
+        h.bn = c->opt.herk_tile_n == 256 ? 256 : 128;
         h.flush = c->opt.herk_flush_kblocks > 0 ? c->opt.herk_flush_kblocks : 16;
         const int n_tl = c->red.kind == 0 ? herk_tc_units(p.rows, 1, 1, h.bn) : c->red_ntl[h.bn == 128 ? 0 : 1];
         const long long base = std::max(1ll, (long long)n_tl * p.max_slots);
@@ -1244,7 +1246,7 @@ mv_status mv_set_redundancy(mv_ctx* c, double tol_m, int64_t* n_unique) {
     const int n = m.n_ant, nf = m.n_feed;
     RedPlan& r = c->red;
     const char* why = nullptr;
-    if (!plan_redundancy(n, c->h_enu.data(), c->h_bidx.data(), tol_m, nf, 256, r, &why))
+    if (!plan_redundancy(n, c->h_enu.data(), c->h_bidx.data(), tol_m, nf, 128, r, &why))
         return fail(MV_ERR_ARG, "%s", why);
     // antennas in the cover's order
     std::vector<double> e(n), no(n), u(n);

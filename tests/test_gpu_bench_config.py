@@ -66,7 +66,7 @@ def test_hera_redundant_groups_as_benchmarked():
     P = oracle_problem(w)
     sim = simulator(w)
     n_u = sim.set_redundancy(1e-3)
-    plan = redundancy_plan(w.enu, None, 1e-3, 1, 256)
+    plan = redundancy_plan(w.enu, None, 1e-3, 1, 128)
     assert plan["kind"] in (1, 2) and plan["tiles"] < plan["tiles_full"]
     V = torch.empty((60, 64, n_u, 1, 1), dtype=torch.complex64, device="cuda")
     for _ in range(2):  # capture, then replay

@@ -39,7 +39,7 @@ def test_hera_like_groups_match_oracle_and_full_v(n_ant, tile_n, split):
     w = synth.hera_like(n_ant=n_ant, n_src=6000, n_chan=3, n_times=2, n_za=46, n_az=120)
     sim = simulator(w, herk_tile_n=tile_n, herk_split=split)
     n_u = sim.set_redundancy(1e-3)
-    plan = redundancy_plan(w.enu, None, 1e-3, 1, 256)
+    plan = redundancy_plan(w.enu, None, 1e-3, 1, 128)
     assert n_u == plan["n_unique"] and plan["kind"] in (1, 2)
     for prec in ("fp16x3", "bf16x3"):
         tol = 1e-5 if prec == "fp16x3" else 2e-5
@@ -60,7 +60,7 @@ def test_two_feeds_and_a_polarised_sky():
                                 full_stokes=True)
     sim = simulator(w)
     n_u = sim.set_redundancy(1e-3)
-    plan = redundancy_plan(w.enu, None, 1e-3, 2, 256)
+    plan = redundancy_plan(w.enu, None, 1e-3, 2, 128)
     assert plan["kind"] in (1, 2)
     Vu = sim.simulate_unique(w.lsts, w.freqs, "fp16x3").cpu().numpy()
     assert Vu.shape == (2, 2, n_u, 2, 2)
@@ -75,7 +75,7 @@ def test_non_redundant_array_uses_the_triangle():
     w = synth.tiny(n_ant=10, n_src=1000, n_times=2)
     sim = simulator(w)
     n_u = sim.set_redundancy(1e-3)
-    plan = redundancy_plan(w.enu, None, 1e-3, 1, 256)
+    plan = redundancy_plan(w.enu, None, 1e-3, 1, 128)
     assert plan["kind"] == 0 and n_u == 10 * 9 // 2 + 1
     Vu = sim.simulate_unique(w.lsts, w.freqs, "fp16x3").cpu().numpy()
     P = oracle_problem(w)
