@@ -72,23 +72,23 @@ __host__ __device__ __forceinline__ int panel_cmax(int ti, int rows) {
 
 template <int BN>
 __host__ __device__ __forceinline__ void tile_at(int idx, int rows, int& ti, int& c0, int& ncol) {
-    if (BN == 128) {  // panel i holds i + 1 full tiles
+    if constexpr (BN == 128) {  // panel i holds i + 1 full tiles
         int i = 0;
         while (idx > i) idx -= ++i;
         ti = i;
         c0 = idx * BN;
         ncol = BN;
-        return;
-    }
-    for (int i = 0;; ++i) {
-        const int cmax = panel_cmax<BN>(i, rows), nch = (cmax + BN - 1) / BN;
-        if (idx < nch) {
-            ti = i;
-            c0 = idx * BN;
-            ncol = min(BN, cmax - c0);
-            return;
+    } else {
+        for (int i = 0;; ++i) {
+            const int cmax = panel_cmax<BN>(i, rows), nch = (cmax + BN - 1) / BN;
+            if (idx < nch) {
+                ti = i;
+                c0 = idx * BN;
+                ncol = min(BN, cmax - c0);
+                return;
+            }
+            idx -= nch;
         }
-        idx -= nch;
     }
 }
 
