@@ -622,7 +622,8 @@ mv_status enqueue_ant_phase(mv_ctx* c, const Prepared& p, const Plan::Batch& b, 
                             long long* L) {
     Timed tz(c, MV_KERNEL_ZBUILD, st);
     cudaError_t e = launch_ant_phase(c->model, (const Inst*)c->inst.p, (const Chan*)c->chan.p,
-                                     (const ZGroup*)c->groups.p, b.g0, b.ng, (AntPhase*)c->aph[k].p, p.n_phase, st, L);
+                                     (const ZGroup*)c->groups.p, b.g0, b.ng, (AntPhase*)c->aph[k].p, p.n_phase,
+                                     p.zprec == 2 ? (float*)c->amax[k].p : nullptr, st, L);
     tz.end();
     return launched(e, "phase table", st);
 }
@@ -635,7 +636,7 @@ mv_status enqueue_zside(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int 
     if ((s = enqueue_wa(c, p, b, k, st, L))) return s;
     Timed tz(c, MV_KERNEL_ZBUILD, st);
     cudaError_t e = launch_zbuild(m, d_inst, (const Chan*)c->chan.p, (const ZGroup*)c->groups.p, b.g0, b.ng, p.lt,
-                      (const float2*)c->wa[k].p, p.pitch, (const float*)c->amax[k].p, c->u[k].p, c->ulo[k].p,
+                      (const float2*)c->wa[k].p, p.pitch, (float*)c->amax[k].p, c->u[k].p, c->ulo[k].p,
                       p.zprec, p.rows, p.k_pitch, p.nbuf == 2 && !p.fuse ? 4 * c->n_sms : 0, (AntPhase*)c->aph[k].p,
                       p.n_phase, st, L);
     tz.end();

@@ -163,16 +163,18 @@ struct ZJob {
     int n_phase;
 };
 
-// Antenna phase table of a batch (the first half of launch_zbuild).
+// Antenna phase table of a batch (the first half of launch_zbuild); with
+// d_amax (FP16 planes) it also gives every instance of a Z group the group's
+// max |WA|, so that one FP16 scale serves the whole group.
 cudaError_t launch_ant_phase(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
-                             int g_first, int n_groups, AntPhase* d_aph, int n_phase, cudaStream_t st,
-                             long long* launches);
+                             int g_first, int n_groups, AntPhase* d_aph, int n_phase, float* d_amax,
+                             cudaStream_t st, long long* launches);
 
 // d_aph: workspace for n_groups x n_phase x n_ant AntPhase entries, n_phase
 // >= max(2, largest group of the batch).
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
                           int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
-                          const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows,
+                          float* d_amax, void* d_u, void* d_u_lo, int prec, int rows,
                           long long k_pitch, int max_blocks, AntPhase* d_aph, int n_phase, cudaStream_t st,
                           long long* launches);
 cudaError_t launch_herk_fp32(const Inst* d_inst, int inst0, int n_inst, LiveTables lt, int n_ax,

@@ -22,11 +22,20 @@ using namespace zcore;
 // gl is kappa0 (e = 0) and dkappa (e = 1) of an equally spaced group, or the
 // wavenumber of its instance e otherwise.
 __global__ void k_ant_phase(Model m, const Inst* __restrict__ inst, const Chan* __restrict__ chan,
-                            const ZGroup* __restrict__ groups, int g_first, int n_phase, AntPhase* __restrict__ tab) {
+                            const ZGroup* __restrict__ groups, int g_first, int n_phase, AntPhase* __restrict__ tab,
+                            float* __restrict__ amax) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     const int e = blockIdx.y, gl = blockIdx.z;
-    if (a >= m.n_ant) return;
     const ZGroup g = groups[g_first + gl];
+    if (amax && blockIdx.x == 0 && e == 0 && threadIdx.x == 0) {
+        // one FP16 scale per group: every instance takes the group's max |WA|
+        // (the Z build folds the scale into its cos/sin factors; the HERK
+        // undoes it per instance from the same value)
+        float mx = 0.f;
+        for (int j = 0; j < g.n; ++j) mx = fmaxf(mx, amax[g.slot0 + j]);
+        for (int j = 0; j < g.n; ++j) amax[g.slot0 + j] = mx;
+    }
+    if (a >= m.n_ant) return;
     double kap;
     if (g.uniform) {
         if (e >= 2) return;
@@ -81,21 +90,22 @@ k_zbuild(Model m, const Inst* __restrict__ inst, const ZGroup* __restrict__ grou
 }  // namespace
 
 cudaError_t launch_ant_phase(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
-                             int g_first, int n_groups, AntPhase* d_aph, int n_phase, cudaStream_t st,
+                             int g_first, int n_groups, AntPhase* d_aph, int n_phase, float* d_amax, cudaStream_t st,
                              long long* launches) {
     if (!d_aph || n_phase < 2) return cudaErrorInvalidValue;
     k_ant_phase<<<dim3((unsigned)((m.n_ant + 127) / 128), (unsigned)n_phase, (unsigned)n_groups), 128, 0, st>>>(
-        m, d_inst, d_chan, d_groups, g_first, n_phase, d_aph);
+        m, d_inst, d_chan, d_groups, g_first, n_phase, d_aph, d_amax);
     *launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan, const ZGroup* d_groups,
                           int g_first, int n_groups, LiveTables lt, const float2* d_wa, long long wa_pitch,
-                          const float* d_amax, void* d_u, void* d_u_lo, int prec, int rows, long long k_pitch,
+                          float* d_amax, void* d_u, void* d_u_lo, int prec, int rows, long long k_pitch,
                           int max_blocks, AntPhase* d_aph, int n_phase, cudaStream_t st, long long* launches) {
     if (!lt.sfix) return cudaErrorInvalidValue;
-    cudaError_t e = launch_ant_phase(m, d_inst, d_chan, d_groups, g_first, n_groups, d_aph, n_phase, st, launches);
+    cudaError_t e = launch_ant_phase(m, d_inst, d_chan, d_groups, g_first, n_groups, d_aph, n_phase,
+                                     prec == 2 ? d_amax : nullptr, st, launches);
     if (e != cudaSuccess) return e;
     const int apb = 32;
     const int nx = (int)((lt.pitch / 2 + 127) / 128), ny = (m.n_ant + apb - 1) / apb;

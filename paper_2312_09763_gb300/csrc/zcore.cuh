@@ -74,9 +74,10 @@ __device__ __forceinline__ void cos_sin_turns(unsigned long long F, float& c, fl
 }
 
 // Store 2 n_ax consecutive entries of one row of U (two sources): FP32, or
-// the hi and lo halves (BF16 or, scaled by sc, FP16) in the two planes.
+// the hi and lo halves (BF16, or FP16 of values already scaled) in the two
+// planes.
 template <int PREC, int NAX>
-__device__ __forceinline__ void put_row(void* pu, void* pl, const float* v, float sc) {
+__device__ __forceinline__ void put_row(void* pu, void* pl, const float* v) {
     if constexpr (PREC == 0) {
         float* p = static_cast<float*>(pu);
         if constexpr (NAX == 1) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
@@ -85,8 +86,7 @@ __device__ __forceinline__ void put_row(void* pu, void* pl, const float* v, floa
         uint32_t hi[NAX], lo[NAX];
 #pragma unroll
         for (int i = 0; i < NAX; ++i) {
-            const float x0 = PREC == 2 ? v[2 * i] * sc : v[2 * i];
-            const float x1 = PREC == 2 ? v[2 * i + 1] * sc : v[2 * i + 1];
+            const float x0 = v[2 * i], x1 = v[2 * i + 1];
             if constexpr (PREC == 1) {
                 const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
                 const float2 hf = __bfloat1622float2(h);
@@ -113,9 +113,10 @@ __device__ __forceinline__ void put_row(void* pu, void* pl, const float* v, floa
 
 // Channels between exact phase evaluations when the channels of a group are
 // equally spaced: in between, cos(2 pi F) + i sin(2 pi F) advances by one
-// complex product with e^{2 pi i dF} per channel (three FP32 steps at most,
-// each adding about 2^-23 relative error).
-constexpr int kAnchor = 4;
+// complex product with e^{2 pi i dF} per channel (seven FP32 steps at most,
+// each adding about 2^-23 relative error); the WA values of kPrefetch
+// channels are loaded together.
+constexpr int kAnchor = 8, kPrefetch = 4;
 
 // Element type of the U planes.
 template <int PREC> struct Plane { using T = uint16_t; };
@@ -125,7 +126,8 @@ template <> struct Plane<0> { using T = float; };
 // adjacent sources 2 (bx nthr + tid) and +1 (columns 2 n_ax wide) for antennas
 // [by ant_per_block, +ant_per_block) and every instance of the group.
 // Sources past the live count (up to the k padding) are written as zeros
-// (their WA entries are zero).  scale[j]: the FP16 scale of instance j.
+// (their WA entries are zero).  scale[0]: the FP16 scale of the group (one
+// power of two for all its instances), folded into the cos/sin factors.
 template <int PREC, int NAX, int NFD>
 __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restrict__ inst, const ZGroup& g,
                                             const LiveTables& lt, const float2* __restrict__ wa,
@@ -161,6 +163,7 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
     T* const lb = PREC != 0 ? static_cast<T*>(ulo) + g.slot0 * slot_stride + col : nullptr;
     const float2* const wb = wa + g.slot0 * wa_slot + s0;
     const bool step = g.uniform && g.n > 1;
+    const float sc = PREC == 2 ? scale[0] : 1.f;
     for (int a = a_begin; a < a_end; ++a) {
         const float2* w = wb + (long long)m.beam_idx[a] * (NFD * NAX) * wa_pitch;
         T* ur = ub + 2ll * a * NFD * k_pitch;
@@ -173,9 +176,9 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
 #pragma unroll
             for (int c = 0; c < NC; ++c) A[c] = *reinterpret_cast<const float4*>(wj + (long long)c * wa_pitch);
         };
-        // U rows 2(a NFD + p) + {0, 1} of instance j of the group, at phase (c, s)
-        auto emit = [&](int j, const float4 (&A)[NC], float c0, float sn0, float c1, float sn1) {
-            const float sc = PREC == 2 ? scale[j] : 1.f;
+        // U rows 2(a NFD + p) + {0, 1} of the next instance of the group, at
+        // phase (c, s) (times the FP16 scale)
+        auto emit = [&](const float4 (&A)[NC], float c0, float sn0, float c1, float sn1) {
 #pragma unroll
             for (int p = 0; p < NFD; ++p) {
                 float re[2 * NAX], im[2 * NAX];
@@ -189,8 +192,8 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                     im[NAX + k] = fmaf(a4.w, c1, -a4.z * sn1);
                 }
                 const long long r0 = 2ll * p * k_pitch;
-                put_row<PREC, NAX>(ur + r0, PREC != 0 ? lr + r0 : nullptr, re, sc);
-                put_row<PREC, NAX>(ur + r0 + k_pitch, PREC != 0 ? lr + r0 + k_pitch : nullptr, im, sc);
+                put_row<PREC, NAX>(ur + r0, PREC != 0 ? lr + r0 : nullptr, re);
+                put_row<PREC, NAX>(ur + r0 + k_pitch, PREC != 0 ? lr + r0 + k_pitch : nullptr, im);
             }
             ur += slot_stride;
             if (PREC != 0) lr += slot_stride;
@@ -205,38 +208,45 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
             cos_sin_turns(Q0, rc0, rs0);
             cos_sin_turns(Q1, rc1, rs1);
             for (int j0 = 0; j0 < g.n; j0 += kAnchor) {
-                // one-component beams: the WA loads of the kAnchor channels go out together
-                constexpr int PF = NC == 1 ? kAnchor : 1;
-                float4 Apf[PF][NC];
-                if constexpr (PF > 1) {
-#pragma unroll
-                    for (int jj = 0; jj < PF; ++jj)
-                        if (j0 + jj < g.n) load_wa(jj, Apf[jj]);
-                }
                 float c0, sn0, c1, sn1;
                 cos_sin_turns(F0, c0, sn0);
                 cos_sin_turns(F1, c1, sn1);
+                c0 *= sc;
+                sn0 *= sc;
+                c1 *= sc;
+                sn1 *= sc;
                 F0 += Q0 * kAnchor;
                 F1 += Q1 * kAnchor;
 #pragma unroll
-                for (int jj = 0; jj < kAnchor; ++jj) {
-                    if (j0 + jj < g.n) {
-                        if constexpr (PF > 1) {
-                            emit(j0 + jj, Apf[jj], c0, sn0, c1, sn1);
-                        } else {
-                            load_wa(jj, Apf[0]);
-                            emit(j0 + jj, Apf[0], c0, sn0, c1, sn1);
+                for (int jb = 0; jb < kAnchor; jb += kPrefetch) {
+                    // one-component beams: the WA loads of kPrefetch channels go out together
+                    constexpr int PF = NC == 1 ? kPrefetch : 1;
+                    float4 Apf[PF][NC];
+                    if constexpr (PF > 1) {
+#pragma unroll
+                        for (int jj = 0; jj < PF; ++jj)
+                            if (j0 + jb + jj < g.n) load_wa(jj, Apf[jj]);
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < kPrefetch; ++jj) {
+                        if (j0 + jb + jj < g.n) {
+                            if constexpr (PF > 1) {
+                                emit(Apf[jj], c0, sn0, c1, sn1);
+                            } else {
+                                load_wa(jj, Apf[0]);
+                                emit(Apf[0], c0, sn0, c1, sn1);
+                            }
+                        }
+                        if (jb + jj + 1 < kAnchor) {  // (c + i s) e^{2 pi i dF}
+                            const float nc0 = fmaf(c0, rc0, -sn0 * rs0), nc1 = fmaf(c1, rc1, -sn1 * rs1);
+                            sn0 = fmaf(sn0, rc0, c0 * rs0);
+                            sn1 = fmaf(sn1, rc1, c1 * rs1);
+                            c0 = nc0;
+                            c1 = nc1;
                         }
                     }
-                    if (jj + 1 < kAnchor) {  // (c + i s) e^{2 pi i dF}
-                        const float nc0 = fmaf(c0, rc0, -sn0 * rs0), nc1 = fmaf(c1, rc1, -sn1 * rs1);
-                        sn0 = fmaf(sn0, rc0, c0 * rs0);
-                        sn1 = fmaf(sn1, rc1, c1 * rs1);
-                        c0 = nc0;
-                        c1 = nc1;
-                    }
+                    w += kPrefetch * wa_slot;
                 }
-                w += kAnchor * wa_slot;
             }
         } else {
             for (int j = 0; j < g.n; ++j) {
@@ -246,7 +256,7 @@ __device__ __forceinline__ void zbuild_item(const Model& m, const Inst* __restri
                 float c0, sn0, c1, sn1;
                 cos_sin_turns(phase64(pj, S0, E0), c0, sn0);
                 cos_sin_turns(phase64(pj, S1, E1), c1, sn1);
-                emit(j, A, c0, sn0, c1, sn1);
+                emit(A, c0 * sc, sn0 * sc, c1 * sc, sn1 * sc);
                 w += wa_slot;
             }
         }
