@@ -97,3 +97,27 @@ def test_unique_output_state_and_arguments():
     sim.set_antennas(w.enu, None, w.lat)
     with pytest.raises(MatvisError, match="MV_ERR_STATE"):
         sim.simulate_unique(w.lsts, w.freqs, "fp16x3")
+
+
+@pytest.mark.parametrize("every,kinds", [(10, (2,)), (25, (1,)), (3, (0,))])
+def test_two_beam_types_split_the_groups(every, kinds):
+    # every n-th antenna has a second beam: groups need equal beam pairs, so a
+    # reversed baseline between different beams joins only the group whose
+    # beams are swapped to match; the cover is a block of either orientation,
+    # or (with many such antennas) the whole triangle
+    w = synth.hera_like(n_ant=250, n_src=5000, n_chan=2, n_times=1, n_za=46, n_az=120)
+    grid = w.beam[1]
+    g2 = (grid * np.complex64(0.7 - 0.2j)).astype(np.complex64)
+    w.beam = ("grid", np.concatenate([grid, g2], axis=0)) + tuple(w.beam[2:])
+    w.beam_idx = (np.arange(w.n_ant) % every == 0).astype(np.int32)
+    sim = simulator(w)
+    n_u = sim.set_redundancy(1e-3)
+    plan = redundancy_plan(w.enu, w.beam_idx, 1e-3, 1, 128)
+    one = redundancy_plan(w.enu, None, 1e-3, 1, 128)
+    assert n_u == plan["n_unique"] > one["n_unique"] and plan["kind"] in kinds
+    Vu = sim.simulate_unique(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+    P = oracle_problem(w)
+    vo = oracle.vis(P, w.lsts[0], w.freqs[1], pairs=(plan["rep_a"], plan["rep_b"]))
+    assert rel_err(Vu[0, 1], vo) <= 1e-5
+    Vf = sim.simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+    assert rel_err(expand(Vu, plan, w.n_ant, 1), Vf) <= 2e-5
