@@ -91,10 +91,10 @@ typedef struct {
                                    workspace sets); 0 (default): one set, strictly in order */
     int fuse_zbuild;            /* 1 (default): with two or more batches and a tensor-core
                                    precision, the HERK launch of batch b also builds the Z matrices
-                                   of batch b + 1 on extra warps of every SM (two workspace sets,
-                                   128-column tiles; one feed and one axis, or two and two); 0: the
-                                   Z build runs as its own launch.  Takes precedence over
-                                   overlap_batches. */
+                                   of batch b + 1 on extra warps of every SM (two workspace sets;
+                                   one feed and one axis, or two and two), unless mv_autotune timed
+                                   separate launches faster for the call's shape; 0: the Z build
+                                   runs as its own launch.  Takes precedence over overlap_batches. */
 } mv_options;
 
 /* A tensor-core HERK configuration chosen by mv_autotune. */

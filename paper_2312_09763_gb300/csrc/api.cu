@@ -497,7 +497,7 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
     // the fused schedule unless the autotuner timed the separate one faster
     // for calls of this shape
-    p.fuse = c->opt.fuse_zbuild && p.zprec != 0 && P.batches.size() > 1 && c->opt.herk_tile_n != 256 &&
+    p.fuse = c->opt.fuse_zbuild && p.zprec != 0 && P.batches.size() > 1 &&
              herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed) && !(tuned_for(c, p) && !c->tuned.fuse) && !P.unique;
     p.nbuf = (P.batches.size() > 1 && (c->opt.overlap_batches || p.fuse)) ? 2 : 1;
     // antenna phase factors: per batch, groups x wavenumbers per group x antennas
@@ -816,7 +816,7 @@ mv_status run(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_device, c
     mv_status s = prepare(c, P, prec, V, V_on_device, st, p);
     if (s || p.n_inst == 0) return s;
     const HerkCfg h = chosen_cfg(c, p);
-    if (h.bn != 128) p.fuse = false;  // a tuned or forced 256-column tile runs the Z build on its own
+
     long long L = 0;
     // CUDA graph: the launch sequence is captured once per key (on the
     // context's own stream) and replayed on the caller's stream.  Kernel
@@ -891,11 +891,11 @@ mv_status autotune(mv_ctx* c, Plan& P, mv_precision prec, cudaStream_t st, mv_tu
     const Plan::Batch b0 = P.batches[0];
     std::vector<HerkCfg> cands;
     const long long est_kb = std::max(1ll, ((long long)c->model.n_ax * c->model.n_src / 2 + 63) / 64);
-    // fused trials (tile width 128) carry the Z build of the first batch into
-    // the second workspace set; separate trials run the HERK alone
+    // fused trials carry the Z build of the first batch into the second
+    // workspace set; separate trials run the HERK alone
     std::vector<bool> fused_trial;
     for (int fz = p.fuse ? 1 : 0; fz >= 0; --fz)
-        for (int bn : fz ? std::vector<int>{128} : std::vector<int>{128, 256})
+        for (int bn : {128, 256})
             for (int split : {1, 2, 4, 8, 16, 32, 64})
                 for (int flush : {4, 8, 16}) {
                     if (split > 1 && est_kb / split < 8) continue;

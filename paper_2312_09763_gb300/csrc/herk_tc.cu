@@ -102,12 +102,15 @@ int n_tiles_for(int rows) {
 
 // Kernel-wide configuration for a tile width BN (128 or 256 columns); ZW > 0:
 // the kernel also runs the Z build of the next batch on ZW extra warps, and
-// keeps the epilogue's running sums in TMEM (columns [2 BN, 3 BN)) so that
-// registers are free for them (the whole block fits 64 K registers).
+// keeps the epilogue's running sums in TMEM so that registers are free for
+// them: at 128 columns two accumulators [0, 256) and the sums [256, 384); at
+// 256 columns one accumulator [0, 256) and the sums [256, 512), the MMAs
+// waiting while the epilogue adds a finished chunk into the sums (SB).
 template <int BN, int ZW = 0>
 struct Cfg {
     static constexpr bool FZ = ZW > 0;
-    static_assert(!FZ || BN == 128, "the fused Z build runs with 128-column tiles");
+    static constexpr bool SB = FZ && BN == 256;                    // single accumulator buffer
+    static constexpr int RUN = SB ? BN : 2 * BN;                   // TMEM column of the running sums
     static constexpr int BK = bk_for<BN>();
     static constexpr int SUB = BM * BK * 2;                        // one 128-row box of one plane
     static constexpr int A_BYTES = SUB;                            // 16 or 8 KB per plane
@@ -330,8 +333,8 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 const uint32_t id = BN == 128 ? idesc : (idesc & ~(0x3Fu << 17)) | ((uint32_t)(w.ncol >> 3) << 17);
                 bool ok = true;
                 for (int kc = w.kb0; kc < w.kb1 && ok; kc += flush, ++cg) {
-                    const int buf = cg & 1;
-                    const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
+                    const int buf = C::SB ? 0 : cg & 1;
+                    const uint32_t ph = C::SB ? (uint32_t)cg & 1u : (uint32_t)(cg >> 1) & 1u;
                     if (!wait_bounded(tempty(buf), ph ^ 1u, abort_flag, err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(buf * BN);
@@ -448,14 +451,14 @@ k_herk_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                 for (int g = 0; g < 4; ++g)
                     if (g * 32 < ncv) write_chunk(std::integral_constant<int, 32>{}, g, run + g * 32);
             } else {
-                // running sums in TMEM columns [2 BN, 3 BN) of this warp's lanes,
-                // 16 columns at a time
-                const uint32_t tl = tmem_base + ((uint32_t)(q4 * 32) << 16);
-                const uint32_t trun = tl + 2 * BN;
+                // running sums in TMEM columns [RUN, RUN + BN) of this warp's lanes
+                // and 128-column group, 16 columns at a time
+                const uint32_t tl = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(h * 128);
+                const uint32_t trun = tl + C::RUN;
                 bool any = false;
                 for (int kc = w.kb0; kc < w.kb1; kc += flush, ++cg) {
-                    const int buf = cg & 1;
-                    const uint32_t ph = (uint32_t)(cg >> 1) & 1u;
+                    const int buf = C::SB ? 0 : cg & 1;
+                    const uint32_t ph = C::SB ? (uint32_t)cg & 1u : (uint32_t)(cg >> 1) & 1u;
                     if (!wait_bounded(tfull(buf), ph, abort_flag, err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t ta = tl + (uint32_t)(buf * BN);
@@ -631,11 +634,20 @@ cudaError_t herk_tc_init() {
         e = cudaFuncSetAttribute(k_herk_tc<128, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, f2);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<128, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, f2);
+    const int w1 = Cfg<256, zwarps(1, 1, 1)>::SMEM, w2 = Cfg<256, zwarps(1, 2, 2)>::SMEM;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<256, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, w1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<256, 2, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, w1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<256, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, w2);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_herk_tc<256, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, w2);
     return e;
 }
 
 bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed) {
-    return bn == 128 && (zprec == 1 || zprec == 2) && n_ax == n_feed && (n_ax == 1 || n_ax == 2);
+    return (bn == 128 || bn == 256) && (zprec == 1 || zprec == 2) && n_ax == n_feed && (n_ax == 1 || n_ax == 2);
 }
 
 int herk_tc_units(int rows, int n_slots, int split, int bn) {
@@ -648,7 +660,7 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                            int bn, int n_ctas, int* d_sched, float* d_partial, int* d_err, const ZJob* zj,
                            int zprec, const HerkOut* out, cudaStream_t st, long long* launches) {
     CUtensorMap mh, ml;
-    const int bk = (zj || bn == 128) ? bk_for<128>() : bk_for<256>();
+    const int bk = bn == 128 ? bk_for<128>() : bk_for<256>();
     if (!make_map(&mh, d_hi, k_pitch, rows, n_slots, fp16, bk) || !make_map(&ml, d_lo, k_pitch, rows, n_slots, fp16, bk))
         return cudaErrorInvalidValue;
     if (flush < 1) flush = 4;
@@ -665,6 +677,14 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                                          split, n_ctas, d_sched, d_partial, d_err, zj, ho, st, launches)
     if (zj) {
         if (!herk_tc_fusable(bn, zprec, zj->m.n_ax, zj->m.n_feed)) return cudaErrorInvalidValue;
+        if (bn == 256) {
+            if (zj->m.n_ax == 1) {
+                if (zprec == 1) MV_LB(256, 1, 1, 1);
+                MV_LB(256, 2, 1, 1);
+            }
+            if (zprec == 1) MV_LB(256, 1, 2, 2);
+            MV_LB(256, 2, 2, 2);
+        }
         if (zj->m.n_ax == 1) {
             if (zprec == 1) MV_LB(128, 1, 1, 1);
             MV_LB(128, 2, 1, 1);
