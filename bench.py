@@ -457,6 +457,8 @@ def main():
                        "parallelism": f"{world} replica(s), instances simulated independently"},
             "gpu_launches": launches, "roofline": roof, "clocks": clk, "herk_tuning": tuning, "learned_beam": learned,
             "redundant_groups": unique_info,
+            # two feeds: every baseline carries n_feed^2 polarisation products
+            "pol_products_per_s": value * nf * nf if nf > 1 else None,
             "kernel_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
 
     if rank == 0 and not args.no_e2e:
