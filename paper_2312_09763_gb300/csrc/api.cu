@@ -72,7 +72,7 @@ struct mv_ctx {
     Buf R, counts, offsets, le, ln, lu, lsfix, lseps, lidx, lazza, nlive, chan, inst, groups, planes, vdev, err, partial, sched;
     // per-batch workspace, double-buffered so that the beam evaluation and Z
     // build of one batch (on zstream) overlap the HERK of the previous one
-    Buf wa[2], amax[2], u[2], ulo[2], aph[2];
+    Buf wa[3], amax[3], u[2], ulo[2], aph[2];  // wa/amax: a third set when the beam runs two batches ahead
     cudaStream_t zstream = nullptr;
     cudaEvent_t ev_prep = nullptr, ev_zdone[2] = {nullptr, nullptr}, ev_hdone[2] = {nullptr, nullptr};
     // copies of each batch's V to pinned host memory, overlapping the next batches
@@ -352,6 +352,7 @@ struct Prepared {
     int N = 0, rows = 0, bpt = 0, ncomp = 0, max_slots = 0, zprec = 0;
     int nbuf = 1;  // workspace sets in use (2: Z side and HERK overlap, or fused Z build)
     bool fuse = false;  // the HERK of batch b builds the Z planes of batch b + 1
+    bool ahead = false;  // (fused) the beam of batch b + 2 runs on zstream beside the HERK of batch b
     int n_phase = 2;  // AntPhase entries per group
     const Plan* plan = nullptr;
     std::vector<int> h_nlive;  // live counts on the host (learned-beam calls only)
@@ -508,11 +509,14 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
         for (int gi = b.g0; gi < b.g0 + b.ng; ++gi)
             if (!P.groups[gi].uniform) p.n_phase = std::max(p.n_phase, P.groups[gi].n);
     }
-    for (int k = 0; k < p.nbuf; ++k) {
+    // the beam two batches ahead (fused, not the learned beam, whose kernel needs whole SMs)
+    p.ahead = p.fuse && !c->use_sur && P.batches.size() > 2;
+    for (int k = 0; k < (p.ahead ? 3 : p.nbuf); ++k) {
         if ((s = ensure(c, c->wa[k], sizeof(float2) * (size_t)max_slots * p.ncomp * pitch))) return s;
         if ((s = ensure(c, c->amax[k], sizeof(float) * (size_t)max_slots))) return s;
-        if ((s = ensure(c, c->aph[k], sizeof(AntPhase) * (size_t)max_groups * p.n_phase * m.n_ant))) return s;
     }
+    for (int k = 0; k < p.nbuf; ++k)
+        if ((s = ensure(c, c->aph[k], sizeof(AntPhase) * (size_t)max_groups * p.n_phase * m.n_ant))) return s;
     if ((s = ensure(c, c->sched, sizeof(int) * (size_t)(max_slots + 8)))) return s;
     const size_t plane_elems = (size_t)p.rows * p.k_pitch * max_slots;
     for (int k = 0; k < p.nbuf; ++k) {
@@ -560,8 +564,10 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
 }
 
 // HERK of one batch with configuration h.
+// (k: the workspace set of the batch's U planes; kw: of its WA and amax, k if < 0)
 cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, const HerkCfg& h, int k,
-                         cudaStream_t st, long long* L, const ZJob* zj = nullptr) {
+                         cudaStream_t st, long long* L, const ZJob* zj = nullptr, int kw = -1) {
+    if (kw < 0) kw = k;
     const Inst* d_inst = (const Inst*)c->inst.p;
     HerkOut ho = p.ho;
     if (ho.uidx) {
@@ -574,12 +580,13 @@ cudaError_t enqueue_herk(mv_ctx* c, const Prepared& p, const Plan::Batch& b, con
                                 p.k_pitch, p.Vout, p.N, 256, st, L);
     return launch_herk_tc(d_inst, b.inst0, b.n, p.lt, c->model.n_ax, (const __nv_bfloat16*)c->u[k].p,
                           (const __nv_bfloat16*)c->ulo[k].p, p.rows, p.k_pitch, p.max_slots, p.zprec == 2 ? 1 : 0,
-                          (const float*)c->amax[k].p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
+                          (const float*)c->amax[kw].p, p.Vout, p.N, h.flush, h.split, h.bn, c->n_sms, (int*)c->sched.p,
                           (float*)c->partial.p, (int*)c->err.p, zj, p.zprec, p.ho.uidx ? &ho : nullptr, st, L);
 }
 
 // The Z build of batch b into workspace set k, for the HERK of the batch before.
-ZJob make_zjob(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k) {
+ZJob make_zjob(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, int kw = -1) {
+    if (kw < 0) kw = k;
     ZJob z{};
     z.m = c->model;
     z.inst = (const Inst*)c->inst.p;
@@ -587,9 +594,9 @@ ZJob make_zjob(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k) {
     z.g_first = b.g0;
     z.n_groups = b.ng;
     z.lt = p.lt;
-    z.wa = (const float2*)c->wa[k].p;
+    z.wa = (const float2*)c->wa[kw].p;
     z.wa_pitch = p.pitch;
-    z.amax = (const float*)c->amax[k].p;
+    z.amax = (const float*)c->amax[kw].p;
     z.u = c->u[k].p;
     z.ulo = c->ulo[k].p;
     z.rows = p.rows;
@@ -619,11 +626,12 @@ mv_status enqueue_wa(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, 
 
 // Antenna phase table of one batch into workspace set k (fused Z build).
 mv_status enqueue_ant_phase(mv_ctx* c, const Prepared& p, const Plan::Batch& b, int k, cudaStream_t st,
-                            long long* L) {
+                            long long* L, int kw = -1) {
+    if (kw < 0) kw = k;
     Timed tz(c, MV_KERNEL_ZBUILD, st);
     cudaError_t e = launch_ant_phase(c->model, (const Inst*)c->inst.p, (const Chan*)c->chan.p,
                                      (const ZGroup*)c->groups.p, b.g0, b.ng, (AntPhase*)c->aph[k].p, p.n_phase,
-                                     p.zprec == 2 ? (float*)c->amax[k].p : nullptr, st, L);
+                                     p.zprec == 2 ? (float*)c->amax[kw].p : nullptr, st, L);
     tz.end();
     return launched(e, "phase table", st);
 }
@@ -689,23 +697,54 @@ mv_status enqueue_all(mv_ctx* c, Plan& P, Prepared& p, const HerkCfg& h, cudaStr
     if (p.fuse) {
         // batch 0 alone; then the HERK launch of batch b also builds the Z
         // planes of batch b + 1 (its beam evaluation and phase table first)
-        // into the other workspace set
+        // into the other workspace set.  With p.ahead the beam evaluation and
+        // phase table of batch b + 2 run on zstream beside the HERK of batch b
+        // (WA and amax in three sets, batch mod 3; U planes and phase tables in
+        // two, batch mod 2): zstream waits for the HERK of batch b - 1, the last
+        // reader of the sets it overwrites, and the HERK of batch b + 1 waits
+        // for them.
+        const size_t B = P.batches.size();
+        auto wset = [&](size_t i) { return p.ahead ? (int)(i % 3) : (int)(i & 1); };
+        cudaStream_t zs = c->zstream;
         if ((s = enqueue_zside(c, p, P.batches[0], 0, st, L))) return s;
-        for (size_t i = 0; i < P.batches.size(); ++i) {
+        if (p.ahead) {
+            if ((s = enqueue_wa(c, p, P.batches[1], wset(1), st, L))) return s;
+            if ((s = enqueue_ant_phase(c, p, P.batches[1], 1, st, L, wset(1)))) return s;
+            if ((s = cuda_check(cudaEventRecord(c->ev_prep, st), "event"))) return s;
+            if ((s = cuda_check(cudaStreamWaitEvent(zs, c->ev_prep, 0), "event wait"))) return s;
+        }
+        for (size_t i = 0; i < B; ++i) {
             const int k = (int)(i & 1);
             ZJob zj{};
-            const bool next = i + 1 < P.batches.size();
-            if (next) {
+            const bool next = i + 1 < B;
+            if (p.ahead) {
+                if (i + 2 < B) {
+                    if (i >= 1 && (s = cuda_check(cudaStreamWaitEvent(zs, c->ev_hdone[(i - 1) & 1], 0), "event wait")))
+                        return s;
+                    const auto& b2 = P.batches[i + 2];
+                    if ((s = enqueue_wa(c, p, b2, wset(i + 2), zs, L))) return s;
+                    if ((s = enqueue_ant_phase(c, p, b2, (int)((i + 2) & 1), zs, L, wset(i + 2)))) return s;
+                    if ((s = cuda_check(cudaEventRecord(c->ev_zdone[(i + 2) & 1], zs), "event"))) return s;
+                }
+                if (i >= 1 && next &&
+                    (s = cuda_check(cudaStreamWaitEvent(st, c->ev_zdone[(i + 1) & 1], 0), "event wait")))
+                    return s;
+            } else if (next) {
                 const auto& bn = P.batches[i + 1];
                 if ((s = enqueue_wa(c, p, bn, k ^ 1, st, L))) return s;
                 if ((s = enqueue_ant_phase(c, p, bn, k ^ 1, st, L))) return s;
-                zj = make_zjob(c, p, bn, k ^ 1);
             }
+            if (next) zj = make_zjob(c, p, P.batches[i + 1], k ^ 1, wset(i + 1));
             Timed th(c, MV_KERNEL_HERK, st);
-            e = enqueue_herk(c, p, P.batches[i], h, k, st, L, next ? &zj : nullptr);
+            e = enqueue_herk(c, p, P.batches[i], h, k, st, L, next ? &zj : nullptr, wset(i));
             th.end();
             if ((s = launched(e, "HERK tc", st))) return s;
+            if (p.ahead && (s = cuda_check(cudaEventRecord(c->ev_hdone[k], st), "event"))) return s;
             if ((s = copy_out(P.batches[i]))) return s;
+        }
+        if (p.ahead) {  // zstream rejoins st (it also joins a stream capture)
+            if ((s = cuda_check(cudaEventRecord(c->ev_prep, zs), "event"))) return s;
+            if ((s = cuda_check(cudaStreamWaitEvent(st, c->ev_prep, 0), "event wait"))) return s;
         }
         return join_copies();
     }
@@ -767,7 +806,8 @@ std::vector<long long> graph_key(mv_ctx* c, const Plan& P, const Prepared& p, co
                                 bits(m.daz), m.interp};
     const Buf* bufs[] = {&c->R, &c->chan, &c->inst, &c->groups, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu,
                          &c->lidx, &c->lazza, &c->nlive, &c->wa[0], &c->amax[0], &c->sched, &c->u[0], &c->ulo[0],
-                         &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->partial, &c->planes, &c->grid, &c->err,
+                         &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->wa[2], &c->amax[2], &c->partial,
+                         &c->planes, &c->grid, &c->err,
                          &c->lsfix, &c->lseps, &c->aph[0], &c->aph[1], &c->pol_m, &c->red_uidx, &c->red_tl[0],
                          &c->red_tl[1]};
     for (const Buf* b : bufs) k.push_back((long long)(uintptr_t)b->p);
@@ -1058,7 +1098,7 @@ void mv_destroy(mv_ctx* c) {
     Buf* all[] = {&c->xeq, &c->sqrt_flux, &c->half_alpha, &c->ant_e, &c->ant_n, &c->ant_u, &c->bidx, &c->grid,
                   &c->R, &c->counts, &c->offsets, &c->le, &c->ln, &c->lu, &c->lidx, &c->lazza, &c->nlive,
                   &c->chan, &c->inst, &c->groups, &c->planes, &c->wa[0], &c->amax[0], &c->u[0], &c->ulo[0],
-                  &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->vdev, &c->err,
+                  &c->wa[1], &c->amax[1], &c->u[1], &c->ulo[1], &c->wa[2], &c->amax[2], &c->vdev, &c->err,
                   &c->partial, &c->sched, &c->lsfix, &c->lseps, &c->aph[0], &c->aph[1], &c->pol_m};
     for (Buf* b : all) buf_free(c, *b);
     surrogate_destroy(c->sur);
