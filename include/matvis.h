@@ -197,6 +197,14 @@ mv_status mv_autotune(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const d
  * flag (MV_ERR_DEVICE_TIMEOUT) or a pending CUDA error. */
 mv_status mv_check_device_status(mv_ctx *ctx, void *stream);
 
+/* Self-test of the failure path: launches one thread that waits, with the
+ * bounded mbarrier wait every tensor-core kernel uses but a limit of limit_s
+ * (0 < limit_s <= 10), on a barrier nothing completes.  The kernel gives up,
+ * records the timeout and returns; the call synchronises and returns what
+ * mv_check_device_status reports, MV_ERR_DEVICE_TIMEOUT, leaving the context
+ * usable (no fault, no hang). */
+mv_status mv_selftest_wait_timeout(mv_ctx *ctx, double limit_s);
+
 /* Number of live (Up > 0) sources at each LST, as the last mv_simulate or
  * mv_simulate_pairs call computed them on the device (its instances, in
  * order): out [n] int64.  Synchronises. */

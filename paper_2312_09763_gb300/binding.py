@@ -30,7 +30,7 @@ EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv
            "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
            "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
            "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation", "mv_redundancy_plan",
-           "mv_set_redundancy", "mv_simulate_unique"]
+           "mv_set_redundancy", "mv_simulate_unique", "mv_selftest_wait_timeout"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_set_redundancy.restype = i32
     lib.mv_simulate_unique.argtypes = [vp, i32, vp, i32, vp, i32, vp, i32, vp]
     lib.mv_simulate_unique.restype = i32
+    lib.mv_selftest_wait_timeout.argtypes = [vp, dp]
+    lib.mv_selftest_wait_timeout.restype = i32
     for name in ("mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params", "mv_surrogate_set_params",
                  "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save", "mv_surrogate_load",
                  "mv_set_beam_surrogate"):
@@ -323,6 +325,12 @@ class Simulator:
         self._check(self._lib.mv_simulate_unique(self._h, lst.size, _p(lst), nu.size, _p(nu), PRECISION[precision],
                                                  ptr, on_dev, None if host else self._stream(stream)))
         return arr
+
+    def selftest_wait_timeout(self, limit_s: float = 0.2) -> str:
+        """Run the failure-path self-test (mv_selftest_wait_timeout); returns the
+        status name it reports (MV_ERR_DEVICE_TIMEOUT when the bounded wait
+        gave up as designed)."""
+        return _STATUS.get(self._lib.mv_selftest_wait_timeout(self._h, float(limit_s)), "?")
 
     def check_device_status(self, stream=None):
         self._check(self._lib.mv_check_device_status(self._h, None if stream is None else self._stream(stream)))

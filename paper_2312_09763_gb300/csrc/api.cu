@@ -1449,6 +1449,16 @@ mv_status mv_check_device_status(mv_ctx* c, void* stream) {
     return MV_OK;
 }
 
+mv_status mv_selftest_wait_timeout(mv_ctx* c, double limit_s) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (!(limit_s > 0) || limit_s > 10) return fail(MV_ERR_ARG, "limit_s must be in (0, 10]");
+    DeviceGuard g(c->device);
+    mv_status s;
+    if ((s = cuda_check(launch_wait_probe((int*)c->err.p, limit_s, c->stream), "wait probe"))) return s;
+    return mv_check_device_status(c, nullptr);
+}
+
 mv_status mv_last_live_counts(mv_ctx* c, int n, int64_t* out) {
     g_err.clear();
     if (!c || !out) return fail(MV_ERR_ARG, "NULL argument");

@@ -193,6 +193,9 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
                            int N, int flush_kblocks, int split, int bn, int n_ctas, int* d_sched,
                            float* d_partial, int* d_err, const ZJob* zj, int zprec, const HerkOut* out,
                            cudaStream_t st, long long* launches);
+// One bounded mbarrier wait that nothing completes, with a limit of limit_s
+// (<= 10 s): records kDevTimeout in d_err (self-test of the failure path).
+cudaError_t launch_wait_probe(int* d_err, double limit_s, cudaStream_t st);
 // Whether the HERK can carry the Z build (tile width 128; one feed and one
 // axis, or two and two; BF16x3 or FP16x3).
 bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed);

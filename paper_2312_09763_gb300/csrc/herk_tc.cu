@@ -617,7 +617,29 @@ cudaError_t launch_bn(const CUtensorMap& mh, const CUtensorMap& ml, const Inst* 
     return cudaGetLastError();
 }
 
+// A bounded mbarrier wait that nothing completes: one thread waits limit_ns
+// through the same wait as every tensor-core kernel, then records the device
+// timeout in err and returns (the failure path of those kernels, without a
+// fault).
+__global__ void k_wait_probe(int* __restrict__ err, unsigned long long limit_ns) {
+    __shared__ alignas(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) wait_bounded(smem_u32(&bar), 0u, &abort_flag, err, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_probe(int* d_err, double limit_s, cudaStream_t st) {
+    if (!d_err || !(limit_s > 0) || limit_s > 10) return cudaErrorInvalidValue;
+    k_wait_probe<<<1, 32, 0, st>>>(d_err, (unsigned long long)(limit_s * 1e9));
+    return cudaGetLastError();
+}
 
 bool herk_tc_available() { return get_encode() != nullptr; }
 

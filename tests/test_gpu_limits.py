@@ -2,7 +2,8 @@
 million sources on a small array (long source axis, 64-bit offsets), a
 256-channel batch (the largest batch, sixteen Z groups in one launch) and
 1000 antennas (2000 real rows, 136 tiles of the lower triangle).  FP16x3 and
-FP32, tolerance 1e-5."""
+FP32, tolerance 1e-5.  And the failure path: a bounded device-side wait that
+runs out reports MV_ERR_DEVICE_TIMEOUT without a fault or a hang."""
 import numpy as np
 import pytest
 
@@ -46,3 +47,18 @@ def test_thousand_antennas(prec):
     for it in range(2):
         vo = oracle.vis(P, w.lsts[it], w.freqs[0], pairs=(pa, pb))[:, 0, 0]
         assert rel_err(V[it, 0][pa, pb], vo) <= 1e-5, it
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    # a barrier nothing completes: the kernel's bounded wait gives up after
+    # the limit, the host reads the timeout, and the context keeps working
+    import time
+    w = synth.hera_like(n_ant=40, n_src=3000, n_chan=2, n_times=1, n_za=46, n_az=120)
+    sim = simulator(w)
+    t0 = time.perf_counter()
+    assert sim.selftest_wait_timeout(0.2) == "MV_ERR_DEVICE_TIMEOUT"
+    assert 0.19 < time.perf_counter() - t0 < 5.0
+    sim.check_device_status()  # the status word was cleared
+    V = sim.simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+    P = oracle_problem(w)
+    assert rel_err(V[0, 1], oracle.vis(P, w.lsts[0], w.freqs[1])) <= 1e-5
