@@ -497,9 +497,13 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if ((s = ensure(c, c->lazza, sizeof(float2) * (size_t)pitch * n_times))) return s;
     if ((s = ensure(c, c->nlive, sizeof(int) * (size_t)n_times))) return s;
     // the fused schedule unless the autotuner timed the separate one faster
-    // for calls of this shape
+    // for calls of this shape; for the redundant-group output only when the
+    // cover is the whole triangle: a cover of fewer tiles leaves the HERK too
+    // short to hide the next batch's Z build (350-antenna array, 9 of 21
+    // tiles: 250 ms per step fused against 210 ms separate)
     p.fuse = c->opt.fuse_zbuild && p.zprec != 0 && P.batches.size() > 1 &&
-             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed) && !(tuned_for(c, p) && !c->tuned.fuse) && !P.unique;
+             herk_tc_fusable(128, p.zprec, m.n_ax, m.n_feed) && !(tuned_for(c, p) && !c->tuned.fuse) &&
+             (!P.unique || c->red.kind == 0);
     p.nbuf = (P.batches.size() > 1 && (c->opt.overlap_batches || p.fuse)) ? 2 : 1;
     // antenna phase factors: per batch, groups x wavenumbers per group x antennas
     p.n_phase = 2;

@@ -55,6 +55,33 @@ def test_hera_like_groups_match_oracle_and_full_v(n_ant, tile_n, split):
         assert rel_err(expand(Vu, plan, w.n_ant, 1), Vf) <= 2 * tol
 
 
+@pytest.mark.parametrize("redundant,tile_n", [(False, 128), (False, 256), (True, 128)])
+def test_fused_schedule_matches_the_separate_one(redundant, tile_n):
+    # several batches.  A non-redundant array's cover is the whole triangle:
+    # there each HERK launch also builds the next batch's Z planes (fused
+    # schedule, no Z-build launch after the first batch); a smaller cover
+    # keeps the Z build in its own launches.  One HERK configuration, so the
+    # schedules sum in the same order.
+    w = synth.hera_like(n_ant=250 if redundant else 120, n_src=6000, n_chan=4, n_times=2, n_za=46, n_az=120)
+    if not redundant:
+        w.enu = synth.square_array(120, 300.0, np.random.default_rng(5))
+    plan = redundancy_plan(w.enu, None, 1e-3, 1, 128)
+    assert (plan["kind"] == 0) == (not redundant)
+    out, n_launch = {}, {}
+    for fuse in (True, False):
+        sim = simulator(w, max_batch=2, herk_tile_n=tile_n, herk_split=2, fuse_zbuild=fuse)
+        sim.set_redundancy(1e-3)
+        out[fuse] = sim.simulate_unique(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+        n_launch[fuse] = sim.last_launch_count()
+    # 4 batches: the fused schedule saves the Z-build launches of batches 1-3
+    assert n_launch[False] - n_launch[True] == (0 if redundant else 3)
+    assert np.array_equal(out[True], out[False])
+    P = oracle_problem(w)
+    for it, ic in ((0, 0), (1, 3)):
+        vo = oracle.vis(P, w.lsts[it], w.freqs[ic], pairs=(plan["rep_a"], plan["rep_b"]))
+        assert rel_err(out[True][it, ic], vo) <= 1e-5, (it, ic)
+
+
 def test_two_feeds_and_a_polarised_sky():
     w = synth.polarised_diffuse(n_ant=100, nside=16, n_chan=2, n_times=2, n_za=31, n_az=72, lmax=40,
                                 full_stokes=True)
