@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "matvis.h"
@@ -231,10 +232,41 @@ struct DeviceGuard {
     }
 };
 
+// fn(begin, end, part) over [0, n) in up to 16 contiguous parts of at least
+// 2^13 items on host threads; part numbers the parts from 0.
+template <typename Fn>
+void parallel_for(int64_t n, Fn fn) {
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n >> 13));
+    if (parts <= 1) {
+        fn((int64_t)0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(parts - 1);
+    int k = 1;
+    try {
+        for (; k < parts; ++k) th.emplace_back(fn, n * k / parts, n * (k + 1) / parts, k);
+    } catch (...) {  // no thread to be had: the rest on this one
+        for (; k < parts; ++k) fn(n * k / parts, n * (k + 1) / parts, k);
+    }
+    fn((int64_t)0, n / parts, 0);
+    for (auto& t : th) t.join();
+}
+
+// Smallest index i < n with !ok(i), or n.
+template <typename Ok>
+int64_t first_bad(int64_t n, Ok ok) {
+    std::vector<int64_t> bad(16, n);
+    parallel_for(n, [&](int64_t b, int64_t e, int part) {
+        for (int64_t i = b; i < e; ++i)
+            if (!ok(i)) { bad[part] = i; return; }
+    });
+    return *std::min_element(bad.begin(), bad.end());
+}
+
 bool finite_all(const double* p, int64_t n) {
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(p[i])) return false;
-    return true;
+    return first_bad(n, [p](int64_t i) { return std::isfinite(p[i]); }) == n;
 }
 
 long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
@@ -1126,22 +1158,24 @@ mv_status mv_init_sky(mv_ctx* c, int64_t n_src, const double* ra, const double* 
     if (!ra || !dec || !flux_ref) return fail(MV_ERR_ARG, "ra, dec and flux_ref are required");
     if (!(std::isfinite(nu_ref) && nu_ref > 0)) return fail(MV_ERR_ARG, "nu_ref must be positive and finite");
     if (!finite_all(ra, n_src) || !finite_all(dec, n_src)) return fail(MV_ERR_ARG, "ra/dec not finite");
-    for (int64_t i = 0; i < n_src; ++i)
-        if (!(std::isfinite(flux_ref[i]) && flux_ref[i] >= 0))
-            return fail(MV_ERR_ARG, "flux_ref[%lld] must be finite and >= 0", (long long)i);
+    const int64_t bad_flux =
+        first_bad(n_src, [flux_ref](int64_t i) { return std::isfinite(flux_ref[i]) && flux_ref[i] >= 0; });
+    if (bad_flux < n_src) return fail(MV_ERR_ARG, "flux_ref[%lld] must be finite and >= 0", (long long)bad_flux);
     if (spec_idx && !finite_all(spec_idx, n_src)) return fail(MV_ERR_ARG, "spec_idx not finite");
     DeviceGuard g(c->device);
     // eq. "xeq": X_eq = (cos ra cos dec, sin ra cos dec, sin dec), SoA
     std::vector<double> xeq(3 * (size_t)n_src);
     std::vector<float> sf(n_src), ha(n_src);
-    for (int64_t s = 0; s < n_src; ++s) {
-        const double cd = std::cos(dec[s]);
-        xeq[s] = std::cos(ra[s]) * cd;
-        xeq[n_src + s] = std::sin(ra[s]) * cd;
-        xeq[2 * n_src + s] = std::sin(dec[s]);
-        sf[s] = (float)std::sqrt(flux_ref[s]);
-        ha[s] = spec_idx ? (float)(0.5 * spec_idx[s]) : 0.f;
-    }
+    parallel_for(n_src, [&](int64_t b, int64_t e, int) {
+        for (int64_t s = b; s < e; ++s) {
+            const double cd = std::cos(dec[s]);
+            xeq[s] = std::cos(ra[s]) * cd;
+            xeq[n_src + s] = std::sin(ra[s]) * cd;
+            xeq[2 * n_src + s] = std::sin(dec[s]);
+            sf[s] = (float)std::sqrt(flux_ref[s]);
+            ha[s] = spec_idx ? (float)(0.5 * spec_idx[s]) : 0.f;
+        }
+    });
     mv_status s;
     if ((s = upload(c, c->xeq, xeq.data(), xeq.size() * sizeof(double), c->stream))) return s;
     if ((s = upload(c, c->sqrt_flux, sf.data(), sf.size() * sizeof(float), c->stream))) return s;
@@ -1219,8 +1253,8 @@ mv_status mv_set_beam_grid(mv_ctx* c, int n_beam, int n_feed, int n_ax, int n_nu
     if (std::fabs(n_az * daz - 2 * kPi) > 1e-9 * 2 * kPi) return fail(MV_ERR_ARG, "n_az * daz must equal 2 pi");
     if (!values) return fail(MV_ERR_ARG, "values is NULL");
     const size_t n = (size_t)n_beam * n_feed * n_ax * n_nu * n_za * n_az;
-    for (size_t i = 0; i < 2 * n; ++i)
-        if (!std::isfinite(values[i])) return fail(MV_ERR_ARG, "beam value %zu not finite", i / 2);
+    const int64_t bad = first_bad((int64_t)(2 * n), [values](int64_t i) { return std::isfinite(values[i]); });
+    if (bad < (int64_t)(2 * n)) return fail(MV_ERR_ARG, "beam value %zu not finite", (size_t)bad / 2);
     DeviceGuard g(c->device);
     mv_status s;
     if ((s = upload(c, c->grid, values, n * sizeof(float2), c->stream))) return s;
