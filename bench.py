@@ -45,6 +45,10 @@ FUSED_DRAM_BYTES_PER_INSTANCE = (2.5454e9 + 2.2658e9) / 16
 # 50,013 live sources): 2.9 MB read + 501.5 MB written, summarised in
 # profiles/k_mlp_wa_learned_350beams_1e5src.txt.
 MLP_DRAM_BYTES_PER_LAUNCH = 2.920e6 + 501.452e6
+# k_herk_tc<128> over the redundant-group cover of the same workload: 2.3151 GB
+# read + 43.1 MB written for 16 instances, summarised in
+# profiles/k_herk_tc_redundant_cover_350ant_1e5src_16ch.txt.
+UNIQUE_DRAM_BYTES_PER_INSTANCE = (2.3151e9 + 0.0431e9) / 16
 METRIC = "vis/s (bl·chan·time) at 350 ant×1e5 src; split-prec TC vs FP32 @1e-5 rel err"
 UNIT = "vis/s"
 
@@ -420,9 +424,23 @@ def main():
         else:
             area = float(sum(4 * nf * nf * (r1 - r0) * (c1 - c0) for r0, r1, c0, c1 in plan["blocks"]))
         flops_u = float(np.sum(3 * 2.0 * area * K))
-        roof.update({"achieved": flops_u * args.steps / (ms_h / 1e3) / 1e12,
-                     "kernel": "k_herk_tc over the redundant-group cover", "traffic": None})
-        roof["frac"] = roof["achieved"] / sustained
+        tflops = flops_u * args.steps / (ms_h / 1e3) / 1e12
+        # the cover's few tiles per instance read each U plane from HBM about
+        # once: that read (hi + lo halves) is the bound that binds here
+        kpad = np.ceil(K / 256.0) * 256
+        u_bytes = float(np.sum(rows * kpad * 4.0))
+        n_launch = max(n_h / args.steps, 1)
+        gbs = u_bytes * args.steps / (ms_h / 1e3) / 1e9
+        traffic = None
+        if args.workload == "hera" and not args.small and args.precision == "fp16x3":
+            traffic = UNIQUE_DRAM_BYTES_PER_INSTANCE * n_instances(w, pairs) / n_launch
+        roof.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "traffic": traffic, "kernel": "k_herk_tc over the redundant-group cover",
+                     "peak_source": f"{src} HBM copy rate",
+                     "algorithmic_bytes_per_launch": u_bytes / n_launch,
+                     "tensor_achieved_tflops": tflops, "tensor_frac": tflops / sustained})
+        for k in ("hbm_bytes_per_step", "hbm_achieved_gbs", "hbm_frac", "hbm_peak_gbs"):
+            roof.pop(k, None)
         unique_info = {"n_unique": n_unique, "cover_kind": plan["kind"], "cover_blocks": plan["blocks"].tolist(),
                        "cover_tiles": plan["tiles"], "triangle_tiles": plan["tiles_full"],
                        "unique_vis_per_s": world * n_unique * nf * nf * n_instances(w, pairs) * args.steps
