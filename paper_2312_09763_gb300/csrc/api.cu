@@ -450,6 +450,7 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     for (int b : c->h_bidx)
         if (b >= m.n_beam) return fail(MV_ERR_ARG, "antenna beam index %d >= n_beam %d", b, m.n_beam);
     Prepared& p = out;
+    p.plan = &P;
     p.n_times = (int)P.lst.size();
     p.n_chan = (int)P.nu.size();
     p.n_inst = (int)P.inst.size();
