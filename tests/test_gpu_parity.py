@@ -166,3 +166,23 @@ def test_errors_are_reported():
     with pytest.raises(MatvisError, match="MV_ERR_ARG"):
         sim.simulate([0.0], [98.5e6], "fp32")   # needs the 97 MHz node
     sim.check_device_status()
+
+
+def test_input_checks_name_the_first_bad_entry():
+    # the set-up calls check large inputs on several host threads: the error
+    # still names the first bad entry, wherever the parts split the array
+    from paper_2312_09763_gb300 import MatvisError
+    w = synth.hera_like(n_ant=10, n_src=100_000, n_chan=1, n_times=1, n_za=31, n_az=60)
+    sim = simulator(w)
+    flux = w.flux_ref.astype(np.float64).copy()
+    flux[[70_001, 99_998]] = -1.0
+    with pytest.raises(MatvisError, match=r"flux_ref\[70001\]"):
+        sim.init_sky(w.ra, w.dec, flux, w.spec_idx, w.nu_ref)
+    grid = np.array(w.beam[1], dtype=np.complex64, copy=True)
+    flat = grid.reshape(-1)
+    flat[flat.size - 5] = np.nan
+    flat[flat.size // 3 + 7] = complex(0.0, np.inf)
+    with pytest.raises(MatvisError, match=rf"beam value {flat.size // 3 + 7} not finite"):
+        sim.set_beam(("grid", grid) + tuple(w.beam[2:]))
+    # the context keeps its previous sky and beam
+    sim.simulate(w.lsts, w.freqs, "fp16x3")
