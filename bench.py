@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 # summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
 HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0178e9) / 16
 # The same for the HERK launch that also builds the next batch's U planes
-# (k_herk_tc<128, 2, 1, 1>): 2.5454 GB read + 2.2658 GB written for 16 + 16
+# (k_herk_tc<128, 2, 1, 1>): 2.5140 GB read + 2.2649 GB written for 16 + 16
 # instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
-FUSED_DRAM_BYTES_PER_INSTANCE = (2.5454e9 + 2.2658e9) / 16
+FUSED_DRAM_BYTES_PER_INSTANCE = (2.5140e9 + 2.2649e9) / 16
 # k_mlp_wa on the learned-beam sample (one launch = one instance of 350 beams x
 # 50,013 live sources): 2.9 MB read + 501.5 MB written, summarised in
 # profiles/k_mlp_wa_learned_350beams_1e5src.txt.
