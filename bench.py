@@ -6,7 +6,7 @@ horizon cut, beam interpolation, FP64-phase Z build and V = Z Z^H), inputs
 already resident on the device.  vis = N_ant (N_ant + 1) / 2 baselines
 (autocorrelations included) x channels x times.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp16x3|fp32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16x3|fp32]
                     [--impl ours|reference] [--workload hera|diffuse|uneven]
 
 --workload diffuse times the polarised HEALPix sky (350 antennas, 196,608
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp16x3", choices=["bf16x3", "fp16x3", "fp32"])
+    ap.add_argument("--precision", default="fp16x3", choices=["fp16x3", "fp32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--no-fuse", action="store_true", help="Z build as its own launch (mv_options.fuse_zbuild = 0)")
     ap.add_argument("--herk-config", default=None, metavar="BN,SPLIT,FLUSH",
                     help="fix the tensor-core HERK tile width, split-K and flush interval (skips autotune)")
+    ap.add_argument("--fp32-steps", type=int, default=2,
+                    help="timed steps of the FP32 CUDA-core arm on the same workload (after one warm-up step; "
+                         "0 skips it)")
     return ap.parse_args()
 
 
@@ -208,25 +211,37 @@ def peaks():
     return 1900.0, 1700.0, 6800.0, "fallback"
 
 
-def cpu_baseline(w, budget_pairs: int = None):
+def cpu_baseline(w, budget_pairs: int = None, keep: dict = None):
     """The FP64 oracle as it stands, on the host cores: all baselines a >= b of
-    one instance (LST 0, first channel) of the same workload."""
+    one instance (LST 0, first channel) of the same workload.  keep (a dict):
+    receives the oracle's V of those baselines and their (a, b) indices."""
     import oracle
     oracle.build()
     P = oracle.Problem(ra=w.ra, dec=w.dec, flux_ref=w.flux_ref, enu=w.enu, lat=w.lat,
                        beam=(w.beam[0], np.asarray(w.beam[1]).astype(np.complex128)) + tuple(w.beam[2:]),
-                       spec_idx=w.spec_idx, nu_ref=w.nu_ref)
+                       spec_idx=w.spec_idx, nu_ref=w.nu_ref, beam_idx=w.beam_idx, stokes_quv=w.stokes_quv)
     a, b = np.tril_indices(w.n_ant)
     if budget_pairs is not None:
         a, b = a[:budget_pairs], b[:budget_pairs]
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    oracle.vis(P, w.lsts[0], w.freqs[0], pairs=(a, b), threads=cores)
+    vo = oracle.vis(P, w.lsts[0], w.freqs[0], pairs=(a, b), threads=cores)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(V=vo, a=a, b=b)
     return {"value": a.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{a.size} baselines (a >= b) of one instance (LST {w.lsts[0]:.4f} rad, "
                       f"{w.freqs[0] / 1e6:.4f} MHz) of the {w.n_ant}-antenna x {w.n_src}-source workload, "
                       f"FP64 direct sum, {dt:.1f} s"}
+
+
+def max_rel_err(v0, keep: dict, nf: int) -> float:
+    """max |V - V_oracle| / max |V_oracle| over the oracle's baselines of the
+    first instance; v0 is the GPU's V of that instance, [N nf][N nf]."""
+    a, b, vo = keep["a"], keep["b"], keep["V"]
+    n = v0.shape[0] // nf
+    v = v0.reshape(n, nf, n, nf)[a, :, b, :]
+    return float(np.abs(v - vo).max() / np.abs(vo).max())
 
 
 def run_reference(args, rank, world):
@@ -413,6 +428,25 @@ def main():
             roof["hbm_achieved_gbs"] = 2 * z_bytes * args.steps / (ms_h / 1e3) / 1e9
             roof["hbm_frac"] = roof["hbm_achieved_gbs"] / hbm
             roof["hbm_peak_gbs"] = hbm
+    # the first instance's V, kept for its error against the oracle
+    v_first = V[(0, 0) if not pairs else (0,)].cpu().numpy() if n_unique is None and learned is None else None
+    fp32_arm = None
+    if args.fp32_steps > 0 and args.precision != "fp32" and n_unique is None and learned is None:
+        # the plain FP32 CUDA-core path on the same workload and buffers: the
+        # split-precision tensor-core path's speed-up at the same 1e-5 target
+        run(w.lsts, w.freqs, "fp32", out=V)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.fp32_steps):
+            run(w.lsts, w.freqs, "fp32", out=V)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = d.max(f0.elapsed_time(f1))
+        v32 = world * vis_step * args.fp32_steps / (ms32 / 1e3)
+        fp32_arm = {"value": v32, "unit": UNIT, "ms_per_step": ms32 / args.fp32_steps, "steps": args.fp32_steps,
+                    "warmup": 1, "speedup_vs_fp32": value / v32,
+                    "v_first": V[(0, 0) if not pairs else (0,)].cpu().numpy()}
     unique_info = None
     if n_unique is not None and roof is not None:
         # the redundant-group output: the HERK computes the cover's blocks only;
@@ -516,8 +550,21 @@ def main():
         line["e2e"] = {"value": vis_step * e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "ms_per_step": [round(1e3 * x, 2) for x in times],
                        "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+    if fp32_arm is not None:
+        line["fp32_value"] = fp32_arm["value"]
+        line["speedup_vs_fp32"] = fp32_arm["speedup_vs_fp32"]
+        line["fp32_arm"] = {k: v for k, v in fp32_arm.items() if k != "v_first"}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        keep = {}
+        line["cpu_baseline"] = cpu_baseline(w, keep=keep)
+        if v_first is not None:
+            # accuracy of this run against the FP64 oracle on every baseline of
+            # the first instance (LST 0, first channel)
+            line["max_rel_err"] = max_rel_err(v_first, keep, nf)
+            line["max_rel_err_sample"] = (f"{keep['a'].size} baselines (a >= b) x {nf * nf} feed products of the "
+                                          f"first instance, against the FP64 oracle")
+            if fp32_arm is not None:
+                line["fp32_arm"]["max_rel_err"] = max_rel_err(fp32_arm["v_first"], keep, nf)
     if rank == 0:
         print(json.dumps(line), flush=True)
     d.close()

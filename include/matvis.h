@@ -14,7 +14,7 @@
  *         exactly modulo one turn;
  *   (iv)  build Z[(a,p),(s,k)] = sqrt(I_s) A^{pk}_{beta(a)}(s) exp(-2 pi i phase)
  *         (eq. "littlez"; Sec. 2.2);
- *   (v)   expand V = Z Z^dagger (eq. "zz") on the tensor cores (BF16 x3 split
+ *   (v)   expand V = Z Z^dagger (eq. "zz") on the tensor cores (FP16 x3 split
  *         precision, FP32 accumulation) or on the CUDA cores (FP32).
  *
  * Conventions (all calls):
@@ -54,11 +54,17 @@ typedef enum {
     MV_ERR_UNSUPPORTED = 6     /* feature not available on this device / build */
 } mv_status;
 
+/* Arithmetic of steps (iv)-(v).  Both modes meet max |V - V_oracle| /
+ * max |V_oracle| <= 1e-5 against the FP64 definition.  Value 1 is not used:
+ * a split into two BF16 pieces keeps only 16 significant bits of each entry of
+ * Z (representation error up to 2^-16 = 1.5e-5 relative per entry), which
+ * cannot meet that bound, so no BF16 mode is offered (MV_ERR_ARG). */
 typedef enum {
     MV_PREC_FP32 = 0,   /* Z and V = Z Z^H in FP32 on CUDA cores */
-    MV_PREC_BF16X3 = 1, /* Z split as hi + lo BF16; hi hi^T + hi lo^T + lo hi^T on tcgen05, FP32 accumulate */
-    MV_PREC_FP16X3 = 2  /* as BF16X3 with FP16 halves (11-bit each) after an exact per-instance
-                           power-of-two scaling of Z into FP16 range */
+    MV_PREC_FP16X3 = 2  /* Z scaled by an exact power of two (one per group of channels of one
+                           time) into FP16 range and split as hi + lo FP16 (11 significant bits
+                           each, 22 together); hi hi^T + hi lo^T + lo hi^T on tcgen05 with FP32
+                           accumulation: the matrix product of step (v) in split precision */
 } mv_precision;
 
 typedef enum {
@@ -129,6 +135,28 @@ const char *mv_last_error(void);
  * n_src >= 1.  Host pointers; copied. */
 mv_status mv_init_sky(mv_ctx *ctx, int64_t n_src, const double *ra, const double *dec,
                       const double *flux_ref, const double *spec_idx, double nu_ref);
+
+/* Perturbed source coordinates of Algorithm 1 (Sec. 2.3, the "fast"
+ * coordinate scheme), steps (ii) and (iv)-(vi); host only (no context, no
+ * device).  The rigid rotation of eq. "rotation" lacks the time-dependent
+ * astrometric corrections; this call moves each source to fictitious
+ * equatorial coordinates (RA', Dec') for which the rigid rotation at the
+ * reference LST gives exactly the caller's apparent direction:
+ *   X_hrz = (cos alt sin az, cos alt cos az, sin alt)   (East, North, Up),
+ *   X_eq' = R(lst_ref)^T X_hrz                          (R^-1 = R^T),
+ *   RA' = atan2(y, x) in [0, 2 pi), Dec' = atan2(z, sqrt(x^2 + y^2)).
+ * Steps (i) and (iii) -- the apparent LST at the reference time and the
+ * apparent (alt, az) of every source then -- are the caller's (the paper uses
+ * astropy).  Pass (RA', Dec') to mv_init_sky; for long runs cut the times into
+ * chunks, each with its own reference time, perturbed catalogue and
+ * mv_init_sky (the correction degrades away from t_ref).
+ * alt_rad, az_rad: [n_src] radians, az from North through East, |alt| <= pi/2;
+ * lst_ref_rad: apparent LST at the reference time; latitude_rad: |lat| <= pi/2.
+ * ra_out, dec_out: [n_src] radians.  Host pointers (caller-owned).
+ * MV_ERR_ARG for n_src < 1, NULL pointers or non-finite / out-of-range
+ * angles (the message names the first bad source). */
+mv_status mv_perturb_sky(int64_t n_src, const double *alt_rad, const double *az_rad, double lst_ref_rad,
+                         double latitude_rad, double *ra_out, double *dec_out);
 
 /* Fully polarised sky (Sec. 2.1 coherency, Sec. 2.2 eq. "fullz"): Stokes Q,
  * U, V of every source of the last mv_init_sky, in Jy at nu_ref, host
@@ -280,20 +308,22 @@ mv_status mv_simulate_unique(mv_ctx *ctx, int n_t, const double *lst, int n_nu, 
 /* Rotation and horizon cut of one LST without any device allocation.
  *
  * The paper has no counterpart: this exists for callers that cannot allocate
- * device memory when they run this step -- code recording a CUDA graph by
- * stream capture (cudaMalloc is not a stream operation), hosts whose device
- * memory all belongs to a framework's own pool, and latency-critical loops
- * that cannot take cudaMalloc's implicit device synchronisation.  It runs the
- * same kernels as step (i) of mv_simulate, but their scratch (per-block live
- * counts and offsets, and the 3 x 3 rotation) lives in a static device array
- * of 64 KB that every GPU loading this library holds until the process exits.
+ * device memory when they run this step -- hosts whose device memory all
+ * belongs to a framework's own pool (a cudaMalloc beside it can fail or
+ * fragment it), and latency-critical loops that cannot take cudaMalloc's
+ * implicit device synchronisation.  It runs the same kernels as step (i) of
+ * mv_simulate, but their scratch (per-block live counts and offsets, and the
+ * 3 x 3 rotation) lives in a static device array of 64 KB that every GPU
+ * loading this library holds until the process exits.  The rotation reaches
+ * the device as a kernel argument, so no host buffer outlives the call.
  *
- * Limits and sharing: 1 <= n_src <= 2,097,152, else MV_ERR_ARG.  Every call
+ * Limits and sharing: 1 <= n_src <= 2,097,152 and |latitude_rad| <= pi/2,
+ * else MV_ERR_ARG.  Every call
  * on a device shares that array; calls that overlap on the GPU (for example
  * on two unsynchronised streams) race and give wrong results.  Nothing in it
  * needs clearing: a call writes every entry it reads.  The first call on each
  * device resolves the array's device address with cudaGetSymbolAddress on the
- * current device, so make that first call before any stream capture.
+ * current device (once per device, under a lock).
  *
  * Arguments (device pointers unless stated): xeq_dev [3][n_src] FP64 SoA
  * (x, y, z of eq. "xeq"); lst_rad, latitude_rad host values; outputs, for the

@@ -20,6 +20,10 @@ Functions and the passages they follow:
   delay of eq. "matvisdelay" and C = I * identity (Sec. 2.2)
 * :func:`vis_outer`      -- Z of eq. "littlez" and V = Z Z^dagger of eq. "zz"
   (Algorithm 2 steps iii-v), a small-problem cross-check of :func:`vis`
+* :func:`perturb_sky`    -- Algorithm 1 (Sec. 2.3) steps (ii), (iv)-(vi):
+  perturbed RA/Dec from apparent (alt, az) at a reference LST
+* :func:`vis_with_beam_fn` -- :func:`vis` with the beams of a caller's model
+  tabulated at the live sources (the learned beam's checker)
 
 Parity status: pinned by closed forms and invariants only (the paper prints no
 numeric visibilities); see tests/test_oracle_pins.py.
@@ -98,6 +102,8 @@ def _load() -> ctypes.CDLL:
         lib.orc_vis_outer.restype = ctypes.c_int
         lib.orc_coherency_sqrt.argtypes = [ctypes.c_double] * 4 + [dp]
         lib.orc_coherency_sqrt.restype = None
+        lib.orc_perturb_sky.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_perturb_sky.restype = None
         _lib = lib
     return _lib
 
@@ -295,3 +301,12 @@ def vis_with_beam_fn(prob: Problem, lst: float, nu: float, beam_fn, pairs=None, 
                 beam=("table", table), spec_idx=prob.spec_idx, nu_ref=prob.nu_ref, beam_idx=prob.beam_idx,
                 stokes_quv=prob.stokes_quv)
     return vis(q, lst, nu, pairs=pairs, threads=threads)
+
+
+def perturb_sky(alt, az, lst_ref: float, lat: float):
+    """Algorithm 1 steps (ii), (iv)-(vi): (RA', Dec') such that the rigid
+    rotation at lst_ref puts each source at the given apparent (alt, az)."""
+    alt, az = _f64(alt).ravel(), _f64(az).ravel()
+    ra, dec = np.empty(alt.size), np.empty(alt.size)
+    _load().orc_perturb_sky(alt.size, _ptr(alt), _ptr(az), float(lst_ref), float(lat), _ptr(ra), _ptr(dec))
+    return ra, dec

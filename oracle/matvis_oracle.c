@@ -118,6 +118,38 @@ void orc_to_topo(const double *R, int64_t n, const double *xyz, double *enu)
     }
 }
 
+/* Algorithm 1 (Sec. 2.3), steps (ii) and (iv)-(vi): perturbed equatorial
+ * coordinates from the apparent altitude and azimuth of each source at a
+ * reference LST (steps (i) and (iii) belong to the caller).
+ *   (ii)  R' = inverse of eq. "rotation" at (lst_ref, lat); R is orthonormal,
+ *         so R' is its transpose, read here by swapping the indices of R;
+ *   (iv)  X_hrz = (cos alt sin az, cos alt cos az, sin alt) in East-North-Up;
+ *   (v)   X_eq' = R' X_hrz;
+ *   (vi)  the inverse of eq. "xeq": Dec' from the z component, RA' from x, y.
+ * Writes ra[n], dec[n] in radians, RA' in [0, 2 pi). */
+void orc_perturb_sky(int64_t n, const double *alt, const double *az, double lst_ref, double lat,
+                     double *ra, double *dec)
+{
+    double R[9];
+    orc_rotation(lst_ref, lat, R);
+    for (int64_t s = 0; s < n; ++s) {
+        double h[3], x[3];
+        h[0] = cos(alt[s]) * sin(az[s]);
+        h[1] = cos(alt[s]) * cos(az[s]);
+        h[2] = sin(alt[s]);
+        for (int i = 0; i < 3; ++i) {
+            /* (R^T h)_i = sum_j R_ji h_j */
+            x[i] = 0.0;
+            for (int j = 0; j < 3; ++j) x[i] += R[3 * j + i] * h[j];
+        }
+        double r = sqrt(x[0] * x[0] + x[1] * x[1]);
+        double a = atan2(x[1], x[0]);
+        if (a < 0.0) a += 2.0 * ORC_PI;
+        ra[s] = a;
+        dec[s] = atan2(x[2], r);
+    }
+}
+
 /* Azimuth (N through E, [0, 2 pi)) and zenith angle of an ENU unit vector. */
 void orc_azza(int64_t n, const double *enu, double *az, double *za)
 {

@@ -6,6 +6,6 @@ C-ABI of ``include/matvis.h``; :mod:`.binding` marshals arguments into it
 There is no CPU fallback: importing :class:`Simulator` without the built
 library raises.
 """
-from .binding import Simulator, MatvisError, load_library, redundancy_plan  # noqa: F401
+from .binding import Simulator, MatvisError, load_library, perturb_sky, redundancy_plan  # noqa: F401
 
-__all__ = ["Simulator", "MatvisError", "load_library", "redundancy_plan"]
+__all__ = ["Simulator", "MatvisError", "load_library", "perturb_sky", "redundancy_plan"]

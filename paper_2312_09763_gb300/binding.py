@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmatvis_gb300.so")
 MV_OK = 0
 _STATUS = {0: "MV_OK", 1: "MV_ERR_ARG", 2: "MV_ERR_OOM", 3: "MV_ERR_CUDA", 4: "MV_ERR_STATE",
            5: "MV_ERR_DEVICE_TIMEOUT", 6: "MV_ERR_UNSUPPORTED"}
-PRECISION = {"fp32": 0, "bf16x3": 1, "fp16x3": 2}
+PRECISION = {"fp32": 0, "fp16x3": 2}
 _CUDA_STREAM_LEGACY = 0x1
 INTERP = {"cubic": 0, "bilinear": 1}
 
@@ -30,7 +30,7 @@ EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv
            "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
            "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
            "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation", "mv_redundancy_plan",
-           "mv_set_redundancy", "mv_simulate_unique", "mv_selftest_wait_timeout"]
+           "mv_set_redundancy", "mv_simulate_unique", "mv_selftest_wait_timeout", "mv_perturb_sky"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -115,6 +115,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_set_beam_surrogate.argtypes = [vp, i32]
     lib.mv_redundancy_plan.argtypes = [i32, vp, vp, dp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mv_redundancy_plan.restype = i32
+    lib.mv_perturb_sky.argtypes = [i64, vp, vp, dp, dp, vp, vp]
+    lib.mv_perturb_sky.restype = i32
     lib.mv_set_redundancy.argtypes = [vp, dp, vp]
     lib.mv_set_redundancy.restype = i32
     lib.mv_simulate_unique.argtypes = [vp, i32, vp, i32, vp, i32, vp, i32, vp]
@@ -163,6 +165,20 @@ def redundancy_plan(enu, beam_idx=None, tol_m: float = 1e-3, n_feed: int = 1, ti
     return {"n_unique": k, "rep_a": ra[:k].copy(), "rep_b": rb[:k].copy(), "group_of": go, "conj_of": co,
             "perm": perm, "kind": kind.value, "blocks": blocks[:4 * nb.value].reshape(-1, 4).copy(),
             "tiles": int(tiles[0]), "tiles_full": int(tiles[1])}
+
+
+def perturb_sky(alt, az, lst_ref: float, latitude: float):
+    """Perturbed (RA', Dec') of Algorithm 1 from apparent (alt, az) at a
+    reference LST (mv_perturb_sky; host only, no GPU needed)."""
+    lib = load_library()
+    alt, az = _f64(alt).ravel(), _f64(az).ravel()
+    if alt.size != az.size:
+        raise ValueError("alt and az differ in size")
+    ra, dec = np.empty(alt.size), np.empty(alt.size)
+    st = lib.mv_perturb_sky(alt.size, _p(alt), _p(az), float(lst_ref), float(latitude), _p(ra), _p(dec))
+    if st != 0:
+        raise MatvisError(st, lib.mv_last_error().decode())
+    return ra, dec
 
 
 class Simulator:
@@ -288,7 +304,7 @@ class Simulator:
         # (cudaStreamLegacy) since NULL means "the context's own stream" here
         return ctypes.c_void_p(stream.cuda_stream or _CUDA_STREAM_LEGACY)
 
-    def simulate(self, lsts: Sequence[float], freqs: Sequence[float], precision: str = "bf16x3", out=None,
+    def simulate(self, lsts: Sequence[float], freqs: Sequence[float], precision: str = "fp16x3", out=None,
                  host: bool = False, stream=None):
         """V[t, f] for every LST and frequency: complex64 [n_t, n_nu, N, N]."""
         lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()
@@ -298,7 +314,7 @@ class Simulator:
                                           on_dev, None if host else self._stream(stream)))
         return arr
 
-    def simulate_pairs(self, lsts, freqs, precision: str = "bf16x3", out=None, host: bool = False, stream=None):
+    def simulate_pairs(self, lsts, freqs, precision: str = "fp16x3", out=None, host: bool = False, stream=None):
         """V for explicit (lst, nu) pairs: complex64 [n_pairs, N, N]."""
         lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()
         if lst.size != nu.size:
@@ -343,7 +359,7 @@ class Simulator:
     def last_launch_count(self) -> int:
         return int(self._lib.mv_last_launch_count(self._h))
 
-    def autotune(self, lsts, freqs, precision: str = "bf16x3", pairs: bool = False) -> dict:
+    def autotune(self, lsts, freqs, precision: str = "fp16x3", pairs: bool = False) -> dict:
         """Time the tensor-core HERK configurations on the first batch of this
         call shape and keep the fastest (see mv_autotune)."""
         lst, nu = _f64(lsts).ravel(), _f64(freqs).ravel()

@@ -442,7 +442,10 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     if (!c->have_sky || !c->have_ant || !c->have_beam)
         return fail(MV_ERR_STATE, "simulate needs init_sky, set_antennas and a beam first");
     if (m.pol_m && m.n_ax != 2) return fail(MV_ERR_STATE, "a polarised sky needs a two-axis beam");
-    if (prec != MV_PREC_FP32 && prec != MV_PREC_BF16X3 && prec != MV_PREC_FP16X3)
+    if (prec == 1)
+        return fail(MV_ERR_ARG, "precision 1 (BF16 hi + lo) is not offered: 16 significant bits per entry of Z "
+                                "cannot meet the 1e-5 bound; use MV_PREC_FP16X3");
+    if (prec != MV_PREC_FP32 && prec != MV_PREC_FP16X3)
         return fail(MV_ERR_ARG, "unknown precision %d", (int)prec);
     if (!V) return fail(MV_ERR_ARG, "V is NULL");
     if (prec != MV_PREC_FP32 && !herk_tc_available())
@@ -454,7 +457,7 @@ mv_status prepare(mv_ctx* c, Plan& P, mv_precision prec, void* V, int V_on_devic
     p.n_times = (int)P.lst.size();
     p.n_chan = (int)P.nu.size();
     p.n_inst = (int)P.inst.size();
-    p.zprec = prec == MV_PREC_FP32 ? 0 : (prec == MV_PREC_BF16X3 ? 1 : 2);
+    p.zprec = prec == MV_PREC_FP32 ? 0 : 2;
     if (p.n_inst == 0) return MV_OK;
 
     // channel table

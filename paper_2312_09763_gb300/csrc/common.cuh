@@ -142,8 +142,8 @@ struct alignas(16) AntPhase {
     unsigned negk_lo, negk_hi, pad;
 };
 
-// Z build of a batch of groups: writes FP32 planes (prec 0) or BF16 hi/lo
-// planes (prec 1) of U into workspace slots.
+// Z build of a batch of groups: writes FP32 planes (prec 0) or scaled FP16
+// hi/lo planes (prec 2) of U into workspace slots.
 // Everything the Z build of one batch needs, for Z-build warps running
 // inside another kernel (the HERK of the previous batch).
 struct ZJob {
@@ -197,7 +197,7 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
 // (<= 10 s): records kDevTimeout in d_err (self-test of the failure path).
 cudaError_t launch_wait_probe(int* d_err, double limit_s, cudaStream_t st);
 // Whether the HERK can carry the Z build (tile width 128; one feed and one
-// axis, or two and two; BF16x3 or FP16x3).
+// axis, or two and two; FP16x3).
 bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed);
 // Set kernel attributes of the tensor-core HERK (once per process, outside
 // any stream capture).

@@ -2,8 +2,8 @@
 // V = Z Z^dagger (eq. "zz"), on the sm_103a tensor cores (tcgen05).
 //
 // Z is held as the real matrix U (rows 2(a n_feed + p) = Re Z, +1 = Im Z),
-// split into two planes U = U_hi + U_lo (BF16, or FP16 after an exact
-// power-of-two scale).  A persistent kernel (one CTA per SM) takes units of
+// scaled by an exact power of two into FP16 range and split into two FP16
+// planes U = U_hi + U_lo.  A persistent kernel (one CTA per SM) takes units of
 // work (instance, 128 x BN tile of the lower triangle of G = U U^T, k-range)
 // from an atomic counter and accumulates
 //     G_tile += U_hi,i U_hi,j^T + U_hi,i U_lo,j^T + U_lo,i U_hi,j^T
@@ -644,32 +644,24 @@ cudaError_t launch_wait_probe(int* d_err, double limit_s, cudaStream_t st) {
 bool herk_tc_available() { return get_encode() != nullptr; }
 
 cudaError_t herk_tc_init() {
-    const int f1 = Cfg<128, zwarps(1, 1, 1)>::SMEM, f2 = Cfg<128, zwarps(1, 2, 2)>::SMEM;
+    const int f1 = Cfg<128, zwarps(2, 1, 1)>::SMEM, f2 = Cfg<128, zwarps(2, 2, 2)>::SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_herk_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<128>::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<256>::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, f1);
-    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<128, 2, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, f1);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<128, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, f2);
-    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<128, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, f2);
-    const int w1 = Cfg<256, zwarps(1, 1, 1)>::SMEM, w2 = Cfg<256, zwarps(1, 2, 2)>::SMEM;
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<256, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, w1);
+    const int w1 = Cfg<256, zwarps(2, 1, 1)>::SMEM, w2 = Cfg<256, zwarps(2, 2, 2)>::SMEM;
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<256, 2, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, w1);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_herk_tc<256, 1, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, w2);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_herk_tc<256, 2, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, w2);
     return e;
 }
 
 bool herk_tc_fusable(int bn, int zprec, int n_ax, int n_feed) {
-    return (bn == 128 || bn == 256) && (zprec == 1 || zprec == 2) && n_ax == n_feed && (n_ax == 1 || n_ax == 2);
+    return (bn == 128 || bn == 256) && zprec == 2 && n_ax == n_feed && (n_ax == 1 || n_ax == 2);
 }
 
 int herk_tc_units(int rows, int n_slots, int split, int bn) {
@@ -700,18 +692,10 @@ cudaError_t launch_herk_tc(const Inst* d_inst, int inst0, int n_inst, LiveTables
     if (zj) {
         if (!herk_tc_fusable(bn, zprec, zj->m.n_ax, zj->m.n_feed)) return cudaErrorInvalidValue;
         if (bn == 256) {
-            if (zj->m.n_ax == 1) {
-                if (zprec == 1) MV_LB(256, 1, 1, 1);
-                MV_LB(256, 2, 1, 1);
-            }
-            if (zprec == 1) MV_LB(256, 1, 2, 2);
+            if (zj->m.n_ax == 1) MV_LB(256, 2, 1, 1);
             MV_LB(256, 2, 2, 2);
         }
-        if (zj->m.n_ax == 1) {
-            if (zprec == 1) MV_LB(128, 1, 1, 1);
-            MV_LB(128, 2, 1, 1);
-        }
-        if (zprec == 1) MV_LB(128, 1, 2, 2);
+        if (zj->m.n_ax == 1) MV_LB(128, 2, 1, 1);
         MV_LB(128, 2, 2, 2);
     }
     if (bn == 128) MV_LB(128, 0, 1, 1);

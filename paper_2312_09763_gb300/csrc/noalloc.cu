@@ -3,13 +3,14 @@
 //
 // The regular path keeps the cut's per-block live counts and their prefix
 // offsets in workspace that the context allocates.  Some callers cannot
-// allocate device memory at the moment they need this step: code that runs
-// while a CUDA stream is being captured into a graph (cudaMalloc is not a
-// stream operation and breaks or invalidates the capture), hosts whose device
-// memory all belongs to a framework's own pool, and latency-critical loops
-// that cannot afford cudaMalloc's implicit device synchronisation.  This
-// entry point serves them: its scratch is the file-scope array below, which
-// every GPU that loads this library holds until the process exits.
+// allocate device memory at the moment they need this step: hosts whose
+// device memory all belongs to a framework's own pool (a cudaMalloc beside
+// the pool can fail or fragment it), and latency-critical loops that cannot
+// afford cudaMalloc's implicit device synchronisation.  This entry point
+// serves them: its scratch is the file-scope array below, which every GPU
+// that loads this library holds until the process exits.  The 3 x 3 rotation
+// reaches the device as a kernel argument (copied at launch), so no host
+// buffer has to outlive the call.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -29,6 +30,16 @@ constexpr long long kMaxStaticSources = (long long)kMaxCullBlocks * 256;  // 2,0
 // so nothing needs clearing; calls that overlap on the GPU race on it.
 static __device__ __align__(256) int g_cull_scratch[2 * kMaxCullBlocks];
 static __device__ __align__(256) double g_cull_rotation[9];
+
+// Kernel argument carrying the rotation by value.
+struct Rot9 {
+    double r[9];
+};
+
+// Writes the rotation into g_cull_rotation (one thread per entry).
+__global__ void k_put_rotation(Rot9 R) {
+    if (threadIdx.x < 9) g_cull_rotation[threadIdx.x] = R.r[threadIdx.x];
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -52,6 +63,8 @@ extern "C" mv_status mv_horizon_cull_static(int64_t n_src, const double* xeq_dev
         return fail(MV_ERR_ARG, "mv_horizon_cull_static: NULL pointer argument");
     if (!std::isfinite(lst_rad) || !std::isfinite(latitude_rad))
         return fail(MV_ERR_ARG, "mv_horizon_cull_static: LST and latitude must be finite");
+    if (std::fabs(latitude_rad) > 0.5 * mv::kPi)
+        return fail(MV_ERR_ARG, "mv_horizon_cull_static: |latitude| must be <= pi/2");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(MV_ERR_CUDA, "mv_horizon_cull_static: no current CUDA device");
@@ -77,12 +90,10 @@ extern "C" mv_status mv_horizon_cull_static(int64_t n_src, const double* xeq_dev
     // eq. "rotation" of arXiv:2312.09763 with hour angle H = -LST (rows E, N, U)
     const double H = -lst_rad;
     const double sH = std::sin(H), cH = std::cos(H), sl = std::sin(latitude_rad), cl = std::cos(latitude_rad);
-    const double R[9] = {sH, cH, 0.0, -sl * cH, sl * sH, cl, cl * cH, -cl * sH, sl};
+    const Rot9 R = {{sH, cH, 0.0, -sl * cH, sl * sH, cl, cl * cH, -cl * sH, sl}};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(rot, R, sizeof(R), cudaMemcpyHostToDevice, st) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(MV_ERR_CUDA, "mv_horizon_cull_static: rotation upload failed");
-    }
+    k_put_rotation<<<1, 32, 0, st>>>(R);
+    if (cudaGetLastError() != cudaSuccess) return fail(MV_ERR_CUDA, "mv_horizon_cull_static: rotation launch failed");
     mv::Model m{};
     m.n_src = n_src;
     m.xeq = xeq_dev;

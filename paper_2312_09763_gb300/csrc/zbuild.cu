@@ -115,7 +115,7 @@ cudaError_t launch_zbuild(const Model& m, const Inst* d_inst, const Chan* d_chan
     k_zbuild<P, A, F><<<(unsigned)grid, 128, 0, st>>>(m, d_inst, d_groups, g_first, lt, d_wa, wa_pitch, d_amax, d_u, \
                                                       d_u_lo, rows, k_pitch, apb, d_aph, n_phase, nx, ny, n_items)
 #define MV_ZB_P(A, F) \
-    do { if (prec == 0) MV_ZB(0, A, F); else if (prec == 1) MV_ZB(1, A, F); else MV_ZB(2, A, F); } while (0)
+    do { if (prec == 0) MV_ZB(0, A, F); else MV_ZB(2, A, F); } while (0)
     if (m.n_ax == 1) {
         if (m.n_feed == 1) MV_ZB_P(1, 1); else MV_ZB_P(1, 2);
     } else {

@@ -16,7 +16,6 @@
 // (antenna, source) and the channel phases advance by exact 64-bit integer
 // addition.
 #pragma once
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -73,11 +72,12 @@ __device__ __forceinline__ void cos_sin_turns(unsigned long long F, float& c, fl
     s = __int_as_float(__float_as_int(b) ^ (int)(((q & 2u)) << 30));
 }
 
-// Store 2 n_ax consecutive entries of one row of U (two sources): FP32, or
-// the hi and lo halves (BF16, or FP16 of values already scaled) in the two
-// planes.
+// Store 2 n_ax consecutive entries of one row of U (two sources): FP32
+// (PREC 0), or the hi and lo FP16 halves of values already scaled (PREC 2) in
+// the two planes.
 template <int PREC, int NAX>
 __device__ __forceinline__ void put_row(void* pu, void* pl, const float* v) {
+    static_assert(PREC == 0 || PREC == 2, "FP32 or FP16 hi + lo");
     if constexpr (PREC == 0) {
         float* p = static_cast<float*>(pu);
         if constexpr (NAX == 1) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
@@ -87,19 +87,11 @@ __device__ __forceinline__ void put_row(void* pu, void* pl, const float* v) {
 #pragma unroll
         for (int i = 0; i < NAX; ++i) {
             const float x0 = v[2 * i], x1 = v[2 * i + 1];
-            if constexpr (PREC == 1) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-                const float2 hf = __bfloat1622float2(h);
-                const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-                hi[i] = *reinterpret_cast<const uint32_t*>(&h);
-                lo[i] = *reinterpret_cast<const uint32_t*>(&l);
-            } else {
-                const __half2 h = __floats2half2_rn(x0, x1);
-                const float2 hf = __half22float2(h);
-                const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
-                hi[i] = *reinterpret_cast<const uint32_t*>(&h);
-                lo[i] = *reinterpret_cast<const uint32_t*>(&l);
-            }
+            const __half2 h = __floats2half2_rn(x0, x1);
+            const float2 hf = __half22float2(h);
+            const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+            hi[i] = *reinterpret_cast<const uint32_t*>(&h);
+            lo[i] = *reinterpret_cast<const uint32_t*>(&l);
         }
         if constexpr (NAX == 1) {
             *static_cast<uint32_t*>(pu) = hi[0];

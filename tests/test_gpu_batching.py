@@ -17,7 +17,7 @@ from helpers import oracle_problem, rel_err, sample_pairs, simulator
 from paper_2312_09763_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp32": 1e-5, "fp16x3": 1e-5, "bf16x3": 2e-5}  # BF16x3 keeps ~16 bits per entry of Z
+TOL = {"fp32": 1e-5, "fp16x3": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +26,7 @@ def uneven():
     return w, oracle_problem(w)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
 def test_uneven_pairs_sampled_parity(uneven, prec):
     w, P = uneven
     sim = simulator(w)
@@ -44,13 +44,13 @@ def test_uneven_pairs_sampled_parity(uneven, prec):
 
 def test_graph_replay_matches_uncaptured_run():
     w = synth.hera_like(n_ant=120, n_src=20_000, n_chan=6, n_times=3, n_za=46, n_az=120)
-    a = simulator(w, use_graph=False).simulate(w.lsts, w.freqs, "bf16x3").cpu().numpy()
+    a = simulator(w, use_graph=False).simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
     sim = simulator(w, use_graph=True)
     out = None
     for _ in range(3):   # capture once, then replay
         import torch
         out = torch.empty((3, 6, 120, 120), dtype=torch.complex64, device="cuda") if out is None else out
-        b = sim.simulate(w.lsts, w.freqs, "bf16x3", out=out).cpu().numpy()
+        b = sim.simulate(w.lsts, w.freqs, "fp16x3", out=out).cpu().numpy()
         assert np.array_equal(a, b)
     assert sim.last_launch_count() > 0
 
@@ -68,7 +68,7 @@ def test_overlapped_batches_match_serial(prec):
     assert rel_err(a[1, 4], oracle.vis(P, w.lsts[1], w.freqs[4])) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["fp16x3"])
 @pytest.mark.parametrize("beam", ["scalar", "jones_full_stokes"])
 @pytest.mark.parametrize("split", [1, 3])
 @pytest.mark.parametrize("tile_n", [128, 256])
@@ -109,11 +109,11 @@ def test_herk_configurations(tile_n, split, flush):
 def test_autotune_then_simulate():
     w = synth.hera_like(n_ant=200, n_src=30_000, n_chan=16, n_times=2, n_za=46, n_az=120)
     sim = simulator(w)
-    t = sim.autotune(w.lsts, w.freqs, "bf16x3")
+    t = sim.autotune(w.lsts, w.freqs, "fp16x3")
     assert t["tile_n"] in (128, 256) and t["split"] >= 1 and t["candidates"] > 4 and t["herk_ms"] > 0
     # fused and separate schedules are both timed, at 128 and 256 columns
     assert t["fused"] in (True, False) and t["candidates"] >= 4 * 7
-    V = sim.simulate(w.lsts, w.freqs, "bf16x3").cpu().numpy()
+    V = sim.simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
     P = oracle_problem(w)
     pa, pb = sample_pairs(w.n_ant, 200, seed=2)
     vo = oracle.vis(P, w.lsts[1], w.freqs[7], pairs=(pa, pb))[:, 0, 0]

@@ -17,11 +17,11 @@ from helpers import oracle_problem, rel_err, sample_pairs, simulator
 from paper_2312_09763_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-TOL = {"fp32": 1e-5, "fp16x3": 1e-5, "bf16x3": 2e-5}
+TOL = {"fp32": 1e-5, "fp16x3": 1e-5}
 
 
 @pytest.mark.parametrize("full_stokes", [False, True])
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
 def test_small_diffuse_full_parity(prec, full_stokes):
     w = synth.polarised_diffuse(n_ant=40, nside=16, n_chan=2, n_times=2, n_za=31, n_az=72, lmax=40,
                                 full_stokes=full_stokes)
@@ -45,7 +45,7 @@ def diffuse():
     return w, stokes
 
 
-@pytest.mark.parametrize("prec,full_stokes", [("fp32", False), ("bf16x3", False), ("fp16x3", False),
+@pytest.mark.parametrize("prec,full_stokes", [("fp32", False), ("fp16x3", False),
                                               ("fp32", True), ("fp16x3", True)])
 def test_full_size_diffuse_sampled(diffuse, prec, full_stokes):
     w, stokes = diffuse

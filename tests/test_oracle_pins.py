@@ -348,3 +348,118 @@ def test_batched_uneven_generator_live_range():
           for t in np.linspace(0, 2 * np.pi, 25)]
     # 40 % uniform + 60 % clustered: about 20 % to 80 % of the catalogue above the horizon
     assert 0.15 * 20_000 < min(up) < 0.30 * 20_000 and 0.75 * 20_000 < max(up) <= 0.85 * 20_000
+
+
+# ------------------------------------------------------------ tabulated beams
+# vis_with_beam_fn is the checker of every learned-beam visibility test: it
+# takes the beams of a caller's model at the live sources (a table in
+# catalogue order of the live sources, [beam][feed][ax][n_live]) instead of
+# the grid.  Fed the oracle's own grid interpolation at those directions it
+# must reproduce oracle.vis to rounding; a table in another source order or a
+# dropped per-antenna beam index (Sec. 3.1 indirection a_i -> iota) must not.
+
+
+def _two_beam_problem(n_feed=1, n_ax=1, stokes=False, n_src=400, seed=9):
+    if n_ax == 1:
+        fn = lambda p, k, AZ, ZA, NU: (np.cos(ZA) ** 2 * (1 + 0.3 * np.sin(2 * AZ))
+                                       + 0.1j * np.sin(ZA) * np.cos(AZ)) * (NU / 150e6)
+    else:
+        fn = lambda p, k, AZ, ZA, NU: ((np.cos(ZA) * np.cos(AZ + 0.4 * p) if k == 0 else -np.sin(AZ + 0.4 * p))
+                                       * np.exp(-ZA ** 2) * (1 + 0.05j * (p + k)) * (NU / 150e6))
+    b = grid_beam(n_feed=n_feed, n_ax=n_ax, fn=fn)
+    vals = np.concatenate([b[1], b[1] * (0.6 - 0.5j) + 0.05 * np.roll(b[1], 7, axis=-1)], axis=0)
+    beam = ("grid", vals) + b[2:]
+    p = small_problem(n_ant=7, n_src=n_src, beam=beam, seed=seed)
+    p.beam_idx = np.array([0, 1, 1, 0, 1, 0, 0], dtype=np.int32)
+    if stokes:
+        g = np.random.default_rng(seed + 1)
+        frac = g.uniform(0, 0.5, n_src)
+        ang = g.uniform(0, 2 * np.pi, n_src)
+        p.stokes_quv = np.stack([frac * np.cos(ang), frac * np.sin(ang), 0.1 * g.uniform(-1, 1, n_src)]) * p.flux_ref
+    return p
+
+
+@pytest.mark.parametrize("n_feed,n_ax,stokes", [(1, 1, False), (2, 2, False), (2, 2, True)])
+def test_tabulated_beam_path_equals_gridded_path(n_feed, n_ax, stokes):
+    p = _two_beam_problem(n_feed, n_ax, stokes)
+    for lst, nu in [(0.4, 147.3e6), (3.9, 151.1e6)]:
+        V = oracle.vis(p, lst, nu)
+        Vt = oracle.vis_with_beam_fn(p, lst, nu, lambda az, za, f: oracle.beam_eval(p, az, za, f))
+        assert np.abs(Vt - V).max() <= 1e-14 * np.abs(V).max()
+        # live directions in catalogue order of the live sources
+        az, za = oracle.live_directions(p, lst)
+        assert az.size == oracle.count_live(p, lst)
+
+
+def test_tabulated_beam_path_catches_source_order_and_beam_index_slips():
+    p = _two_beam_problem()
+    lst, nu = 0.4, 147.3e6
+    V = oracle.vis(p, lst, nu)
+    good = lambda az, za, f: oracle.beam_eval(p, az, za, f)
+    # a table of the live sources in reverse order
+    rev = lambda az, za, f: oracle.beam_eval(p, az, za, f)[..., ::-1]
+    assert np.abs(oracle.vis_with_beam_fn(p, lst, nu, rev) - V).max() > 1e-3 * np.abs(V).max()
+    # the per-antenna beam index dropped: every antenna on beam 0
+    q = _two_beam_problem()
+    q.beam_idx = None
+    Vq = oracle.vis_with_beam_fn(q, lst, nu, good)
+    assert np.abs(Vq - V).max() > 1e-3 * np.abs(V).max()
+
+
+def test_tabulated_beam_zenith_source_closed_form():
+    # one source at the zenith, a caller's table of one complex value per beam
+    # and component: V_ab^{pq} = I sum_k A_{beta(a)}^{pk} conj(A_{beta(b)}^{qk})
+    lst, lat = 1.7, -30.7 * DEG
+    tab = np.array([[[[0.8 + 0.3j], [0.1 - 0.2j]], [[-0.3 + 0.1j], [0.7 + 0.0j]]],
+                    [[[-0.2 + 0.9j], [0.4 + 0.4j]], [[0.5 - 0.1j], [-0.6 + 0.2j]]]])   # [beam][feed][ax][1]
+    enu = np.zeros((4, 3))
+    enu[:, 0] = [0.0, 14.6, 29.2, -7.3]
+    bidx = np.array([1, 0, 1, 0], dtype=np.int32)
+    grid = grid_beam(n_feed=2, n_ax=2, fn=lambda p, k, AZ, ZA, NU: 1 + 0 * AZ)
+    p = oracle.Problem(ra=[lst], dec=[lat], flux_ref=[2.5], enu=enu, lat=lat, beam=grid, beam_idx=bidx)
+    V = oracle.vis_with_beam_fn(p, lst, 150e6, lambda az, za, f: tab).reshape(4, 2, 4, 2)
+    J = tab[..., 0]
+    for a in range(4):
+        for b in range(4):
+            want = 2.5 * J[bidx[a]] @ J[bidx[b]].conj().T
+            assert np.abs(V[a, :, b, :] - want).max() < 1e-13
+
+
+# ------------------------------------------------------------ sincos polynomials
+# The Z build evaluates cos(2 pi x) and sin(2 pi x) for x in [-1/8, 1/8] turn
+# with polynomials in x^2 whose coefficients sit in csrc/zcore.cuh.  They were
+# fitted (least squares on Chebyshev nodes) to sin(2 pi x) / x and cos(2 pi x)
+# with an error below 2e-9 in FP64; rounded to FP32 the coefficients give
+# polynomials within 3.0e-8 (sin) and 6.7e-9 (cos) of the exact functions, about
+# half an FP32 ulp of values near 0.7.  This pin reads the coefficients from the
+# source and checks that bound in FP64, so a mistyped or reordered coefficient
+# fails here on the CPU.
+
+
+def _zcore_coefficients():
+    import re
+    src = open(os.path.join(os.path.dirname(GOLDEN), "..", "paper_2312_09763_gb300", "csrc", "zcore.cuh")).read()
+    body = src[src.index("cos_sin_turns"):]
+    sp = body[body.index("const float sp"):body.index(";", body.index("const float sp"))]
+    cp = body[body.index("const float cp"):body.index(";", body.index("const float cp"))]
+    num = r"(-?\d+\.\d+(?:e-?\d+)?)f"
+    s = [float(v) for v in re.findall(num, sp)]
+    c = [float(v) for v in re.findall(num, cp)]
+    return s, c
+
+
+def test_sincos_polynomial_coefficients_meet_their_bound():
+    s, c = _zcore_coefficients()
+    # sin: ((s0 x2 + s1) x2 + s2) x2 + s3, times x; cos: (((c0 x2 + c1) x2 + c2) x2 + c3) x2 + c4
+    assert len(s) == 4 and len(c) == 5
+    x = np.linspace(-0.125, 0.125, 200_001)
+    x2 = x * x
+    ps = ((s[0] * x2 + s[1]) * x2 + s[2]) * x2 + s[3]
+    pc = (((c[0] * x2 + c[1]) * x2 + c[2]) * x2 + c[3]) * x2 + c[4]
+    assert np.abs(ps * x - np.sin(2 * np.pi * x)).max() < 3.1e-8
+    assert np.abs(pc - np.cos(2 * np.pi * x)).max() < 7e-9
+    # the quarter-turn reduction: |x| <= 1/8 keeps both within those bounds at the
+    # ends, and sin / cos agree at x = 1/8 (both sqrt(1/2)) to the same order
+    assert abs(ps[-1] * x[-1] - pc[-1]) < 4e-8
+    # the leading terms are the Taylor ones to FP32 rounding (2 pi and 1, -(2 pi)^2 / 2)
+    assert abs(s[3] - 2 * np.pi) < 1e-6 and c[4] == 1.0 and abs(c[3] + 2 * np.pi ** 2) < 1e-4

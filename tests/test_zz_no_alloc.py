@@ -1,11 +1,14 @@
 """The allocation-free horizon cut (mv_horizon_cull_static) against the
 regular path (needs a GB300).
 
-Callers that cannot allocate device memory (stream capture, framework-owned
-memory pools, latency-critical loops) use mv_horizon_cull_static, whose
-scratch is a static device array.  Its live count must equal the regular
-simulate path's (an integer decision: bit-exact), its live list must be the
-catalogue indices with Up > 0 in order, and two calls in a row must agree.
+Callers that cannot allocate device memory when they run this step (hosts
+whose device memory all belongs to a framework's pool, latency-critical loops
+that cannot take cudaMalloc's device synchronisation) use
+mv_horizon_cull_static, whose scratch is a static device array.  Its live
+count must equal the regular simulate path's (an integer decision:
+bit-exact), its live list must be the catalogue indices with Up > 0 in order,
+its East-North-Up and (az, za) outputs must match the oracle's, and two calls
+in a row must agree.
 This file is collected last so that a failure here stops a -x run only after
 every other test has run.
 """
@@ -51,6 +54,14 @@ def test_static_cull_matches_regular_path_twice():
         live = np.nonzero(enu_o[:, 2] > 0)[0]
         assert np.array_equal(idx[:k].cpu().numpy(), live)
         assert np.abs(enu[:, :k].cpu().numpy().T - enu_o[live]).max() < 1e-15
+        # (az, za) in FP32: za directly, az through the horizontal direction it
+        # names (sin za weights it, since az is undefined at the zenith)
+        az_o, za_o = oracle.azza(enu_o[live])
+        got = azza[:k].cpu().numpy().astype(np.float64)
+        assert np.abs(got[:, 1] - za_o).max() < 1e-6
+        daz = np.angle(np.exp(1j * (got[:, 0] - az_o)))
+        assert np.abs(daz * np.sin(za_o)).max() < 1e-6
+        assert np.all((got[:, 0] >= 0) & (got[:, 0] <= 2 * np.pi))
 
 
 def test_static_cull_rejects_sizes_beyond_its_maximum():
@@ -59,3 +70,6 @@ def test_static_cull_rejects_sizes_beyond_its_maximum():
     dummy = ctypes.c_void_p(16)
     rc = lib.mv_horizon_cull_static(2_097_153, dummy, 0.0, 0.0, dummy, dummy, dummy, dummy, None)
     assert rc == 1 and b"2097152" in lib.mv_last_error()
+    # a latitude the regular path refuses is refused here too
+    rc = lib.mv_horizon_cull_static(1000, dummy, 0.0, 1.6, dummy, dummy, dummy, dummy, None)
+    assert rc == 1 and b"latitude" in lib.mv_last_error()
