@@ -348,15 +348,17 @@ mv_status mv_horizon_cull_static(int64_t n_src, const double *xeq_dev, double ls
  *   h_l = relu(W_l h_{l-1} + b_l) for depth hidden layers of `width` units;
  *   y = W_out h + b_out: 2 n_feed n_ax real outputs (re, im of each component
  *       in (feed, axis) order).
- * It is trained on the GPU (BF16 tensor-core products, FP32 master weights,
- * Adam, MSE) on samples (beta, az, za, nu) drawn uniformly and labelled by the
- * Keys interpolation of the gridded beam set with mv_set_beam_grid, one
- * embedding per gridded beam. */
+ * It is trained on the GPU (every product of the forward and backward pass on
+ * the tcgen05 tensor cores with BF16 operands and FP32 accumulation, FP32
+ * master weights, Adam, MSE) on samples (beta, az, za, nu) drawn uniformly and
+ * labelled by the Keys interpolation of the gridded beam set with
+ * mv_set_beam_grid, one embedding per gridded beam.  The first layer's input
+ * is padded to d0p = max(64, 2 n_freq + emb_dim rounded up to 32) columns. */
 typedef struct {
     int n_freq;                          /* Fourier frequencies (default 64) */
-    int emb_dim;                         /* embedding size (16) */
-    int width;                           /* hidden width (256) */
-    int depth;                           /* hidden layers (4) */
+    int emb_dim;                         /* embedding size (16); 2 n_freq + emb_dim <= 240 */
+    int width;                           /* hidden width (256; a multiple of 16 in [64, 256]) */
+    int depth;                           /* hidden layers (4; 1 to 16) */
     float sigma_az, sigma_za, sigma_nu;  /* scales of B's columns (2, 3, 1) */
     uint64_t seed;                       /* initial weights and B */
 } mv_mlp_config;
@@ -377,8 +379,8 @@ mv_status mv_surrogate_train(mv_ctx *ctx, int steps, int batch, float lr0, float
 /* Parameters: *n_params receives the count; if host != NULL the FP32 master
  * vector is copied there; if fourier != NULL, B ([n_freq][3]); if layout !=
  * NULL, 2 (depth + 1) + 2 offsets: W_l, b_l for l = 0..depth (W_depth is the
- * output layer, stored [8][width]; W_0 is [width][d0p] with d0p = 2 n_freq +
- * emb_dim rounded up to 32), then the embedding offset and d0p. */
+ * output layer, stored [8][width]; W_0 is [width][d0p] with d0p = max(64,
+ * 2 n_freq + emb_dim rounded up to 32)), then the embedding offset and d0p. */
 mv_status mv_surrogate_params(mv_ctx *ctx, int64_t *n_params, float *host, float *fourier, int64_t *layout);
 mv_status mv_surrogate_set_params(mv_ctx *ctx, const float *host);
 

@@ -1096,7 +1096,7 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
     mv_ctx* c = new mv_ctx();
     c->device = device;
     c->n_sms = pr.multiProcessorCount;
-    if (herk_tc_init() != cudaSuccess || mlp_tc_init() != cudaSuccess) {
+    if (herk_tc_init() != cudaSuccess || mlp_tc_init() != cudaSuccess || gemm_tc_init() != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return fail(MV_ERR_CUDA, "kernel attribute set-up failed");
@@ -1564,9 +1564,10 @@ mv_status mv_surrogate_create(mv_ctx* c, const mv_mlp_config* cfg) {
     mv_mlp_config k;
     mv_default_mlp_config(&k);
     if (cfg) k = *cfg;
-    if (k.n_freq < 1 || k.n_freq > 512 || k.emb_dim < 1 || k.emb_dim > 256 || k.width < 8 || k.width > 1024 ||
-        k.width % 8 || k.depth < 1 || k.depth > 16)
-        return fail(MV_ERR_ARG, "MLP configuration out of range");
+    if (k.n_freq < 1 || k.emb_dim < 1 || 2 * k.n_freq + k.emb_dim > 240 || k.width < 64 || k.width > 256 ||
+        k.width % 16 || k.depth < 1 || k.depth > 16)
+        return fail(MV_ERR_ARG, "MLP configuration out of range (width a multiple of 16 in [64, 256], 2 n_freq + "
+                                "emb_dim <= 240, depth 1-16)");
     DeviceGuard g(c->device);
     const Model& m = c->model;
     const double nu_lo = c->grid_nu0, nu_hi = c->grid_nu0 + (m.n_nu - 1) * c->grid_dnu;

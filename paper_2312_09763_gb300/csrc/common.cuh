@@ -250,6 +250,45 @@ cudaError_t launch_mlp_wa_tc(const MlpTcArgs& a, const Model& m, LiveTables lt, 
                              float ln_ratio, float2* wa_slot, long long wa_pitch, float* amax, int* d_err,
                              int n_sms, cudaStream_t st, long long* launches);
 
+// ------------------------------------- tensor-core products (mlp_train_tc.cu)
+// A K-major BF16 operand: rows x kext used of a [rows][ld] array (ld and the
+// base 16-byte aligned; columns past kext read as zero).
+struct GemmOperand {
+    const __nv_bfloat16* p;
+    long long ld;
+    int rows, kext;
+};
+// Fused epilogue of D = A B^T (see mlp_train_tc.cu).
+enum GemmEpiKind : int { GEPI_RELU = 0, GEPI_LOSS = 1, GEPI_MASK = 2, GEPI_F32 = 3, GEPI_EMB = 4, GEPI_Y = 5 };
+struct GemmEpi {
+    int kind;
+    void* out;                   // rows of D: BF16 (RELU, MASK, LOSS) or FP32 (F32, Y)
+    long long ldo;
+    __nv_bfloat16* outT;         // columns of D as rows (RELU, MASK: may be NULL; LOSS: 16 rows)
+    long long ldt;
+    const float* bias;           // RELU, LOSS, Y
+    const __nv_bfloat16* mask;   // MASK: h_prev, rows of ldm
+    long long ldm;
+    const float* target;         // LOSS: [M][n_out]
+    int n_out;                   // LOSS, Y
+    float gscale;                // LOSS: dL/dy = gscale (y - target)
+    double* loss;                // LOSS: sum of squared residuals (atomic)
+    const int* ant;              // EMB: beam of each row
+    float* gemb;                 // EMB: [n_beam][emb] (atomic)
+    int emb;
+    long long part_stride;       // F32: elements between the partials of two k-splits
+    float* bias_part;            // F32 (may be NULL): row sums of A over each k-split's K range,
+    long long ldo_bias;          // [split][M] at bias_part + split ldo_bias
+};
+cudaError_t gemm_tc_init();
+// D[M][N] = A[M][K] B[N][K]^T on tcgen05 with the epilogue e; the K axis is
+// cut into `splits` ranges (F32 writes one partial per range); two_row_tiles:
+// 256-row units (two 128-row MMAs sharing each B panel), for long-K products.
+cudaError_t launch_gemm_tc(const GemmOperand& A, const GemmOperand& B, int M, int N, int splits, bool two_row_tiles,
+                           const GemmEpi& e, int n_sms, int* d_err, cudaStream_t st, long long* launches);
+// CTAs of that launch.
+int gemm_tc_grid(int M, int N, int splits, bool two_row_tiles, int kext, int n_sms);
+
 // Exponent e of the exact power-of-two scale 2^e that brings max |Z| of an
 // instance into [2^13, 2^14) before the FP16 hi/lo split (the HERK epilogue
 // multiplies by 2^-2e).

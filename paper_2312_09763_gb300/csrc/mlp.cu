@@ -10,8 +10,14 @@
 //   x = (az / 2 pi, za / (pi/2), (nu - nu_mid) / nu_half)
 //   f = [sin(2 pi B x), cos(2 pi B x), e_a]  (B: F x 3, az column integer)
 //   h_l = relu(W_l h_{l-1} + b_l), y = W_out h_L + b_out;  MSE loss; Adam.
-// Matrix products run on the tensor cores (mma.sync m16n8k16, BF16 operands,
-// FP32 accumulation); master weights and Adam state are FP32.
+// Every matrix product of a training step runs on the tcgen05 tensor cores
+// (mlp_train_tc.cu: BF16 operands staged by TMA, FP32 accumulation in TMEM,
+// fused epilogues); master weights and Adam state are FP32.  The backward
+// products read transposed copies: the forward epilogues write each layer's
+// activations also as columns (with a row of ones appended, so that the
+// weight-gradient product yields the bias gradient as one more column), the
+// gradient epilogues do the same for dL/dz, and the optimiser keeps BF16
+// copies of W and W^T.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -27,252 +33,218 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
-// ------------------------------------------------------------------ GEMM
-enum Epi : int { EPI_F32 = 0, EPI_BIAS_RELU_BF16 = 1, EPI_BIAS_F32 = 2, EPI_MASK_BF16 = 3, EPI_BF16 = 4, EPI_F32_ADD = 5 };
-
-constexpr int GM = 128, GN = 128, GK = 32, GPAD = 8;
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// Load a GM x GK (or GN x GK) tile into shared memory laid out [row][k].
-// kmajor: source stored [rows][K] with leading dimension ld (k contiguous);
-// otherwise stored [K][rows] (row index contiguous).  Rows >= R or k >= K are
-// zero.  K and ld are multiples of 8.
-template <bool KMAJOR>
-__device__ __forceinline__ void load_tile(bf16 (*S)[GK + GPAD], const bf16* __restrict__ src, int ld, int r0, int R,
-                                          int k0, int K) {
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int idx = tid + q * 256;
-        if (KMAJOR) {
-            const int row = idx >> 2, ch = (idx & 3) * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (r0 + row < R && k0 + ch < K) v = *reinterpret_cast<const uint4*>(src + (long long)(r0 + row) * ld + k0 + ch);
-            *reinterpret_cast<uint4*>(&S[row][ch]) = v;
-        } else {
-            const int kr = idx >> 4, mc = (idx & 15) * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (k0 + kr < K && r0 + mc < R) {
-                if (r0 + mc + 8 <= R) {
-                    v = *reinterpret_cast<const uint4*>(src + (long long)(k0 + kr) * ld + r0 + mc);
-                } else {
-                    bf16 tmp[8];
-                    for (int j = 0; j < 8; ++j)
-                        tmp[j] = r0 + mc + j < R ? src[(long long)(k0 + kr) * ld + r0 + mc + j] : __float2bfloat16(0.f);
-                    v = *reinterpret_cast<uint4*>(tmp);
-                }
-            }
-            const bf16* e = reinterpret_cast<const bf16*>(&v);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) S[mc + j][kr] = e[j];
-        }
-    }
-}
-
-// C[M][N] = op(A)[M][K] op(B)[K][N] with a fused epilogue (see Epi).
-// A_KM: A stored [M][K], else [K][M].  B_KM: B stored [N][K], else [K][N].
-// blockIdx.z takes the k-range [z kc, (z + 1) kc); with EPI_F32_ADD the
-// partial products are added into C (which the caller zeroes).
-template <bool A_KM, bool B_KM>
-__global__ void __launch_bounds__(256)
-k_gemm(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B, int ldb, void* C, int ldc,
-       int epi, const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm, int kc) {
-    __shared__ __align__(16) bf16 As[GM][GK + GPAD];
-    __shared__ __align__(16) bf16 Bs[GN][GK + GPAD];
-    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps: 64 x 32 each
-    const int g = lane >> 2, t = lane & 3;
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-    const int kb = blockIdx.z * kc, ke = min(K, kb + kc);
-    for (int k0 = kb; k0 < ke; k0 += GK) {
-        load_tile<A_KM>(As, A, lda, m0, M, k0, ke);
-        load_tile<B_KM>(Bs, B, ldb, n0, N, k0, ke);
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; kk += 16) {
-            uint32_t af[4][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = wm * 64 + i * 16 + g;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int n = wn * 32 + j * 8 + g;
-                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 2 * t]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[n][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int m = m0 + wm * 64 + i * 16 + g + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + j * 8 + 2 * t + (r & 1);
-                if (m >= M || n >= N) continue;
-                float v = acc[i][j][r];
-                const long long o = (long long)m * ldc + n;
-                if (epi == EPI_F32) {
-                    static_cast<float*>(C)[o] = v;
-                } else if (epi == EPI_F32_ADD) {
-                    atomicAdd(static_cast<float*>(C) + o, v);
-                } else if (epi == EPI_BIAS_F32) {
-                    static_cast<float*>(C)[o] = v + bias[n];
-                } else if (epi == EPI_BIAS_RELU_BF16) {
-                    static_cast<bf16*>(C)[o] = __float2bfloat16(fmaxf(v + bias[n], 0.f));
-                } else if (epi == EPI_BF16) {
-                    static_cast<bf16*>(C)[o] = __float2bfloat16(v);
-                } else {
-                    const float mk = __bfloat162float(mask[(long long)m * ldm + n]) > 0.f ? 1.f : 0.f;
-                    static_cast<bf16*>(C)[o] = __float2bfloat16(v * mk);
-                }
-            }
-}
-
-cudaError_t gemm(bool a_km, bool b_km, int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb, void* C,
-                 int ldc, int epi, const float* bias, const bf16* mask, int ldm, cudaStream_t st, long long* L) {
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, 1);
-    int kc = (K + GK - 1) / GK * GK;
-    if (epi == EPI_F32_ADD) {
-        // split the (long) k axis so that the grid fills the GPU
-        const int tiles = grid.x * grid.y;
-        const int ks = std::max(1, std::min((K + 127) / 128, 600 / std::max(tiles, 1)));
-        kc = ((K + ks - 1) / ks + GK - 1) / GK * GK;
-        grid.z = (K + kc - 1) / kc;
-    }
-    if (a_km && b_km)
-        k_gemm<true, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, epi, bias, mask, ldm, kc);
-    else if (a_km)
-        k_gemm<true, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, epi, bias, mask, ldm, kc);
-    else if (b_km)
-        k_gemm<false, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, epi, bias, mask, ldm, kc);
-    else
-        k_gemm<false, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, epi, bias, mask, ldm, kc);
-    ++*L;
-    return cudaGetLastError();
-}
-
 // ------------------------------------------------------- small kernels
 struct Dims {
     int F, E, H, depth, n_out, n_ant;
-    int d0, d0p;  // feature width 2F + E, padded to a multiple of 32
+    int d0, d0p;  // feature width 2F + E, padded to a multiple of 32 (at least 64)
     float nu_mid, nu_half;
 };
 
-// Fourier features + embedding: X0[m][0..d0p) in BF16 (zero padding).
-__global__ void k_features(Dims d, const float* __restrict__ Bf, const float* __restrict__ emb, int M,
-                           const int* __restrict__ ant, const float* __restrict__ az, const float* __restrict__ za,
-                           const float* __restrict__ nu, bf16* __restrict__ X0) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)M * d.d0p) return;
-    const int m = (int)(i / d.d0p), j = (int)(i % d.d0p);
-    float v = 0.f;
-    if (j < 2 * d.F) {
-        const int f = j % d.F;
-        const float x0 = az[m] * 0.15915494309189535f;           // az / 2 pi
-        const float x1 = za[m] * 0.63661977236758134f;           // za / (pi / 2)
-        const float x2 = (nu[m] - d.nu_mid) / d.nu_half;
+// Fourier features + embedding: X0[m][0..d0p) in BF16 (zero padding), and
+// with X0T the same values as columns, X0T[j][m] (ld ldt).  A block of 256
+// threads takes 64 rows: each (row, frequency) pair evaluates its sine and
+// cosine once into a shared-memory tile, which is then written out as rows
+// and, with X0T, as columns (both coalesced).  Dynamic shared memory:
+// 64 (d0p + 2) BF16 values.
+constexpr int kFeatRows = 64;
+__global__ void __launch_bounds__(256)
+k_features(Dims d, const float* __restrict__ Bf, const float* __restrict__ emb, int M, const int* __restrict__ ant,
+           const float* __restrict__ az, const float* __restrict__ za, const float* __restrict__ nu,
+           bf16* __restrict__ X0, bf16* __restrict__ X0T, long long ldt) {
+    extern __shared__ bf16 tile[];  // [kFeatRows][d0p + 2]
+    const int ld = d.d0p + 2;
+    const int m0 = blockIdx.x * kFeatRows;
+    const int rl = threadIdx.x % kFeatRows, cg = threadIdx.x / kFeatRows;  // row, column group (4)
+    const int m = m0 + rl;
+    const bool valid = m < M;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    int a = 0;
+    if (valid) {
+        x0 = az[m] * 0.15915494309189535f;  // az / 2 pi
+        x1 = za[m] * 0.63661977236758134f;  // za / (pi / 2)
+        x2 = (nu[m] - d.nu_mid) / d.nu_half;
+        a = ant[m];
+    }
+    for (int f = cg; f < d.F; f += 4) {
         float ph = Bf[3 * f] * x0 + Bf[3 * f + 1] * x1 + Bf[3 * f + 2] * x2;  // turns
         ph -= rintf(ph);
-        float s, c;
-        sincospif(2.f * ph, &s, &c);
-        v = j < d.F ? s : c;
-    } else if (j < d.d0) {
-        v = emb[(long long)ant[m] * d.E + (j - 2 * d.F)];
+        float sv, cv;
+        sincospif(2.f * ph, &sv, &cv);
+        tile[rl * ld + f] = __float2bfloat16(valid ? sv : 0.f);
+        tile[rl * ld + d.F + f] = __float2bfloat16(valid ? cv : 0.f);
     }
-    X0[i] = __float2bfloat16(v);
-}
-
-// dY = 2 (y - t) / (M n_out) (BF16, padded outputs zero) and sum of squares.
-__global__ void k_loss(int M, int n_out, const float* __restrict__ Y, const float* __restrict__ T,
-                       bf16* __restrict__ dY, double* __restrict__ loss) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    float r2 = 0.f;
-    if (i < M * 8) {
-        const int m = i >> 3, o = i & 7;
-        float g = 0.f;
-        if (o < n_out) {
-            const float r = Y[i] - T[(long long)m * n_out + o];
-            r2 = r * r;
-            g = 2.f * r / (float)((long long)M * n_out);
-        }
-        dY[i] = __float2bfloat16(g);
-    }
-    for (int off = 16; off > 0; off >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, (double)r2);
-}
-
-// db[n] = sum_m dZ[m][n] (fixed order: one thread per column, rows in sequence
-// over a strided split, then a fixed tree in shared memory).
-__global__ void k_colsum(int M, int N, const bf16* __restrict__ dZ, int ld, float* __restrict__ db) {
-    __shared__ float part[8][32];
-    const int n = blockIdx.x * 32 + (threadIdx.x & 31), r = threadIdx.x >> 5;
-    float s = 0.f;
-    if (n < N)
-        for (int m = r; m < M; m += 8) s += __bfloat162float(dZ[(long long)m * ld + n]);
-    part[r][threadIdx.x & 31] = s;
+    for (int j = 2 * d.F + cg; j < d.d0p; j += 4)
+        tile[rl * ld + j] = __float2bfloat16(valid && j < d.d0 ? emb[(long long)a * d.E + (j - 2 * d.F)] : 0.f);
     __syncthreads();
-    if (r == 0 && n < N) {
-        float t = 0.f;
-        for (int q = 0; q < 8; ++q) t += part[q][threadIdx.x & 31];
-        db[n] = t;
+    // rows: consecutive threads along a row
+    for (int q = threadIdx.x; q < kFeatRows * d.d0p; q += blockDim.x) {
+        const int r = q / d.d0p, j = q % d.d0p;
+        if (m0 + r < M) X0[(long long)(m0 + r) * d.d0p + j] = tile[r * ld + j];
+    }
+    if (X0T) {
+        // columns: consecutive threads along m
+        for (int q = threadIdx.x; q < kFeatRows * d.d0p; q += blockDim.x) {
+            const int j = q / kFeatRows, r = q % kFeatRows;
+            if (m0 + r < M) X0T[(long long)j * ldt + m0 + r] = tile[r * ld + j];
+        }
     }
 }
 
-// Embedding gradient: columns [2F, 2F + E) of dX0, summed per antenna.
-__global__ void k_emb_grad(Dims d, int M, const int* __restrict__ ant, const bf16* __restrict__ dX0,
-                           float* __restrict__ gemb) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M * d.E) return;
-    const int m = i / d.E, e = i % d.E;
-    atomicAdd(&gemb[(long long)ant[m] * d.E + e], __bfloat162float(dX0[(long long)m * d.d0p + 2 * d.F + e]));
-}
-
-// Adam on one parameter array; writes the BF16 copy used by the products.
-__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, bf16* __restrict__ pb, float lr, float b1, float b2, float eps, float c1,
-                       float c2) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    p[i] = pi;
-    if (pb) pb[i] = __float2bfloat16(pi);
+cudaError_t launch_features(const Dims& d, const float* Bf, const float* emb, int M, const int* ant, const float* az,
+                            const float* za, const float* nu, bf16* X0, bf16* X0T, long long ldt, cudaStream_t st) {
+    const size_t sm = sizeof(bf16) * kFeatRows * (size_t)(d.d0p + 2);
+    k_features<<<(unsigned)((M + kFeatRows - 1) / kFeatRows), 256, sm, st>>>(d, Bf, emb, M, ant, az, za, nu, X0, X0T,
+                                                                            ldt);
+    return cudaGetLastError();
 }
 
 __global__ void k_to_bf16(long long n, const float* __restrict__ p, bf16* __restrict__ q) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) q[i] = __float2bfloat16(p[i]);
+}
+
+// The network's layers as the kernels below walk them: hidden layers, then
+// the output layer.  The weight gradient of layer l is summed from `splits`
+// partial products at part + part_off[l] + s part_stride[l], laid out
+// [nout][kin] (the output layer's rows padded to 16); its bias gradient from
+// the same products' row sums of dL/dz, bpart + bias_off[l] + s bias_ld[l].
+constexpr int kMaxLayers = 17;
+struct LayerTab {
+    int n;
+    long long off_w[kMaxLayers], off_b[kMaxLayers];
+    int kin[kMaxLayers], nout[kMaxLayers];
+    long long part_off[kMaxLayers], part_stride[kMaxLayers];
+    long long bias_off[kMaxLayers];
+    int bias_ld[kMaxLayers];
+    bf16* wt[kMaxLayers];  // W^T [kin][H] of the hidden layers
+};
+
+// BF16 copies of the weights that the products read: W_l^T of every hidden
+// layer, the output layer padded to 16 rows and its transpose padded to 64
+// columns (the padding is zero from allocation and never written).
+__global__ void k_weight_copies(LayerTab t, const float* __restrict__ p, int H, bf16* __restrict__ wout16,
+                                bf16* __restrict__ woutT) {
+    const int l = blockIdx.y;
+    const int kin = t.kin[l];
+    const long long n = (long long)t.nout[l] * kin;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int o = (int)(q / kin), i = (int)(q % kin);
+        const bf16 v = __float2bfloat16(p[t.off_w[l] + q]);
+        if (l < t.n - 1) {
+            t.wt[l][(long long)i * H + o] = v;
+        } else {
+            wout16[(long long)o * H + i] = v;
+            woutT[(long long)i * 64 + o] = v;
+        }
+    }
+}
+
+// Weight and bias gradients from the k-split partial products, summed in a
+// fixed order (deterministic).
+// Weight gradient (o, i) of layer l from its k-split partials.
+__device__ __forceinline__ float layer_grad(const LayerTab& t, int l, const float* __restrict__ part, int splits, int o,
+                                            int i) {
+    float sum = 0.f;
+    const float* P = part + t.part_off[l] + (long long)o * t.kin[l] + i;
+    for (int s = 0; s < splits; ++s) sum += P[s * t.part_stride[l]];
+    return sum;
+}
+
+// Bias gradient o of layer l from its partial rows, by one warp: lane k adds
+// rows k, k + 32, ..., then a fixed butterfly (the same sum on every lane).
+__device__ __forceinline__ float bias_grad_warp(const LayerTab& t, int l, const float* __restrict__ bpart, int brows,
+                                                int o, int lane) {
+    const float* B = bpart + t.bias_off[l] + o;
+    float sum = 0.f;
+    for (int r = lane; r < brows; r += 32) sum += B[(long long)r * t.bias_ld[l]];
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    return sum;
+}
+
+__global__ void k_reduce_grads(LayerTab t, const float* __restrict__ part, int splits, const float* __restrict__ bpart,
+                               int brows, float* __restrict__ g) {
+    const int l = blockIdx.y;
+    const int kin = t.kin[l], nout = t.nout[l];
+    const long long n = (long long)nout * kin;
+    const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+    for (long long q = q0; q < n; q += step) {
+        const int o = (int)(q / kin), i = (int)(q % kin);
+        g[t.off_w[l] + q] = layer_grad(t, l, part, splits, o, i);
+    }
+    // biases: one warp each
+    const int lane = threadIdx.x & 31;
+    for (long long w = q0 >> 5; w < nout; w += step >> 5) {
+        const float b = bias_grad_warp(t, l, bpart, brows, (int)w, lane);
+        if (lane == 0) g[t.off_b[l] + w] = b;
+    }
+}
+
+struct AdamArgs {
+    float lr, b1, b2, eps, c1, c2;
+};
+
+__device__ __forceinline__ float adam_step(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                                           long long i, float gi, const AdamArgs& a) {
+    const float mi = a.b1 * m[i] + (1.f - a.b1) * gi;
+    const float vi = a.b2 * v[i] + (1.f - a.b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - a.lr * (mi / a.c1) / (sqrtf(vi / a.c2) + a.eps);
+    p[i] = pi;
+    return pi;
+}
+
+// One optimiser step of training: the weight and bias gradients summed from
+// the k-split partials (fixed order), Adam on them and on the embedding
+// (whose gradient is in g), and every BF16 copy the products read (W, W^T,
+// the padded output layer).  blockIdx.y: layer, or t.n for the embedding.
+__global__ void k_reduce_adam(LayerTab t, const float* __restrict__ part, int splits, const float* __restrict__ bpart,
+                              int brows, const float* __restrict__ g, long long off_emb, long long n_emb,
+                              float* __restrict__ p, float* __restrict__ am, float* __restrict__ av,
+                              bf16* __restrict__ pb, int H, bf16* __restrict__ wout16, bf16* __restrict__ woutT,
+                              AdamArgs a) {
+    const int l = blockIdx.y;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l == t.n) {
+        for (long long q = q0; q < n_emb; q += step) {
+            const long long i = off_emb + q;
+            pb[i] = __float2bfloat16(adam_step(p, am, av, i, g[i], a));
+        }
+        return;
+    }
+    const bool out = l == t.n - 1;
+    const int kin = t.kin[l], nout = t.nout[l];
+    const long long n = (long long)nout * kin;
+    const int lane = threadIdx.x & 31;
+    for (long long w = q0 >> 5; w < nout; w += step >> 5) {  // biases: one warp each
+        const float gb = bias_grad_warp(t, l, bpart, brows, (int)w, lane);
+        if (lane == 0) {
+            const long long ib = t.off_b[l] + w;
+            pb[ib] = __float2bfloat16(adam_step(p, am, av, ib, gb, a));
+        }
+    }
+    for (long long q = q0; q < n; q += step) {
+        const int o = (int)(q / kin), i = (int)(q % kin);
+        const float sum = layer_grad(t, l, part, splits, o, i);
+        const long long iw = t.off_w[l] + (long long)o * kin + i;
+        const bf16 w = __float2bfloat16(adam_step(p, am, av, iw, sum, a));
+        pb[iw] = w;
+        if (!out) {
+            t.wt[l][(long long)i * H + o] = w;
+        } else {
+            wout16[(long long)o * H + i] = w;
+            woutT[(long long)i * 64 + o] = w;
+        }
+    }
+}
+
+// Row r of a [rows][ld] BF16 array set to one (the bias row of the
+// transposed activations).
+__global__ void k_fill_row(bf16* __restrict__ a, long long ld, long long n, float v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = __float2bfloat16(v);
+    (void)ld;
 }
 
 // ----------------------------------------------------- training samples
@@ -295,16 +267,13 @@ __device__ __forceinline__ float keys_w(float x) {
     return 0.f;
 }
 
-// Keys-cubic interpolation of component `comp` of beam `b` of the raw grid at
-// (az, za) and fractional frequency node u (Sec. 2.4; pole and az wrap as in
-// the beam step of the simulator).
-__device__ float2 grid_value(const Model& m, const float2* __restrict__ grid, int b, int comp, float az, float za,
-                             float u) {
+// Keys-cubic interpolation in (za, az) of component `comp` of beam `b` of the
+// raw grid at frequency node f (Sec. 2.4; pole and az wrap as in the beam
+// step of the simulator).
+__device__ float2 grid_value_node(const Model& m, const float2* __restrict__ grid, int b, int comp, float az,
+                                  float za, int f) {
     const long long plane = (long long)m.n_za * m.n_az;
-    const float2* G = grid + ((long long)b * m.n_feed * m.n_ax + comp) * m.n_nu * plane;
-    const float fu = floorf(u), tu = u - fu;
-    const int f0 = (int)fu - 1;
-    const float wf[4] = {keys_w(tu + 1.f), keys_w(tu), keys_w(1.f - tu), keys_w(2.f - tu)};
+    const float2* G = grid + (((long long)b * m.n_feed * m.n_ax + comp) * m.n_nu + f) * plane;
     const float uz = za / m.dza, ua = az / m.daz;
     const float fz = floorf(uz), fa = floorf(ua);
     const float tz = uz - fz, ta = ua - fa;
@@ -313,46 +282,69 @@ __device__ float2 grid_value(const Model& m, const float2* __restrict__ grid, in
     const float wa[4] = {keys_w(ta + 1.f), keys_w(ta), keys_w(1.f - ta), keys_w(2.f - ta)};
     const float pole_sign = m.n_ax == 2 ? -1.f : 1.f;
     float re = 0.f, im = 0.f;
+#pragma unroll
     for (int r = 0; r < 4; ++r) {
         int row = z0 + r, sh = 0;
         float sg = 1.f;
         if (row < 0) { row = -row; sh = m.n_az / 2; sg = pole_sign; }
         if (row > m.n_za - 1) row = m.n_za - 1;
+#pragma unroll
         for (int q = 0; q < 4; ++q) {
             int col = (a0 + q + sh) % m.n_az;
             if (col < 0) col += m.n_az;
             const float w2 = wz[r] * wa[q] * sg;
-            for (int j = 0; j < 4; ++j) {
-                const float2 v = G[(long long)(f0 + j) * plane + (long long)row * m.n_az + col];
-                re = fmaf(w2 * wf[j], v.x, re);
-                im = fmaf(w2 * wf[j], v.y, im);
-            }
+            const float2 v = G[(long long)row * m.n_az + col];
+            re = fmaf(w2, v.x, re);
+            im = fmaf(w2, v.y, im);
         }
     }
     return make_float2(re, im);
 }
 
-// Draw M training samples (antenna, az, za, nu) uniformly (nu inside the
-// grid's cubic margin) and their targets from the gridded beams.
+// Draw M training samples (antenna, az, za, nu): beams stratified over the
+// batch, (az, za, nu) uniform (nu inside the grid's cubic margin), and their
+// targets from the gridded beams (Keys cubic in az, za and frequency): four
+// consecutive threads per (sample, component),
+// one per frequency node of the stencil, summed with shuffles; every thread
+// of a sample draws the same values.
 __global__ void k_sample(Model m, const float2* __restrict__ grid, double nu0, double dnu, double nu_lo,
                          double nu_hi, unsigned long long seed, unsigned long long step, int M, int n_out,
                          int* __restrict__ ant, float* __restrict__ az, float* __restrict__ za, float* __restrict__ nu,
                          float* __restrict__ T) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M) return;
+    const int ncomp = m.n_feed * m.n_ax;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int jt = (int)(q & 3);
+    const long long qc = q >> 2;
+    const bool valid = qc < (long long)M * ncomp;
+    const int i = valid ? (int)(qc / ncomp) : 0, c = valid ? (int)(qc % ncomp) : 0;
     const unsigned long long base = (step * (unsigned long long)M + i) * 4ull;
-    const int a = min(m.n_beam - 1, (int)(uniform01(seed, base) * m.n_beam));
+    // beams stratified over the batch: rows [b M / n_beam, (b + 1) M / n_beam)
+    // belong to beam b (each beam equally often, its rows together)
+    const int a = min(m.n_beam - 1, (int)(((long long)i * m.n_beam) / M));
     const double vaz = uniform01(seed, base + 1) * 2.0 * kPi;
     const double vza = uniform01(seed, base + 2) * 0.5 * kPi;
     const double vnu = nu_lo + uniform01(seed, base + 3) * (nu_hi - nu_lo);
-    ant[i] = a;
-    az[i] = (float)vaz;
-    za[i] = (float)vza;
-    nu[i] = (float)vnu;
-    const float u = (float)((vnu - nu0) / dnu);
-    const int ncomp = m.n_feed * m.n_ax;
-    for (int c = 0; c < ncomp && 2 * c < n_out; ++c) {
-        const float2 v = grid_value(m, grid, a, c, (float)vaz, (float)vza, u);
+    float2 v = make_float2(0.f, 0.f);
+    if (valid && 2 * c < n_out) {
+        const float u = (float)((vnu - nu0) / dnu);
+        const float fu = floorf(u), tu = u - fu;
+        const float w = keys_w(tu + 1.f - (float)jt);
+        v = grid_value_node(m, grid, a, c, (float)vaz, (float)vza, (int)fu - 1 + jt);
+        v.x *= w;
+        v.y *= w;
+    }
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+    if (!valid || jt != 0) return;
+    if (c == 0) {
+        ant[i] = a;
+        az[i] = (float)vaz;
+        za[i] = (float)vza;
+        nu[i] = (float)vnu;
+    }
+    if (2 * c < n_out) {
         T[(long long)i * n_out + 2 * c] = v.x;
         T[(long long)i * n_out + 2 * c + 1] = v.y;
     }
@@ -425,109 +417,271 @@ struct Surrogate {
     float* Bf = nullptr;  // Fourier matrix [F][3]
     std::vector<float> hB;
     long long adam_k = 0;
-    // work buffers for up to `cap` rows
+    int n_sms = 148;
+    int* err = nullptr;   // device status word of the tensor-core products
+    // BF16 weight copies for the products (see k_weight_copies)
+    std::vector<bf16*> wt;
+    bf16* wout16 = nullptr;
+    bf16* woutT = nullptr;
+    // k-split partial weight gradients (kMaxSplits per layer) and partial bias
+    // gradients (four rows per SM per layer)
+    float* part = nullptr;
+    float* bpart = nullptr;
+    LayerTab tab{};
+    // work buffers for up to `cap` rows (a multiple of 128)
     long long cap = 0;
     int *ant = nullptr;
     float *az = nullptr, *za = nullptr, *nu = nullptr, *T = nullptr, *Y = nullptr;
-    bf16 *X0 = nullptr, *dX0 = nullptr, *dY = nullptr;
-    std::vector<bf16*> Hs;  // hidden activations (training keeps all layers)
-    bf16 *dZa = nullptr, *dZb = nullptr;
+    bf16 *X0 = nullptr, *X0T = nullptr;      // [cap][d0p], [rows_x0t][cap] (row d0p = 1)
+    std::vector<bf16*> Hs, HT;               // [cap][H], [rows_ht][cap] (row H = 1)
+    bf16 *dY = nullptr, *dYT = nullptr;      // [cap][64], [128][cap] (rows past 16 zero)
+    bf16 *dZa = nullptr, *dZb = nullptr;     // [cap][H]
+    bf16 *dZTa = nullptr, *dZTb = nullptr;   // [rows_dzt][cap]
     double* loss = nullptr;
+    int rows_x0t() const { return std::max(128, d.d0p + 16); }
+    int rows_ht() const { return std::max(128, d.H + 16); }
+    int rows_dzt() const { return std::max(128, d.H); }
 };
 
 namespace {
+
+constexpr int kMaxSplits = 32;
 
 void sfree(void* p) {
     if (p) cudaFree(p);
 }
 
+void free_rows(Surrogate* S) {
+    for (void* q : {(void*)S->ant, (void*)S->az, (void*)S->za, (void*)S->nu, (void*)S->T, (void*)S->Y, (void*)S->X0,
+                    (void*)S->X0T, (void*)S->dY, (void*)S->dYT, (void*)S->dZa, (void*)S->dZb, (void*)S->dZTa,
+                    (void*)S->dZTb})
+        sfree(q);
+    for (auto* h : S->Hs) sfree(h);
+    for (auto* h : S->HT) sfree(h);
+    S->ant = nullptr; S->az = S->za = S->nu = S->T = S->Y = nullptr;
+    S->X0 = S->X0T = S->dY = S->dYT = S->dZa = S->dZb = S->dZTa = S->dZTb = nullptr;
+    S->Hs.assign(S->d.depth, nullptr);
+    S->HT.assign(S->d.depth, nullptr);
+    S->cap = 0;
+}
+
+// Work buffers for `rows` rows: every array zeroed, then the rows of ones
+// of the transposed activations.
 cudaError_t ensure_rows(Surrogate* S, long long rows) {
     if (rows <= S->cap) return cudaSuccess;
-    sfree(S->ant); sfree(S->az); sfree(S->za); sfree(S->nu); sfree(S->T); sfree(S->Y);
-    sfree(S->X0); sfree(S->dX0); sfree(S->dY); sfree(S->dZa); sfree(S->dZb);
-    for (auto* h : S->Hs) sfree(h);
-    S->Hs.assign(S->d.depth, nullptr);
+    free_rows(S);
+    const long long cap = std::max(128ll, (rows + 127) / 128 * 128);
     cudaError_t e = cudaSuccess;
     auto A = [&](void** q, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(q, bytes);
+        if (e == cudaSuccess) e = cudaMemset(*q, 0, bytes);
     };
     const Dims& d = S->d;
-    A((void**)&S->ant, sizeof(int) * rows);
-    A((void**)&S->az, sizeof(float) * rows);
-    A((void**)&S->za, sizeof(float) * rows);
-    A((void**)&S->nu, sizeof(float) * rows);
-    A((void**)&S->T, sizeof(float) * rows * 8);
-    A((void**)&S->Y, sizeof(float) * rows * 8);
-    A((void**)&S->X0, sizeof(bf16) * rows * d.d0p);
-    A((void**)&S->dX0, sizeof(bf16) * rows * d.d0p);
-    A((void**)&S->dY, sizeof(bf16) * rows * 8);
-    A((void**)&S->dZa, sizeof(bf16) * rows * d.H);
-    A((void**)&S->dZb, sizeof(bf16) * rows * d.H);
-    for (int l = 0; l < d.depth; ++l) A((void**)&S->Hs[l], sizeof(bf16) * rows * d.H);
-    if (e == cudaSuccess) S->cap = rows;
+    A((void**)&S->ant, sizeof(int) * cap);
+    A((void**)&S->az, sizeof(float) * cap);
+    A((void**)&S->za, sizeof(float) * cap);
+    A((void**)&S->nu, sizeof(float) * cap);
+    A((void**)&S->T, sizeof(float) * cap * 8);
+    A((void**)&S->Y, sizeof(float) * cap * 8);
+    A((void**)&S->X0, sizeof(bf16) * cap * d.d0p);
+    A((void**)&S->X0T, sizeof(bf16) * cap * S->rows_x0t());
+    A((void**)&S->dY, sizeof(bf16) * cap * 64);
+    A((void**)&S->dYT, sizeof(bf16) * cap * 128);  // rows 16..127 stay zero (a full 128-row A box)
+    A((void**)&S->dZa, sizeof(bf16) * cap * d.H);
+    A((void**)&S->dZb, sizeof(bf16) * cap * d.H);
+    A((void**)&S->dZTa, sizeof(bf16) * cap * S->rows_dzt());
+    A((void**)&S->dZTb, sizeof(bf16) * cap * S->rows_dzt());
+    for (int l = 0; l < d.depth; ++l) {
+        A((void**)&S->Hs[l], sizeof(bf16) * cap * d.H);
+        A((void**)&S->HT[l], sizeof(bf16) * cap * S->rows_ht());
+    }
+    if (e == cudaSuccess) {
+        k_fill_row<<<gridsz(cap, 256), 256>>>(S->X0T + (long long)d.d0p * cap, cap, cap, 1.f);
+        for (int l = 0; l < d.depth; ++l)
+            k_fill_row<<<gridsz(cap, 256), 256>>>(S->HT[l] + (long long)d.H * cap, cap, cap, 1.f);
+        e = cudaDeviceSynchronize();
+    }
+    if (e == cudaSuccess) S->cap = cap;
+    else free_rows(S);
     return e;
 }
 
-// Forward pass of `rows` rows whose features are in X0: hidden layers into
-// Hs[l] (all kept for training) and the FP32 output into Y [rows][8].
-cudaError_t forward(Surrogate* S, int rows, cudaStream_t st, long long* L) {
+GemmOperand opnd(const bf16* p, long long ld, long long rows, long long kext) {
+    GemmOperand o;
+    o.p = p;
+    o.ld = ld;
+    o.rows = (int)rows;
+    o.kext = (int)kext;
+    return o;
+}
+
+// Forward pass of `rows` rows whose features are in X0 (and X0T when
+// training): hidden layers into Hs[l] (and HT[l] when training); then, when
+// training, dL/dy (dY, dYT) and the loss, else the FP32 outputs Y [rows][8].
+cudaError_t forward(Surrogate* S, int rows, bool train, cudaStream_t st, long long* L) {
     const Dims& d = S->d;
     cudaError_t e = cudaSuccess;
     const bf16* in = S->X0;
     int kin = d.d0p;
     for (int l = 0; l < d.depth && e == cudaSuccess; ++l) {
-        e = gemm(true, true, rows, d.H, kin, in, kin, S->pb + S->off_w[l], kin, S->Hs[l], d.H, EPI_BIAS_RELU_BF16,
-                 S->p + S->off_b[l], nullptr, 0, st, L);
+        GemmEpi ep{};
+        ep.kind = GEPI_RELU;
+        ep.out = S->Hs[l];
+        ep.ldo = d.H;
+        ep.outT = train ? S->HT[l] : nullptr;
+        ep.ldt = S->cap;
+        ep.bias = S->p + S->off_b[l];
+        e = launch_gemm_tc(opnd(in, kin, S->cap, kin), opnd(S->pb + S->off_w[l], kin, d.H, kin), rows, d.H, 1, false,
+                           ep, S->n_sms, S->err, st, L);
         in = S->Hs[l];
         kin = d.H;
     }
-    if (e == cudaSuccess)
-        e = gemm(true, true, rows, 8, d.H, in, d.H, S->pb + S->off_w[d.depth], d.H, S->Y, 8, EPI_BIAS_F32,
-                 S->p + S->off_b[d.depth], nullptr, 0, st, L);
+    if (e != cudaSuccess) return e;
+    GemmEpi ep{};
+    ep.bias = S->p + S->off_b[d.depth];
+    ep.n_out = d.n_out;
+    if (train) {
+        ep.kind = GEPI_LOSS;
+        ep.out = S->dY;
+        ep.ldo = 64;
+        ep.outT = S->dYT;
+        ep.ldt = S->cap;
+        ep.target = S->T;
+        ep.gscale = 2.f / (float)((long long)rows * d.n_out);
+        ep.loss = S->loss;
+    } else {
+        ep.kind = GEPI_Y;
+        ep.out = S->Y;
+        ep.ldo = 8;
+    }
+    return launch_gemm_tc(opnd(in, d.H, S->cap, d.H), opnd(S->wout16, d.H, 16, d.H), rows, 16, 1, false, ep,
+                          S->n_sms, S->err, st, L);
+}
+
+// k-splits of a weight-gradient product over `rows` rows: pieces of at least
+// 512 rows, at most kMaxSplits.
+int grad_splits(int rows) {
+    const int kb = (rows + 63) / 64;
+    return std::max(1, std::min(kMaxSplits, (kb + 7) / 8));
+}
+
+// Partial rows of the bias gradients: one per k-split of the weight-gradient
+// products.
+int bias_rows(const Surrogate*, int rows) { return grad_splits(rows); }
+
+// Backward pass for the batch left by forward(train = true): the embedding
+// gradient into S->g, the weight and bias gradients as k-split partials, and
+// with `reduce` those summed into S->g as well (training sums them in its
+// optimiser step instead, k_reduce_adam).
+cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long long* L) {
+    const Dims& d = S->d;
+    const int D = d.depth, H = d.H;
+    const long long cap = S->cap;
+    const long long kpad = (rows + 63) / 64 * 64;  // K extent of the weight-gradient products
+    const int splits = grad_splits(rows);
+    // the embedding gradient accumulates; the rest is written by the reduction
+    cudaError_t e = reduce ? cudaMemsetAsync(S->g, 0, sizeof(float) * (size_t)S->n_par, st)
+                           : cudaMemsetAsync(S->g + S->off_emb, 0, sizeof(float) * (size_t)(S->n_par - S->off_emb), st);
+    // columns [rows, kpad) of the gradients read by those products must be zero
+    if (e == cudaSuccess && kpad > rows) {
+        const size_t w = sizeof(bf16) * (size_t)(kpad - rows), pitch = sizeof(bf16) * (size_t)cap;
+        e = cudaMemset2DAsync(S->dYT + rows, pitch, 0, w, 16, st);
+        if (e == cudaSuccess) e = cudaMemset2DAsync(S->dZTa + rows, pitch, 0, w, S->rows_dzt(), st);
+        if (e == cudaSuccess) e = cudaMemset2DAsync(S->dZTb + rows, pitch, 0, w, S->rows_dzt(), st);
+    }
+    if (e != cudaSuccess) return e;
+    // output layer: dW_out = dY^T H_D and db_out (the row sums of dY^T), then
+    // dZ_D = (dY W_out) * (H_D > 0)
+    {
+        GemmEpi ep{};
+        ep.kind = GEPI_F32;
+        ep.out = S->part + S->tab.part_off[D];
+        ep.ldo = H;
+        ep.part_stride = S->tab.part_stride[D];
+        ep.bias_part = S->bpart + S->tab.bias_off[D];
+        ep.ldo_bias = 16;
+        e = launch_gemm_tc(opnd(S->dYT, cap, 128, kpad), opnd(S->HT[D - 1], cap, S->rows_ht(), kpad), 16, H, splits,
+                           false, ep, S->n_sms, S->err, st, L);
+    }
+    bf16 *dz = S->dZa, *dzT = S->dZTa, *dz2 = S->dZb, *dz2T = S->dZTb;
+    if (e == cudaSuccess) {
+        GemmEpi ep{};
+        ep.kind = GEPI_MASK;
+        ep.out = dz;
+        ep.ldo = H;
+        ep.outT = dzT;
+        ep.ldt = cap;
+        ep.mask = S->Hs[D - 1];
+        ep.ldm = H;
+        e = launch_gemm_tc(opnd(S->dY, 64, cap, 64), opnd(S->woutT, 64, H, 64), rows, H, 1, false, ep, S->n_sms,
+                           S->err, st, L);
+    }
+    for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int kin = l == 0 ? d.d0p : H;
+        const bf16* xT = l == 0 ? S->X0T : S->HT[l - 1];
+        const int xrows = l == 0 ? S->rows_x0t() : S->rows_ht();
+        // dW_l = dZ_l^T X_l and db_l (the row sums of dZ_l^T)
+        {
+            GemmEpi ep{};
+            ep.kind = GEPI_F32;
+            ep.out = S->part + S->tab.part_off[l];
+            ep.ldo = kin;
+            ep.part_stride = S->tab.part_stride[l];
+            ep.bias_part = S->bpart + S->tab.bias_off[l];
+            ep.ldo_bias = H;
+            e = launch_gemm_tc(opnd(dzT, cap, S->rows_dzt(), kpad), opnd(xT, cap, xrows, kpad), H, kin, splits, false,
+                               ep, S->n_sms, S->err, st, L);
+        }
+        if (e != cudaSuccess) break;
+        if (l > 0) {
+            // dZ_{l-1} = (dZ_l W_l) * (H_{l-1} > 0)
+            GemmEpi ep{};
+            ep.kind = GEPI_MASK;
+            ep.out = dz2;
+            ep.ldo = H;
+            ep.outT = dz2T;
+            ep.ldt = cap;
+            ep.mask = S->Hs[l - 1];
+            ep.ldm = H;
+            e = launch_gemm_tc(opnd(dz, H, cap, H), opnd(S->wt[l], H, kin, H), rows, kin, 1, false, ep, S->n_sms,
+                               S->err, st, L);
+            std::swap(dz, dz2);
+            std::swap(dzT, dz2T);
+        } else {
+            // features: only the embedding columns [2F, 2F + E) need a gradient,
+            // added into the embedding of each row's beam
+            GemmEpi ep{};
+            ep.kind = GEPI_EMB;
+            ep.ant = S->ant;
+            ep.gemb = S->g + S->off_emb;
+            ep.emb = d.E;
+            const int erows = (d.E + 15) / 16 * 16;
+            e = launch_gemm_tc(opnd(dz, H, cap, H), opnd(S->wt[0] + (long long)2 * d.F * H, H, erows, H), rows, d.E, 1,
+                               false, ep, S->n_sms, S->err, st, L);
+        }
+    }
+    if (e == cudaSuccess && reduce) {
+        k_reduce_grads<<<dim3(64, D + 1), 256, 0, st>>>(S->tab, S->part, splits, S->bpart, bias_rows(S, rows), S->g);
+        ++*L;
+        e = cudaGetLastError();
+    }
     return e;
 }
 
-// Backward pass for the batch in X0 / Hs / dY: all gradients into S->g.
-cudaError_t backward(Surrogate* S, int rows, cudaStream_t st, long long* L) {
-    const Dims& d = S->d;
-    // weight and embedding gradients accumulate (split over the batch): zero all
-    cudaError_t e = cudaMemsetAsync(S->g, 0, sizeof(float) * (size_t)S->n_par, st);
-    // output layer: dW_out = dY^T H_L, db_out = sum dY, dH_L = (dY W_out) * (H_L > 0)
-    const int D = d.depth;
-    bf16* dz = S->dZa;
-    bf16* dz_next = S->dZb;
-    if (e == cudaSuccess)
-        e = gemm(false, false, 8, d.H, rows, S->dY, 8, S->Hs[D - 1], d.H, S->g + S->off_w[D], d.H, EPI_F32_ADD,
-                 nullptr, nullptr, 0, st, L);
-    if (e == cudaSuccess) {
-        k_colsum<<<gridsz(8, 32), 256, 0, st>>>(rows, 8, S->dY, 8, S->g + S->off_b[D]);
-        ++*L;
-        e = gemm(true, false, rows, d.H, 8, S->dY, 8, S->pb + S->off_w[D], d.H, dz, d.H, EPI_MASK_BF16, nullptr,
-                 S->Hs[D - 1], d.H, st, L);
-    }
-    for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
-        const bf16* in = l == 0 ? S->X0 : S->Hs[l - 1];
-        const int kin = l == 0 ? d.d0p : d.H;
-        // dW_l = dZ^T in, db_l = sum dZ
-        e = gemm(false, false, d.H, kin, rows, dz, d.H, in, kin, S->g + S->off_w[l], kin, EPI_F32_ADD, nullptr, nullptr,
-                 0, st, L);
-        if (e != cudaSuccess) break;
-        k_colsum<<<gridsz(d.H, 32), 256, 0, st>>>(rows, d.H, dz, d.H, S->g + S->off_b[l]);
-        ++*L;
-        if (l > 0) {
-            e = gemm(true, false, rows, d.H, d.H, dz, d.H, S->pb + S->off_w[l], d.H, dz_next, d.H, EPI_MASK_BF16,
-                     nullptr, S->Hs[l - 1], d.H, st, L);
-            std::swap(dz, dz_next);
-        } else {
-            // features: only the embedding columns need a gradient
-            e = gemm(true, false, rows, d.d0p, d.H, dz, d.H, S->pb + S->off_w[0], d.d0p, S->dX0, d.d0p, EPI_BF16,
-                     nullptr, nullptr, 0, st, L);
-        }
-    }
-    if (e == cudaSuccess) {
-        k_emb_grad<<<gridsz((long long)rows * d.E, 256), 256, 0, st>>>(d, rows, S->ant, S->dX0, S->g + S->off_emb);
-        ++*L;
-        e = cudaGetLastError();
+cudaError_t weight_copies(Surrogate* S, cudaStream_t st, long long* L) {
+    k_weight_copies<<<dim3(64, S->d.depth + 1), 256, 0, st>>>(S->tab, S->p, S->d.H, S->wout16, S->woutT);
+    if (L) ++*L;
+    return cudaGetLastError();
+}
+
+cudaError_t check_err(Surrogate* S, cudaStream_t st) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, S->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h != 0) {
+        cudaMemsetAsync(S->err, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        return cudaErrorLaunchTimeout;
     }
     return e;
 }
@@ -540,7 +694,7 @@ Surrogate* surrogate_create(int F, int E, int H, int depth, int n_out, int n_ant
     Dims& d = S->d;
     d.F = F; d.E = E; d.H = H; d.depth = depth; d.n_out = n_out; d.n_ant = n_ant;
     d.d0 = 2 * F + E;
-    d.d0p = (d.d0 + 31) / 32 * 32;
+    d.d0p = std::max(64, (d.d0 + 31) / 32 * 32);  // one 64-column panel at least
     d.nu_mid = (float)nu_mid;
     d.nu_half = (float)nu_half;
     long long o = 0;
@@ -596,10 +750,44 @@ Surrogate* surrogate_create(int F, int E, int H, int depth, int n_out, int n_ant
     if (e == cudaSuccess) e = cudaMemset(S->am, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMemset(S->av, 0, sizeof(float) * o);
     if (e == cudaSuccess) e = cudaMalloc(&S->loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&S->err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(S->err, 0, sizeof(int));
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&S->n_sms, cudaDevAttrMultiProcessorCount, dev);
+    // BF16 weight copies and the layer table of the products
+    S->wt.assign(depth, nullptr);
+    LayerTab& t = S->tab;
+    t.n = depth + 1;
+    long long part = 0;
+    for (int l = 0; l <= depth; ++l) {
+        const bool out = l == depth;
+        const int kin = l == 0 ? d.d0p : H;
+        t.off_w[l] = S->off_w[l];
+        t.off_b[l] = S->off_b[l];
+        t.kin[l] = kin;
+        t.nout[l] = out ? 8 : H;
+        t.part_off[l] = part;
+        t.part_stride[l] = out ? (long long)H * 16 : (long long)H * kin;
+        part += kMaxSplits * t.part_stride[l];
+        t.bias_ld[l] = out ? 16 : H;
+        t.bias_off[l] = (long long)l * kMaxSplits * H;
+        if (!out && e == cudaSuccess) {
+            e = cudaMalloc(&S->wt[l], sizeof(bf16) * (size_t)kin * H);
+            t.wt[l] = S->wt[l];
+        }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&S->part, sizeof(float) * (size_t)part);
+    if (e == cudaSuccess) e = cudaMalloc(&S->bpart, sizeof(float) * (size_t)(depth + 1) * kMaxSplits * H);
+    if (e == cudaSuccess) e = cudaMalloc(&S->wout16, sizeof(bf16) * 16 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMemset(S->wout16, 0, sizeof(bf16) * 16 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMalloc(&S->woutT, sizeof(bf16) * 64 * (size_t)H);
+    if (e == cudaSuccess) e = cudaMemset(S->woutT, 0, sizeof(bf16) * 64 * (size_t)H);
     if (e == cudaSuccess) {
         k_to_bf16<<<gridsz(o, 256), 256>>>(o, S->p, S->pb);
-        e = cudaDeviceSynchronize();
+        e = weight_copies(S, 0, nullptr);
     }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     *err = e;
     if (e != cudaSuccess) {
         surrogate_destroy(S);
@@ -611,11 +799,11 @@ Surrogate* surrogate_create(int F, int E, int H, int depth, int n_out, int n_ant
 void surrogate_destroy(Surrogate* S) {
     if (!S) return;
     cudaDeviceSynchronize();
-    for (void* q : {(void*)S->p, (void*)S->g, (void*)S->am, (void*)S->av, (void*)S->pb, (void*)S->Bf, (void*)S->ant,
-                    (void*)S->az, (void*)S->za, (void*)S->nu, (void*)S->T, (void*)S->Y, (void*)S->X0, (void*)S->dX0,
-                    (void*)S->dY, (void*)S->dZa, (void*)S->dZb, (void*)S->loss})
+    free_rows(S);
+    for (void* q : {(void*)S->p, (void*)S->g, (void*)S->am, (void*)S->av, (void*)S->pb, (void*)S->Bf, (void*)S->loss,
+                    (void*)S->err, (void*)S->part, (void*)S->bpart, (void*)S->wout16, (void*)S->woutT})
         sfree(q);
-    for (auto* h : S->Hs) sfree(h);
+    for (auto* w : S->wt) sfree(w);
     delete S;
 }
 
@@ -641,7 +829,8 @@ cudaError_t surrogate_set_params(Surrogate* S, const float* host) {
     cudaError_t e = cudaMemcpy(S->p, host, sizeof(float) * S->n_par, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_to_bf16<<<gridsz(S->n_par, 256), 256>>>(S->n_par, S->p, S->pb);
-        e = cudaDeviceSynchronize();
+        e = weight_copies(S, 0, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
     }
     S->adam_k = 0;
     if (e == cudaSuccess) e = cudaMemset(S->am, 0, sizeof(float) * S->n_par);
@@ -663,16 +852,12 @@ cudaError_t surrogate_grad(Surrogate* S, int n, const int* ant, const float* az,
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->T, T, sizeof(float) * n * d.n_out, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    k_features<<<gridsz((long long)n * d.d0p, 256), 256, 0, st>>>(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za,
-                                                                    S->nu, S->X0);
-    e = forward(S, n, st, &L);
-    if (e == cudaSuccess) {
-        k_loss<<<gridsz((long long)n * 8, 256), 256, 0, st>>>(n, d.n_out, S->Y, S->T, S->dY, S->loss);
-        e = backward(S, n, st, &L);
-    }
+    e = launch_features(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za, S->nu, S->X0, S->X0T, S->cap, st);
+    if (e == cudaSuccess) e = forward(S, n, true, st, &L);
+    if (e == cudaSuccess) e = backward(S, n, true, st, &L);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grads_host, S->g, sizeof(float) * S->n_par, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss, S->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = check_err(S, st);
     if (e == cudaSuccess) *loss /= (double)n * d.n_out;
     return e;
 }
@@ -688,13 +873,12 @@ cudaError_t surrogate_eval(Surrogate* S, int n, const int* ant, const float* az,
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->za, za, sizeof(float) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->nu, nu, sizeof(float) * n, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    k_features<<<gridsz((long long)n * d.d0p, 256), 256, 0, st>>>(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za,
-                                                                    S->nu, S->X0);
-    e = forward(S, n, st, &L);
+    e = launch_features(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
+    if (e == cudaSuccess) e = forward(S, n, false, st, &L);
     if (e != cudaSuccess) return e;
     std::vector<float> y((size_t)n * 8);
     e = cudaMemcpyAsync(y.data(), S->Y, sizeof(float) * n * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = check_err(S, st);
     for (int i = 0; i < n; ++i)
         for (int o = 0; o < d.n_out; ++o) out_host[(size_t)i * d.n_out + o] = y[(size_t)i * 8 + o];
     return e;
@@ -712,15 +896,13 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
     const double nu_lo = nu0 + 1.0 * dnu, nu_hi = nu0 + (m.n_nu - 3) * dnu * 0.999999;
     for (int it = 0; it < steps && e == cudaSuccess; ++it) {
         if (it == 0 || it == steps - 1) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
-        k_sample<<<gridsz(batch, 128), 128, 0, st>>>(m, grid, nu0, dnu, nu_lo, nu_hi, seed, (unsigned long long)it,
-                                                      batch, d.n_out, S->ant, S->az, S->za, S->nu, S->T);
-        k_features<<<gridsz((long long)batch * d.d0p, 256), 256, 0, st>>>(d, S->Bf, S->p + S->off_emb, batch, S->ant,
-                                                                            S->az, S->za, S->nu, S->X0);
+        k_sample<<<gridsz(4ll * batch * m.n_feed * m.n_ax, 128), 128, 0, st>>>(
+            m, grid, nu0, dnu, nu_lo, nu_hi, seed, (unsigned long long)it, batch, d.n_out, S->ant, S->az, S->za, S->nu,
+            S->T);
+        e = launch_features(d, S->Bf, S->p + S->off_emb, batch, S->ant, S->az, S->za, S->nu, S->X0, S->X0T, S->cap, st);
         *L += 2;
-        e = forward(S, batch, st, L);
+        if (e == cudaSuccess) e = forward(S, batch, true, st, L);
         if (e != cudaSuccess) break;
-        k_loss<<<gridsz((long long)batch * 8, 256), 256, 0, st>>>(batch, d.n_out, S->Y, S->T, S->dY, S->loss);
-        ++*L;
         if (it == 0 || it == steps - 1) {
             double l = 0;
             e = cudaMemcpyAsync(&l, S->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -729,16 +911,26 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
             if (it == 0) *loss_first = l;
             if (it == steps - 1) *loss_last = l;
         }
-        e = backward(S, batch, st, L);
+        e = backward(S, batch, false, st, L);
         if (e != cudaSuccess) break;
-        const float lr = lr1 + 0.5f * (lr0 - lr1) * (1.f + cosf((float)kPi * it / std::max(1, steps - 1)));
+        AdamArgs a;
+        a.lr = lr1 + 0.5f * (lr0 - lr1) * (1.f + cosf((float)kPi * it / std::max(1, steps - 1)));
         S->adam_k += 1;
-        const float c1 = 1.f - powf(0.9f, (float)S->adam_k), c2 = 1.f - powf(0.999f, (float)S->adam_k);
-        k_adam<<<gridsz(S->n_par, 256), 256, 0, st>>>(S->n_par, S->p, S->g, S->am, S->av, S->pb, lr, 0.9f, 0.999f,
-                                                       1e-8f, c1, c2);
+        a.b1 = 0.9f;
+        a.b2 = 0.999f;
+        a.eps = 1e-8f;
+        a.c1 = 1.f - powf(0.9f, (float)S->adam_k);
+        a.c2 = 1.f - powf(0.999f, (float)S->adam_k);
+        const long long n_emb = S->n_par - S->off_emb;
+        const long long max_layer = (long long)std::max(d.d0p, d.H) * (d.H + 1);
+        k_reduce_adam<<<dim3(gridsz(std::max(max_layer, n_emb), 256), d.depth + 2), 256, 0, st>>>(S->tab, S->part, grad_splits(batch), S->bpart,
+                                                              bias_rows(S, batch), S->g, S->off_emb,
+                                                              n_emb, S->p, S->am, S->av, S->pb, d.H, S->wout16,
+                                                              S->woutT, a);
         ++*L;
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = check_err(S, st);
     return e;
 }
 
@@ -751,8 +943,9 @@ cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& 
     const Dims& d = S->d;
     const int ncomp = m.n_feed * m.n_ax;
     const long long chunk = 1 << 19;
-    // the tensor-core forward pass (features, layers and WA in one launch per
-    // instance) where the network shape allows, else the mma.sync GEMMs
+    // the fused tensor-core forward pass (features, layers and WA in one
+    // launch per instance) where the network shape allows, else the network's
+    // layer-by-layer tensor-core products
     const bool tc = mlp_tc_supported(d.F, d.E, d.H, d.depth, d.d0p, d.n_out);
     MlpTcArgs ta{};
     if (tc) {
@@ -773,10 +966,9 @@ cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& 
         for (long long r0 = 0; !tc && r0 < rows && e == cudaSuccess; r0 += chunk) {
             const int R = (int)std::min(chunk, rows - r0);
             k_rows<<<gridsz(R, 256), 256, 0, st>>>(d.n_ant, K, r0, R, in.t, nu, lt, S->ant, S->az, S->za, S->nu);
-            k_features<<<gridsz((long long)R * d.d0p, 256), 256, 0, st>>>(d, S->Bf, S->p + S->off_emb, R, S->ant,
-                                                                            S->az, S->za, S->nu, S->X0);
+            e = launch_features(d, S->Bf, S->p + S->off_emb, R, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
             *L += 2;
-            e = forward(S, R, st, L);
+            if (e == cudaSuccess) e = forward(S, R, false, st, L);
             if (e != cudaSuccess) break;
             k_wa_rows<<<gridsz(R, 256), 256, 0, st>>>(m, K, r0, R, in.t, lnr, lt, S->Y, ncomp, wslot, wa_pitch,
                                                        amax + j);

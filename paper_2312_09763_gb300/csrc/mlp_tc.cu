@@ -184,7 +184,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                 for (int l = 0; l < D && ok; ++l)
                     for (int pnl = 0; pnl < panels(l); ++pnl, ++it) {
                         const int sl = it % NSLOT;
-                        if (!wait_bounded(wfree(sl), ((uint32_t)(it / NSLOT) & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
+                        if (!wait_bounded_spin(wfree(sl), ((uint32_t)(it / NSLOT) & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
                         mbar_expect_tx(wfull(sl), (uint32_t)w_panel);
                         tma_load_2d(w_base + sl * W_PANEL_MAX, &maps.w[l], pnl * KP, 0, wfull(sl));
                     }
@@ -194,17 +194,17 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             const uint32_t id_hidden = idesc_f16(false, TM, H), id_out = idesc_f16(false, TM, 16);
             int it = 0;
             int na = 0;
-            bool ok = wait_bounded(ofull, 0u, abort_flag, err);
+            bool ok = wait_bounded_spin(ofull, 0u, abort_flag, err);
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 for (int l = 0; l <= D && ok; ++l) {
-                    if (!wait_bounded(afull, (uint32_t)(na++) & 1u, abort_flag, err)) { ok = false; break; }
+                    if (!wait_bounded_spin(afull, (uint32_t)(na++) & 1u, abort_flag, err)) { ok = false; break; }
                     tc_fence_after();
                     const bool out = l == D;
                     const int np = out ? H / KP : panels(l);
                     for (int pnl = 0; pnl < np; ++pnl) {
                         const int sl = it % NSLOT;
                         if (!out) {
-                            if (!wait_bounded(wfull(sl), (uint32_t)(it / NSLOT) & 1u, abort_flag, err)) { ok = false; break; }
+                            if (!wait_bounded_spin(wfull(sl), (uint32_t)(it / NSLOT) & 1u, abort_flag, err)) { ok = false; break; }
                             tc_fence_after();
                         }
                         const uint32_t b0 = out ? o_base + pnl * O_PANEL : w_base + sl * W_PANEL_MAX;
@@ -305,7 +305,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             const int src = wa_row ? lt.idx[(long long)t * lt.pitch + s] : 0;
             // ---- hidden layers: accumulator -> bias, ReLU -> BF16 activations
             for (int l = 0; l < D; ++l) {
-                if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
+                if (!wait_bounded_spin(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
                 if (l == 0 && wa_row) {  // the source index has landed by now
                     cp_async<4>(smem_u32(&g_alpha[row]), m.half_alpha + src);
@@ -344,7 +344,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             if (!ok) break;
             // ---- output layer: accumulator -> registers, then the next tile's
             // features (the accumulator columns are free again), then WA
-            if (!wait_bounded(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
+            if (!wait_bounded_spin(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
             tc_fence_after();
             float y[8];
             if (h == 0) {

@@ -59,16 +59,35 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parit
     return ok != 0;
 }
 __device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                             unsigned long long limit_ns = kTimeoutNs) {
+                                             unsigned long long limit_ns = kTimeoutNs, uint32_t hint_ns = 20000u) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (;;) {
-        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (mbar_try_wait_sleep(bar, parity, hint_ns)) return true;
         if (*abort_flag) return false;
         if (gtimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicCAS(err, 0, (int)kDevTimeout);
             return false;
+        }
+    }
+}
+// Bounded wait without the suspend-time hint: try_wait in a loop, the clock
+// read every 64 tries.  For short kernels whose waits end within a few
+// microseconds (the hinted wait above can oversleep by up to its hint there).
+__device__ __forceinline__ bool wait_bounded_spin(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                                  unsigned long long limit_ns = kTimeoutNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (unsigned n = 1;; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((n & 63u) == 0u) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > limit_ns) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, (int)kDevTimeout);
+                return false;
+            }
         }
     }
 }
