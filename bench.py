@@ -78,8 +78,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="scaling sweep instead of the benchmark line: time per instance over sources 2^10..2^19 "
                          "x antennas 2^3..2^8 (one LST x 16 channels each), one JSON line per point")
-    ap.add_argument("--train-steps", type=int, default=1221,
-                    help="learned workload: Adam steps of 8192 samples (default 1221, i.e. 1e7 samples)")
+    ap.add_argument("--train-steps", type=int, default=611,
+                    help="learned workload: Adam steps (default 611 of 16384 samples, i.e. 1e7 samples)")
+    ap.add_argument("--train-batch", type=int, default=16384, help="learned workload: samples per Adam step")
     ap.add_argument("--no-fuse", action="store_true", help="Z build as its own launch (mv_options.fuse_zbuild = 0)")
     ap.add_argument("--herk-config", default=None, metavar="BN,SPLIT,FLUSH",
                     help="fix the tensor-core HERK tile width, split-K and flush interval (skips autotune)")
@@ -338,21 +339,37 @@ def main():
         # no host round trip of the 5.5 GB of per-antenna grids each step, and
         # no CPU baseline over 350 per-antenna beams: device-side numbers only
         args.no_e2e = args.no_cpu_baseline = True
-        # the surrogate of the 350 gridded beams: by default 1221 Adam steps of 8192 samples (1e7 samples)
+        # the surrogate of the 350 gridded beams: by default 611 Adam steps of 16384 samples (1e7 samples)
         sim.surrogate_create()
+        p_init = sim.surrogate_params()[0].copy()
+        # untimed: the work buffers and first launches, then back to the initial weights (and a fresh Adam)
+        sim.surrogate_train(steps=3, batch=args.train_batch, lr0=1e-6, lr1=1e-6, seed=99)
+        sim.surrogate_set_params(p_init)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        l0, l1 = sim.surrogate_train(steps=args.train_steps, batch=8192, lr0=2e-3, lr1=1e-5, seed=1)
+        l0, l1 = sim.surrogate_train(steps=args.train_steps, batch=args.train_batch, lr0=2e-3, lr1=1e-5, seed=1)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        # the gridded path's V on this sample, for the surrogate's modelling error
+        # the gridded path's V on this sample (the surrogate's modelling error) and
+        # its time per instance, against the surrogate's below
         tuning = None if args.precision == "fp32" or args.no_autotune else sim.autotune(w.lsts, w.freqs, args.precision)
         args.no_autotune = True
         Vg = sim.simulate(w.lsts, w.freqs, args.precision)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(2):
+            sim.simulate(w.lsts, w.freqs, args.precision, out=Vg)
+        g1.record()
+        torch.cuda.synchronize()
+        grid_ms = g0.elapsed_time(g1) / 2
+        grid_bytes, sur_bytes = sim.beam_model_bytes()
         sim.set_beam_surrogate(True)
-        learned = {"train_samples": args.train_steps * 8192, "train_s": t_train,
-                   "train_samples_per_s": args.train_steps * 8192 / t_train,
-                   "loss_first": l0, "loss_last": l1}
+        n_samp = args.train_steps * args.train_batch
+        learned = {"train_samples": n_samp, "train_batch": args.train_batch, "train_s": t_train,
+                   "train_samples_per_s": n_samp / t_train, "loss_first": l0, "loss_last": l1,
+                   "grid_ms_per_instance": grid_ms / n_instances(w, pairs),
+                   "grid_beam_bytes": grid_bytes, "surrogate_beam_bytes": sur_bytes}
     N = w.n_ant
     nf, nax = sim.n_feed, sim._n_ax()
     shape = (len(w.lsts), N * nf, N * nf) if pairs else (len(w.lsts), len(w.freqs), N * nf, N * nf)
@@ -491,7 +508,8 @@ def main():
         mlp_tf = 2.0 * macs * rows_step * args.steps / (ms_b / 1e3) / 1e12
         err = float((V - Vg).abs().max() / Vg.abs().max())
         learned.update({"network_rows_per_step": rows_step, "flop_per_row": 2 * macs,
-                        "surrogate_vs_grid_rel_err": err})
+                        "surrogate_vs_grid_rel_err": err,
+                        "surrogate_ms_per_instance": ms_max / args.steps / n_instances(w, pairs)})
         roof = {"bound": "tensor", "achieved": mlp_tf, "peak": sustained, "unit": "TFLOP/s",
                 "frac": mlp_tf / sustained,
                 "traffic": MLP_DRAM_BYTES_PER_LAUNCH, "traffic_unit": "B per launch",

@@ -401,6 +401,14 @@ mv_status mv_surrogate_load(mv_ctx *ctx, const char *path);
  * uses embedding beam_idx[a]) instead of interpolating the grid. */
 mv_status mv_set_beam_surrogate(mv_ctx *ctx, int enable);
 
+/* Device memory of the two beam models (the cost Sec. 3.1 names for
+ * per-antenna beams): *grid_bytes, the gridded beams as held (all unique
+ * beams' grids plus the per-channel planes of the last call; 0 without a
+ * gridded beam); *surrogate_bytes, what evaluating the surrogate reads (FP32
+ * parameters, their BF16 copy, the Fourier matrix; 0 without a surrogate).
+ * Either pointer may be NULL. */
+mv_status mv_beam_model_bytes(mv_ctx *ctx, int64_t *grid_bytes, int64_t *surrogate_bytes);
+
 /* enable != 0 switches timing on and clears the counters; 0 switches it off. */
 mv_status mv_profile_enable(mv_ctx *ctx, int enable);
 

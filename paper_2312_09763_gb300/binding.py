@@ -30,7 +30,8 @@ EXPORTS = ["mv_default_options", "mv_create", "mv_destroy", "mv_last_error", "mv
            "mv_default_mlp_config", "mv_surrogate_create", "mv_surrogate_train", "mv_surrogate_params",
            "mv_surrogate_set_params", "mv_surrogate_eval", "mv_surrogate_grad", "mv_surrogate_save",
            "mv_surrogate_load", "mv_set_beam_surrogate", "mv_set_sky_polarisation", "mv_redundancy_plan",
-           "mv_set_redundancy", "mv_simulate_unique", "mv_selftest_wait_timeout", "mv_perturb_sky"]
+           "mv_set_redundancy", "mv_simulate_unique", "mv_selftest_wait_timeout", "mv_perturb_sky",
+           "mv_beam_model_bytes"]
 KERNEL_KINDS = {"cull": 0, "beam": 1, "zbuild": 2, "herk": 3}
 
 
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mv_surrogate_save.argtypes = [vp, ctypes.c_char_p]
     lib.mv_surrogate_load.argtypes = [vp, ctypes.c_char_p]
     lib.mv_set_beam_surrogate.argtypes = [vp, i32]
+    lib.mv_beam_model_bytes.argtypes = [vp, vp, vp]
     lib.mv_redundancy_plan.argtypes = [i32, vp, vp, dp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mv_redundancy_plan.restype = i32
     lib.mv_perturb_sky.argtypes = [i64, vp, vp, dp, dp, vp, vp]
@@ -428,6 +430,12 @@ class Simulator:
 
     def set_beam_surrogate(self, enable: bool = True):
         self._check(self._lib.mv_set_beam_surrogate(self._h, 1 if enable else 0))
+
+    def beam_model_bytes(self):
+        """(device bytes of the gridded beams as held, device bytes the surrogate's evaluation reads)."""
+        g, m = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._lib.mv_beam_model_bytes(self._h, ctypes.byref(g), ctypes.byref(m)))
+        return g.value, m.value
 
     def _n_ax(self) -> int:
         return getattr(self, "n_ax", 1)

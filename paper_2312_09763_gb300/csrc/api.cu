@@ -1746,4 +1746,12 @@ mv_status mv_set_beam_surrogate(mv_ctx* c, int enable) {
     return MV_OK;
 }
 
+mv_status mv_beam_model_bytes(mv_ctx* c, int64_t* grid_bytes, int64_t* surrogate_bytes) {
+    g_err.clear();
+    if (!c) return fail(MV_ERR_ARG, "ctx is NULL");
+    if (grid_bytes) *grid_bytes = c->model.beam_kind == 2 ? (int64_t)(c->grid.bytes + c->planes.bytes) : 0;
+    if (surrogate_bytes) *surrogate_bytes = c->sur ? surrogate_eval_bytes(c->sur) : 0;
+    return MV_OK;
+}
+
 }  // extern "C"

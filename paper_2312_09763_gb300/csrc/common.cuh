@@ -215,6 +215,9 @@ Surrogate* surrogate_create(int F, int E, int H, int depth, int n_out, int n_ant
                             unsigned long long seed, double nu_mid, double nu_half, cudaError_t* err);
 void surrogate_destroy(Surrogate* S);
 long long surrogate_param_count(const Surrogate* S);
+// Device bytes the surrogate's evaluation reads: FP32 parameters (biases,
+// embedding), their BF16 copy (weights) and the Fourier matrix.
+long long surrogate_eval_bytes(const Surrogate* S);
 int surrogate_fourier(const Surrogate* S, float* out);
 void surrogate_layout(const Surrogate* S, long long* off_w, long long* off_b, long long* off_emb, int* d0p);
 cudaError_t surrogate_get_params(const Surrogate* S, float* host);

@@ -808,6 +808,9 @@ void surrogate_destroy(Surrogate* S) {
 }
 
 long long surrogate_param_count(const Surrogate* S) { return S->n_par; }
+long long surrogate_eval_bytes(const Surrogate* S) {
+    return S->n_par * (long long)(sizeof(float) + sizeof(bf16)) + (long long)S->hB.size() * (long long)sizeof(float);
+}
 int surrogate_fourier(const Surrogate* S, float* out) {
     std::memcpy(out, S->hB.data(), sizeof(float) * S->hB.size());
     return (int)S->hB.size();

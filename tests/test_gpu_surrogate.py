@@ -11,13 +11,16 @@ rounds its inputs to 8 significant bits, relative 2^-9):
                    per-antenna Jones grids: RMS |A_net - A_grid| <= 0.06 RMS |A_grid|
                    (measured 0.026-0.044) and visibilities within 0.08 of the
                    gridded path's (measured 0.033-0.035)
+  gain             on 350 per-antenna Jones grids the network holds >= 500x less
+                   device memory than the grids; the gridded path stays within
+                   1e-5 of the oracle and the network within 0.08
 """
 import numpy as np
 import pytest
 
 import oracle
 from oracle import mlp
-from helpers import flat_grads, oracle_net, oracle_problem, rel_err, simulator
+from helpers import flat_grads, oracle_net, oracle_problem, rel_err, sample_pairs, simulator
 from paper_2312_09763_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -175,3 +178,50 @@ def test_surrogate_several_tiles_per_sm(polarised):
         return out
     Vo = oracle.vis_with_beam_fn(P, w.lsts[0], f, beam_fn)
     assert rel_err(V[0, 1], Vo) <= 3e-2
+
+
+def test_what_the_surrogate_gains_over_per_antenna_grids():
+    # Sec. 3.1: with a beam per antenna the interpolation step holds and reads
+    # one grid per antenna.  On 350 per-antenna Jones beams (1 deg x 1 deg x
+    # 1 MHz, 9 frequency nodes) the trained network stands in for all of them:
+    # measured here are the device bytes each beam model holds, the time per
+    # instance of each path, and each path's visibility error against the FP64
+    # oracle (which interpolates the grids).
+    import time
+    import torch
+    w = synth.learned_beam(n_ant=350, n_src=6000, n_chan=2, n_times=1, nu_lo=146e6, nu_hi=154e6)
+    w.freqs = np.array([149.5e6, 150.5e6])
+    sim = simulator(w)
+    sim.surrogate_create()
+    sim.surrogate_train(steps=2000, batch=16384, lr0=2e-3, lr1=1e-5, seed=11)
+    V = {}
+    ms = {}
+    for path in ("grid", "surrogate"):
+        sim.set_beam_surrogate(path == "surrogate")
+        out = sim.simulate(w.lsts, w.freqs, "fp16x3")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            sim.simulate(w.lsts, w.freqs, "fp16x3", out=out)
+        torch.cuda.synchronize()
+        ms[path] = (time.perf_counter() - t0) / 3 / len(w.freqs) * 1e3
+        V[path] = out.cpu().numpy()
+    grid_bytes, sur_bytes = sim.beam_model_bytes()
+    # memory: the gridded beams (350 x 2 x 2 x 9 x 91 x 360 complex64 plus the
+    # per-channel planes, ~1.8 GB) against the network's ~1.5 MB
+    assert grid_bytes >= 1.5e9 and sur_bytes <= 3e6
+    assert grid_bytes >= 500 * sur_bytes
+    # accuracy against the oracle's interpolation of the grids on sampled baselines
+    P = oracle_problem(w)
+    pa, pb = sample_pairs(w.n_ant, 150, seed=3)
+    err = {}
+    for ic, nu in enumerate(w.freqs):
+        vo = oracle.vis(P, w.lsts[0], nu, pairs=(pa, pb))
+        for path in V:
+            vv = V[path][0, ic].reshape(w.n_ant, 2, w.n_ant, 2)[pa, :, pb, :]
+            err[path] = max(err.get(path, 0.0), rel_err(vv, vo))
+    assert err["grid"] <= 1e-5
+    assert err["surrogate"] <= 0.08
+    print(f"beam model bytes: grid {grid_bytes:.3e}, surrogate {sur_bytes:.3e} ({grid_bytes / sur_bytes:.0f}x); "
+          f"ms per instance: grid {ms['grid']:.3f}, surrogate {ms['surrogate']:.3f}; "
+          f"max rel err vs oracle: grid {err['grid']:.2e}, surrogate {err['surrogate']:.3f}")
