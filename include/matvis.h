@@ -182,7 +182,11 @@ mv_status mv_set_beam_gaussian(mv_ctx *ctx, double fwhm_rad);
  * (periodic; n_az even).  n_feed, n_ax in {1, 2}; n_ax = 2 means the columns
  * are (theta, phi) E-field components, which change sign across the pole.
  * Interpolation per mv_options.interp.  Rows past the last za node repeat the
- * last row.  Host pointer; copied. */
+ * last row.  Host pointer; copied.
+ * The grid's first za row is always the zenith (no za0 argument): Sec. 2.4
+ * needs the zenith treated as the grid's pole, and the pole reflection (a
+ * stencil row at za < 0 is row -za at az + pi) is only defined when row 0 sits
+ * on it. */
 mv_status mv_set_beam_grid(mv_ctx *ctx, int n_beam, int n_feed, int n_ax, int n_nu, int n_za,
                            int n_az, const float *values_c64, double nu0, double dnu,
                            double dza, double daz);
@@ -203,7 +207,12 @@ mv_status mv_set_antennas(mv_ctx *ctx, int n_ant, const double *enu, const int32
 mv_status mv_simulate(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const double *nu,
                       mv_precision prec, void *V, int V_on_device, void *stream);
 
-/* Simulate an explicit list of (lst, nu) pairs: V complex64 [n_pairs][N][N]. */
+/* Simulate an explicit list of (lst, nu) pairs: V complex64 [n_pairs][N][N].
+ * Every (time, frequency) instance of Algorithm 2 is independent (Sec. 3.1:
+ * frequency is the outer loop and times the inner one, with no interaction
+ * between them), so an arbitrary list of instances is as valid a call as the
+ * n_t x n_nu grid of mv_simulate; lst[i], nu[i] as there.  Arguments, output
+ * placement, stream and errors as mv_simulate. */
 mv_status mv_simulate_pairs(mv_ctx *ctx, int n_pairs, const double *lst, const double *nu,
                             mv_precision prec, void *V, int V_on_device, void *stream);
 
@@ -222,7 +231,9 @@ mv_status mv_autotune(mv_ctx *ctx, int n_t, const double *lst, int n_nu, const d
                       mv_precision prec, int pairs, mv_tuning *out);
 
 /* Synchronise the context's work and report (and clear) a device-side error
- * flag (MV_ERR_DEVICE_TIMEOUT) or a pending CUDA error. */
+ * flag (MV_ERR_DEVICE_TIMEOUT) or a pending CUDA error.  The paper has no
+ * counterpart (its GPU steps are synchronous library calls); here every
+ * bounded wait of the tensor-core kernels reports through this flag. */
 mv_status mv_check_device_status(mv_ctx *ctx, void *stream);
 
 /* Self-test of the failure path: launches one thread that waits, with the
@@ -338,7 +349,11 @@ mv_status mv_horizon_cull_static(int64_t n_src, const double *xeq_dev, double ls
                                  int32_t *n_live_dev, void *stream);
 
 /* ---------------------------------------------------------------------
- * Learned beam.  The paper interpolates gridded beams (Sec. 2.4) and notes
+ * Learned beam.  (The calls are named mv_surrogate_*: create, train, params,
+ * set_params, eval, grad, save, load; training reports its first and last
+ * loss through mv_surrogate_train's arguments rather than a report struct, and
+ * mv_mlp_config is the network's configuration.)  The paper interpolates
+ * gridded beams (Sec. 2.4) and notes
  * that per-antenna beams make that step expensive (Sec. 3.1); here a
  * Fourier-feature MLP stands in for a set of gridded beams:
  *   x = (az / 2 pi, za / (pi/2), (nu - nu_mid) / nu_half), nu_mid and nu_half
