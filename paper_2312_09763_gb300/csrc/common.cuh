@@ -254,12 +254,15 @@ cudaError_t launch_mlp_wa_tc(const MlpTcArgs& a, const Model& m, LiveTables lt, 
                              int n_sms, cudaStream_t st, long long* launches);
 
 // ------------------------------------- tensor-core products (mlp_train_tc.cu)
-// A K-major BF16 operand: rows x kext used of a [rows][ld] array (ld and the
-// base 16-byte aligned; columns past kext read as zero).
+// A BF16 operand of rows (M or N) x kext (K).  K-major (mn = 0): a
+// [rows][ld] array, K contiguous.  MN-major (mn = 1): a [kext][ld] array, the
+// rows dimension contiguous (the transpose, read without a transposed copy).
+// ld and the base 16-byte aligned; entries past kext (or rows) read as zero.
 struct GemmOperand {
     const __nv_bfloat16* p;
     long long ld;
     int rows, kext;
+    int mn;
 };
 // Fused epilogue of D = A B^T (see mlp_train_tc.cu).
 enum GemmEpiKind : int { GEPI_RELU = 0, GEPI_LOSS = 1, GEPI_MASK = 2, GEPI_F32 = 3, GEPI_EMB = 4, GEPI_Y = 5 };

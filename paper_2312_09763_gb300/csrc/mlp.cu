@@ -12,12 +12,10 @@
 //   h_l = relu(W_l h_{l-1} + b_l), y = W_out h_L + b_out;  MSE loss; Adam.
 // Every matrix product of a training step runs on the tcgen05 tensor cores
 // (mlp_train_tc.cu: BF16 operands staged by TMA, FP32 accumulation in TMEM,
-// fused epilogues); master weights and Adam state are FP32.  The backward
-// products read transposed copies: the forward epilogues write each layer's
-// activations also as columns (with a row of ones appended, so that the
-// weight-gradient product yields the bias gradient as one more column), the
-// gradient epilogues do the same for dL/dz, and the optimiser keeps BF16
-// copies of W and W^T.
+// fused epilogues); master weights and Adam state are FP32.  The weight
+// gradients dW = dZ^T X read dZ and X batch-major (MN-major operands) and get
+// the bias gradients as row sums of dZ^T from an extra MMA; the input
+// gradients read BF16 copies of W^T that the optimiser keeps.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,11 +39,11 @@ struct Dims {
 };
 
 // Fourier features + embedding: X0[m][0..d0p) in BF16 (zero padding), and
-// with X0T the same values as columns, X0T[j][m] (ld ldt).  A block of 256
-// threads takes 64 rows: each (row, frequency) pair evaluates its sine and
-// cosine once into a shared-memory tile, which is then written out as rows
-// and, with X0T, as columns (both coalesced).  Dynamic shared memory:
-// 64 (d0p + 2) BF16 values.
+// with X0T (may be NULL) the same values as columns, X0T[j][m] (ld ldt).  A
+// block of 256 threads takes 64 rows: each (row, frequency) pair evaluates
+// its sine and cosine once into a shared-memory tile, which is then written
+// out as rows (and columns), coalesced.  Dynamic shared memory: 64 (d0p + 2)
+// BF16 values.
 constexpr int kFeatRows = 64;
 __global__ void __launch_bounds__(256)
 k_features(Dims d, const float* __restrict__ Bf, const float* __restrict__ emb, int M, const int* __restrict__ ant,
@@ -239,14 +237,6 @@ __global__ void k_reduce_adam(LayerTab t, const float* __restrict__ part, int sp
     }
 }
 
-// Row r of a [rows][ld] BF16 array set to one (the bias row of the
-// transposed activations).
-__global__ void k_fill_row(bf16* __restrict__ a, long long ld, long long n, float v) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = __float2bfloat16(v);
-    (void)ld;
-}
-
 // ----------------------------------------------------- training samples
 // splitmix64 (Steele, Lea and Flood 2014): a counter-based stream of 64-bit
 // values; uniform doubles take its top 53 bits.
@@ -432,15 +422,11 @@ struct Surrogate {
     long long cap = 0;
     int *ant = nullptr;
     float *az = nullptr, *za = nullptr, *nu = nullptr, *T = nullptr, *Y = nullptr;
-    bf16 *X0 = nullptr, *X0T = nullptr;      // [cap][d0p], [rows_x0t][cap] (row d0p = 1)
-    std::vector<bf16*> Hs, HT;               // [cap][H], [rows_ht][cap] (row H = 1)
-    bf16 *dY = nullptr, *dYT = nullptr;      // [cap][64], [128][cap] (rows past 16 zero)
+    bf16* X0 = nullptr;                      // [cap][d0p]
+    std::vector<bf16*> Hs;                   // [cap][H]
+    bf16* dY = nullptr;                      // [cap][64] (columns past 16 zero)
     bf16 *dZa = nullptr, *dZb = nullptr;     // [cap][H]
-    bf16 *dZTa = nullptr, *dZTb = nullptr;   // [rows_dzt][cap]
     double* loss = nullptr;
-    int rows_x0t() const { return std::max(128, d.d0p + 16); }
-    int rows_ht() const { return std::max(128, d.H + 16); }
-    int rows_dzt() const { return std::max(128, d.H); }
 };
 
 namespace {
@@ -453,20 +439,16 @@ void sfree(void* p) {
 
 void free_rows(Surrogate* S) {
     for (void* q : {(void*)S->ant, (void*)S->az, (void*)S->za, (void*)S->nu, (void*)S->T, (void*)S->Y, (void*)S->X0,
-                    (void*)S->X0T, (void*)S->dY, (void*)S->dYT, (void*)S->dZa, (void*)S->dZb, (void*)S->dZTa,
-                    (void*)S->dZTb})
+                    (void*)S->dY, (void*)S->dZa, (void*)S->dZb})
         sfree(q);
     for (auto* h : S->Hs) sfree(h);
-    for (auto* h : S->HT) sfree(h);
     S->ant = nullptr; S->az = S->za = S->nu = S->T = S->Y = nullptr;
-    S->X0 = S->X0T = S->dY = S->dYT = S->dZa = S->dZb = S->dZTa = S->dZTb = nullptr;
+    S->X0 = S->dY = S->dZa = S->dZb = nullptr;
     S->Hs.assign(S->d.depth, nullptr);
-    S->HT.assign(S->d.depth, nullptr);
     S->cap = 0;
 }
 
-// Work buffers for `rows` rows: every array zeroed, then the rows of ones
-// of the transposed activations.
+// Work buffers for `rows` rows (every array zeroed).
 cudaError_t ensure_rows(Surrogate* S, long long rows) {
     if (rows <= S->cap) return cudaSuccess;
     free_rows(S);
@@ -484,40 +466,28 @@ cudaError_t ensure_rows(Surrogate* S, long long rows) {
     A((void**)&S->T, sizeof(float) * cap * 8);
     A((void**)&S->Y, sizeof(float) * cap * 8);
     A((void**)&S->X0, sizeof(bf16) * cap * d.d0p);
-    A((void**)&S->X0T, sizeof(bf16) * cap * S->rows_x0t());
     A((void**)&S->dY, sizeof(bf16) * cap * 64);
-    A((void**)&S->dYT, sizeof(bf16) * cap * 128);  // rows 16..127 stay zero (a full 128-row A box)
     A((void**)&S->dZa, sizeof(bf16) * cap * d.H);
     A((void**)&S->dZb, sizeof(bf16) * cap * d.H);
-    A((void**)&S->dZTa, sizeof(bf16) * cap * S->rows_dzt());
-    A((void**)&S->dZTb, sizeof(bf16) * cap * S->rows_dzt());
-    for (int l = 0; l < d.depth; ++l) {
-        A((void**)&S->Hs[l], sizeof(bf16) * cap * d.H);
-        A((void**)&S->HT[l], sizeof(bf16) * cap * S->rows_ht());
-    }
-    if (e == cudaSuccess) {
-        k_fill_row<<<gridsz(cap, 256), 256>>>(S->X0T + (long long)d.d0p * cap, cap, cap, 1.f);
-        for (int l = 0; l < d.depth; ++l)
-            k_fill_row<<<gridsz(cap, 256), 256>>>(S->HT[l] + (long long)d.H * cap, cap, cap, 1.f);
-        e = cudaDeviceSynchronize();
-    }
+    for (int l = 0; l < d.depth; ++l) A((void**)&S->Hs[l], sizeof(bf16) * cap * d.H);
     if (e == cudaSuccess) S->cap = cap;
     else free_rows(S);
     return e;
 }
 
-GemmOperand opnd(const bf16* p, long long ld, long long rows, long long kext) {
+GemmOperand opnd(const bf16* p, long long ld, long long rows, long long kext, int mn = 0) {
     GemmOperand o;
     o.p = p;
     o.ld = ld;
     o.rows = (int)rows;
     o.kext = (int)kext;
+    o.mn = mn;
     return o;
 }
 
-// Forward pass of `rows` rows whose features are in X0 (and X0T when
-// training): hidden layers into Hs[l] (and HT[l] when training); then, when
-// training, dL/dy (dY, dYT) and the loss, else the FP32 outputs Y [rows][8].
+// Forward pass of `rows` rows whose features are in X0: hidden layers into
+// Hs[l]; then, when training, dL/dy (dY) and the loss, else the FP32 outputs
+// Y [rows][8].
 cudaError_t forward(Surrogate* S, int rows, bool train, cudaStream_t st, long long* L) {
     const Dims& d = S->d;
     cudaError_t e = cudaSuccess;
@@ -528,8 +498,6 @@ cudaError_t forward(Surrogate* S, int rows, bool train, cudaStream_t st, long lo
         ep.kind = GEPI_RELU;
         ep.out = S->Hs[l];
         ep.ldo = d.H;
-        ep.outT = train ? S->HT[l] : nullptr;
-        ep.ldt = S->cap;
         ep.bias = S->p + S->off_b[l];
         e = launch_gemm_tc(opnd(in, kin, S->cap, kin), opnd(S->pb + S->off_w[l], kin, d.H, kin), rows, d.H, 1, false,
                            ep, S->n_sms, S->err, st, L);
@@ -544,8 +512,6 @@ cudaError_t forward(Surrogate* S, int rows, bool train, cudaStream_t st, long lo
         ep.kind = GEPI_LOSS;
         ep.out = S->dY;
         ep.ldo = 64;
-        ep.outT = S->dYT;
-        ep.ldt = S->cap;
         ep.target = S->T;
         ep.gscale = 2.f / (float)((long long)rows * d.n_out);
         ep.loss = S->loss;
@@ -577,21 +543,28 @@ cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long 
     const Dims& d = S->d;
     const int D = d.depth, H = d.H;
     const long long cap = S->cap;
-    const long long kpad = (rows + 63) / 64 * 64;  // K extent of the weight-gradient products
+    // K extent of the weight-gradient products (the batch; TMA reads rows past
+    // it as zeros), at least one 64-row box
+    const long long kext = std::max(rows, 64);
     const int splits = grad_splits(rows);
     // the embedding gradient accumulates; the rest is written by the reduction
     cudaError_t e = reduce ? cudaMemsetAsync(S->g, 0, sizeof(float) * (size_t)S->n_par, st)
                            : cudaMemsetAsync(S->g + S->off_emb, 0, sizeof(float) * (size_t)(S->n_par - S->off_emb), st);
-    // columns [rows, kpad) of the gradients read by those products must be zero
-    if (e == cudaSuccess && kpad > rows) {
-        const size_t w = sizeof(bf16) * (size_t)(kpad - rows), pitch = sizeof(bf16) * (size_t)cap;
-        e = cudaMemset2DAsync(S->dYT + rows, pitch, 0, w, 16, st);
-        if (e == cudaSuccess) e = cudaMemset2DAsync(S->dZTa + rows, pitch, 0, w, S->rows_dzt(), st);
-        if (e == cudaSuccess) e = cudaMemset2DAsync(S->dZTb + rows, pitch, 0, w, S->rows_dzt(), st);
+    if (e == cudaSuccess && kext > rows) {
+        // a batch below 64 rows: the rows [rows, 64) the box reads must be zero in every operand
+        auto zero = [&](bf16* a, int width) {
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(a + (long long)rows * width, 0, sizeof(bf16) * (size_t)(kext - rows) * width, st);
+        };
+        zero(S->X0, d.d0p);
+        for (int l = 0; l < D; ++l) zero(S->Hs[l], H);
+        zero(S->dY, 64);
+        zero(S->dZa, H);
+        zero(S->dZb, H);
     }
     if (e != cudaSuccess) return e;
-    // output layer: dW_out = dY^T H_D and db_out (the row sums of dY^T), then
-    // dZ_D = (dY W_out) * (H_D > 0)
+    // output layer: dW_out = dY^T H_D and db_out (the row sums of dY^T), both
+    // operands read batch-major; then dZ_D = (dY W_out) * (H_D > 0)
     {
         GemmEpi ep{};
         ep.kind = GEPI_F32;
@@ -600,17 +573,15 @@ cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long 
         ep.part_stride = S->tab.part_stride[D];
         ep.bias_part = S->bpart + S->tab.bias_off[D];
         ep.ldo_bias = 16;
-        e = launch_gemm_tc(opnd(S->dYT, cap, 128, kpad), opnd(S->HT[D - 1], cap, S->rows_ht(), kpad), 16, H, splits,
-                           false, ep, S->n_sms, S->err, st, L);
+        e = launch_gemm_tc(opnd(S->dY, 64, 64, kext, 1), opnd(S->Hs[D - 1], H, H, kext, 1), 16, H, splits, false, ep,
+                           S->n_sms, S->err, st, L);
     }
-    bf16 *dz = S->dZa, *dzT = S->dZTa, *dz2 = S->dZb, *dz2T = S->dZTb;
+    bf16 *dz = S->dZa, *dz2 = S->dZb;
     if (e == cudaSuccess) {
         GemmEpi ep{};
         ep.kind = GEPI_MASK;
         ep.out = dz;
         ep.ldo = H;
-        ep.outT = dzT;
-        ep.ldt = cap;
         ep.mask = S->Hs[D - 1];
         ep.ldm = H;
         e = launch_gemm_tc(opnd(S->dY, 64, cap, 64), opnd(S->woutT, 64, H, 64), rows, H, 1, false, ep, S->n_sms,
@@ -618,9 +589,8 @@ cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long 
     }
     for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
         const int kin = l == 0 ? d.d0p : H;
-        const bf16* xT = l == 0 ? S->X0T : S->HT[l - 1];
-        const int xrows = l == 0 ? S->rows_x0t() : S->rows_ht();
-        // dW_l = dZ_l^T X_l and db_l (the row sums of dZ_l^T)
+        const bf16* x = l == 0 ? S->X0 : S->Hs[l - 1];
+        // dW_l = dZ_l^T X_l and db_l (the row sums of dZ_l^T), both read batch-major
         {
             GemmEpi ep{};
             ep.kind = GEPI_F32;
@@ -629,8 +599,8 @@ cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long 
             ep.part_stride = S->tab.part_stride[l];
             ep.bias_part = S->bpart + S->tab.bias_off[l];
             ep.ldo_bias = H;
-            e = launch_gemm_tc(opnd(dzT, cap, S->rows_dzt(), kpad), opnd(xT, cap, xrows, kpad), H, kin, splits, false,
-                               ep, S->n_sms, S->err, st, L);
+            e = launch_gemm_tc(opnd(dz, H, H, kext, 1), opnd(x, kin, kin, kext, 1), H, kin, splits, false, ep, S->n_sms,
+                               S->err, st, L);
         }
         if (e != cudaSuccess) break;
         if (l > 0) {
@@ -639,14 +609,11 @@ cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long 
             ep.kind = GEPI_MASK;
             ep.out = dz2;
             ep.ldo = H;
-            ep.outT = dz2T;
-            ep.ldt = cap;
             ep.mask = S->Hs[l - 1];
             ep.ldm = H;
             e = launch_gemm_tc(opnd(dz, H, cap, H), opnd(S->wt[l], H, kin, H), rows, kin, 1, false, ep, S->n_sms,
                                S->err, st, L);
             std::swap(dz, dz2);
-            std::swap(dzT, dz2T);
         } else {
             // features: only the embedding columns [2F, 2F + E) need a gradient,
             // added into the embedding of each row's beam
@@ -855,7 +822,7 @@ cudaError_t surrogate_grad(Surrogate* S, int n, const int* ant, const float* az,
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->T, T, sizeof(float) * n * d.n_out, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    e = launch_features(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za, S->nu, S->X0, S->X0T, S->cap, st);
+    e = launch_features(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
     if (e == cudaSuccess) e = forward(S, n, true, st, &L);
     if (e == cudaSuccess) e = backward(S, n, true, st, &L);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grads_host, S->g, sizeof(float) * S->n_par, cudaMemcpyDeviceToHost, st);
@@ -902,7 +869,7 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
         k_sample<<<gridsz(4ll * batch * m.n_feed * m.n_ax, 128), 128, 0, st>>>(
             m, grid, nu0, dnu, nu_lo, nu_hi, seed, (unsigned long long)it, batch, d.n_out, S->ant, S->az, S->za, S->nu,
             S->T);
-        e = launch_features(d, S->Bf, S->p + S->off_emb, batch, S->ant, S->az, S->za, S->nu, S->X0, S->X0T, S->cap, st);
+        e = launch_features(d, S->Bf, S->p + S->off_emb, batch, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
         *L += 2;
         if (e == cudaSuccess) e = forward(S, batch, true, st, L);
         if (e != cudaSuccess) break;

@@ -3,13 +3,17 @@
 //
 // Every product of the network's forward and backward pass is written as
 //     D[M][N] = A[M][K] B[N][K]^T
-// with both operands K-major BF16 in global memory (the backward products
-// read transposed copies of the activations, gradients and weights that the
-// producing epilogues and the optimiser write, so that no product needs an
-// MN-major operand).  One persistent CTA per SM walks units (row tile,
-// up-to-256-column tile, k-split) in a fixed order; warp 0 streams 64-column
-// K panels of A and B (up to 256 rows) with TMA (128-byte swizzle) through a
-// ring of stages, warp 1 owns TMEM and issues tcgen05.mma (M = 128, N = the
+// with BF16 operands in global memory, K-major ([rows][K]: the forward and
+// input-gradient products, with the weights and their transposed copies
+// that the optimiser writes) or MN-major ([K][rows]: the weight gradients
+// dW = dZ^T X read dZ and X as the batch-major arrays the other products
+// write, with no transposed copies).  In shared memory a K-major operand is
+// one 64-column, 128-byte-swizzled box per 64 K; an MN-major one is 64-element
+// MN boxes of 64 K rows (8 KB each, 128-byte swizzle), the MMA descriptor
+// stepping 8 KB between MN boxes and 1 KB between groups of 8 K rows.  One
+// persistent CTA per SM walks units (row tile, up-to-256-column tile,
+// k-split) in a fixed order; warp 0 streams 64-K panels of A and B (up to
+// 256 rows) with TMA through a ring of stages, warp 1 owns TMEM and issues tcgen05.mma (M = 128, N = the
 // tile's width, K = 16; FP32 accumulation), and warps 2-17 (four per TMEM
 // lane quadrant, one output row per thread) drain the accumulators through
 // the fused epilogue of the product:
@@ -67,8 +71,16 @@ struct Job {
     int bnb;                // B rows per tile (the B tensor map's box)
     int stages, stage_bytes;
     int ones;               // row sums of A in TMEM columns [256, 272) (single accumulator)
+    int a_mn, b_mn;         // operand layouts (1: MN-major)
     GemmEpi e;
 };
+
+// Shared-memory descriptor of an MN-major operand: 64-element MN boxes of 64 K
+// rows (8 KB apart), 128-byte swizzle, groups of 8 K rows 1 KB apart.
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
 
 __device__ __forceinline__ void st_global_v4(void* p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
     asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -154,7 +166,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
     const uint32_t tmem = *tmem_slot;
     const uint32_t sbase = smem_u32(smem);
     const int n_units = j.m_tiles * j.n_tiles * j.splits;
-    const uint32_t tx_bytes = (uint32_t)(MT * A_BYTES + j.bnb * BK * 2);
+    const int b_boxes = (j.bnb + 63) / 64;  // MN-major B: 64-element boxes (the last may read past N as zeros)
+    const uint32_t tx_bytes = (uint32_t)(MT * A_BYTES + (j.b_mn ? b_boxes * 8192 : j.bnb * BK * 2));
     // one accumulator set per unit with two 128-row MMAs or the row sums;
     // else two sets in turn
     const bool single = MT == 2 || j.ones;
@@ -172,8 +185,20 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
                     if (!wait_bounded_spin(empty(s), ((uint32_t)(it / S) & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
                     mbar_expect_tx(full(s), tx_bytes);
                     const uint32_t st = sbase + s * SB;
-                    for (int t = 0; t < MT; ++t) tma_load_2d(st + t * A_BYTES, &map_a, kb * BK, p.m0 + t * TM, full(s));
-                    tma_load_2d(st + MT * A_BYTES, &map_b, kb * BK, p.n0, full(s));
+                    for (int t = 0; t < MT; ++t) {
+                        if (j.a_mn) {  // two 64-row MN boxes per 128-row tile
+                            tma_load_2d(st + t * A_BYTES, &map_a, p.m0 + t * TM, kb * BK, full(s));
+                            tma_load_2d(st + t * A_BYTES + A_BYTES / 2, &map_a, p.m0 + t * TM + 64, kb * BK, full(s));
+                        } else {
+                            tma_load_2d(st + t * A_BYTES, &map_a, kb * BK, p.m0 + t * TM, full(s));
+                        }
+                    }
+                    if (j.b_mn) {
+                        for (int b = 0; b < b_boxes; ++b)
+                            tma_load_2d(st + MT * A_BYTES + b * 8192, &map_b, p.n0 + 64 * b, kb * BK, full(s));
+                    } else {
+                        tma_load_2d(st + MT * A_BYTES, &map_b, kb * BK, p.n0, full(s));
+                    }
                 }
             }
         }
@@ -186,25 +211,33 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
                 const int buf = buf_of(cnt);
                 if (!wait_bounded_spin(tempty(buf), phase_of(cnt) ^ 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t id = idesc_f16(false, TM, p.ncols);
+                // operand majors: bit 15 (A), bit 16 (B) set for MN-major
+                const uint32_t id = idesc_f16(false, TM, p.ncols) | ((uint32_t)j.a_mn << 15) | ((uint32_t)j.b_mn << 16);
+                const uint32_t id_ones = idesc_f16(false, TM, 16) | ((uint32_t)j.a_mn << 15);
                 for (int kb = p.kb0; kb < p.kb1; ++kb, ++it) {
                     const int s = it % S;
                     if (!wait_bounded_spin(full(s), (uint32_t)(it / S) & 1u, abort_flag, err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t st = sbase + s * SB;
+                    // K step kk: 32 bytes into every K-major row, or 16 K rows (2 KB) of
+                    // every MN-major box
+                    auto adesc = [&](int t, int kk) {
+                        const uint32_t a = st + t * A_BYTES;
+                        return j.a_mn ? sdesc_mn(a + kk * 2048) : sdesc(a + kk * 32);
+                    };
+                    const uint32_t b = st + MT * A_BYTES;
                     for (int t = 0; t < MT; ++t) {
                         const uint32_t d = tmem + (uint32_t)((MT == 2 ? t : buf) * 256);
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
-                            tc_mma(d, sdesc(st + t * A_BYTES + kk * 32), sdesc(st + MT * A_BYTES + kk * 32), id,
+                            tc_mma(d, adesc(t, kk), j.b_mn ? sdesc_mn(b + kk * 2048) : sdesc(b + kk * 32), id,
                                    (kb > p.kb0 || kk > 0) ? 1u : 0u);
                     }
                     if (j.ones) {
-                        // row sums of A: A times the all-ones tile, N = 16
+                        // row sums of A: A times the all-ones tile (K-major), N = 16
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk)
-                            tc_mma(tmem + 256u, sdesc(st + kk * 32), sdesc(sbase + RING), idesc_f16(false, TM, 16),
-                                   (kb > p.kb0 || kk > 0) ? 1u : 0u);
+                            tc_mma(tmem + 256u, adesc(0, kk), sdesc(sbase + RING), id_ones, (kb > p.kb0 || kk > 0) ? 1u : 0u);
                     }
                     tc_commit(empty(s));
                 }
@@ -320,8 +353,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
                         st_global_v4(o, pack2(g[0], g[1]), pack2(g[2], g[3]), pack2(g[4], g[5]), pack2(g[6], g[7]));
                         st_global_v4(o + 8, pack2(g[8], g[9]), pack2(g[10], g[11]), pack2(g[12], g[13]),
                                      pack2(g[14], g[15]));
+                        if (e.outT) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) e.outT[(long long)i * e.ldt + m] = __float2bfloat16(g[i]);
+                            for (int i = 0; i < 16; ++i) e.outT[(long long)i * e.ldt + m] = __float2bfloat16(g[i]);
+                        }
                     }
                 } else if constexpr (KIND == GEPI_F32 || KIND == GEPI_Y) {
                     if (valid) {
@@ -388,9 +423,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUt
 bool make_map(CUtensorMap* map, const GemmOperand& o, int box_rows) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)o.kext, (cuuint64_t)o.rows};
+    // K-major: (K, rows) with boxes of 64 K x box_rows rows; MN-major: (rows,
+    // K) with boxes of 64 rows x 64 K
+    cuuint64_t dims[2] = {(cuuint64_t)(o.mn ? o.rows : o.kext), (cuuint64_t)(o.mn ? o.kext : o.rows)};
     cuuint64_t strides[1] = {(cuuint64_t)o.ld * 2};
-    cuuint32_t box[2] = {BK, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {BK, (cuuint32_t)(o.mn ? BK : box_rows)};
     cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(o.p), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -422,12 +459,19 @@ cudaError_t launch_gemm_tc(const GemmOperand& A, const GemmOperand& B, int M, in
     // operand shapes the TMA boxes need: K extents of one panel or more, A at
     // least one 128-row box, B at least as many rows as its box; 16-byte rows.
     // Row sums of A (bias_part) ride on weight-gradient products (F32, 128-row units).
-    if (A.kext < BK || B.kext < BK || A.kext != B.kext || A.rows < TM || A.ld % 8 || B.ld % 8 || A.ld < A.kext ||
-        B.ld < B.kext || ((uintptr_t)A.p & 15) || ((uintptr_t)B.p & 15) ||
-        (e.bias_part && (e.kind != GEPI_F32 || two_row_tiles)))
-        return cudaErrorInvalidValue;
+    // K-major: A at least one 128-row box, B at least as many rows as its box,
+    // K at least one 64-column panel.  MN-major: rows and K at least one 64 box
+    // each (a 128-row A tile reads two MN boxes, the second may lie past the
+    // rows and reads zeros), B's last box likewise.
     const int bnb = std::min(BMAX, (N + 15) / 16 * 16);
-    if (B.rows < bnb) return cudaErrorInvalidValue;
+    auto bad = [&](const GemmOperand& o, bool is_a) {
+        if (o.kext < BK || o.ld % 8 || ((uintptr_t)o.p & 15)) return true;
+        if (o.mn) return o.rows < BK || o.ld < o.rows;
+        return o.ld < o.kext || (is_a ? o.rows < TM : o.rows < bnb);
+    };
+    if (bad(A, true) || bad(B, false) || A.kext != B.kext || (B.mn && two_row_tiles) ||
+        (A.mn && two_row_tiles) || (e.bias_part && (e.kind != GEPI_F32 || two_row_tiles)))
+        return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, TM) || !make_map(&mb, B, bnb)) return cudaErrorInvalidValue;
     Job j{};
@@ -442,6 +486,8 @@ cudaError_t launch_gemm_tc(const GemmOperand& A, const GemmOperand& B, int M, in
     j.kblocks = (A.kext + BK - 1) / BK;
     j.splits = std::max(1, std::min(splits, j.kblocks));
     j.ones = e.bias_part != nullptr;
+    j.a_mn = A.mn;
+    j.b_mn = B.mn;
     j.e = e;
     const int grid = gemm_tc_grid(M, N, splits, two_row_tiles, A.kext, n_sms);
     switch (e.kind) {
