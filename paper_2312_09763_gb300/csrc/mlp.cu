@@ -422,6 +422,12 @@ struct Surrogate {
     long long cap = 0;
     int *ant = nullptr;
     float *az = nullptr, *za = nullptr, *nu = nullptr, *T = nullptr, *Y = nullptr;
+    // a second set of training samples: the sampler of step i + 1 runs on a
+    // side stream while step i trains on the other set
+    int* ant2 = nullptr;
+    float *az2 = nullptr, *za2 = nullptr, *nu2 = nullptr, *T2 = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     bf16* X0 = nullptr;                      // [cap][d0p]
     std::vector<bf16*> Hs;                   // [cap][H]
     bf16* dY = nullptr;                      // [cap][64] (columns past 16 zero)
@@ -431,7 +437,7 @@ struct Surrogate {
 
 namespace {
 
-constexpr int kMaxSplits = 32;
+constexpr int kMaxSplits = 64;
 
 void sfree(void* p) {
     if (p) cudaFree(p);
@@ -439,10 +445,12 @@ void sfree(void* p) {
 
 void free_rows(Surrogate* S) {
     for (void* q : {(void*)S->ant, (void*)S->az, (void*)S->za, (void*)S->nu, (void*)S->T, (void*)S->Y, (void*)S->X0,
-                    (void*)S->dY, (void*)S->dZa, (void*)S->dZb})
+                    (void*)S->dY, (void*)S->dZa, (void*)S->dZb, (void*)S->ant2, (void*)S->az2, (void*)S->za2,
+                    (void*)S->nu2, (void*)S->T2})
         sfree(q);
     for (auto* h : S->Hs) sfree(h);
-    S->ant = nullptr; S->az = S->za = S->nu = S->T = S->Y = nullptr;
+    S->ant = S->ant2 = nullptr;
+    S->az = S->za = S->nu = S->T = S->Y = S->az2 = S->za2 = S->nu2 = S->T2 = nullptr;
     S->X0 = S->dY = S->dZa = S->dZb = nullptr;
     S->Hs.assign(S->d.depth, nullptr);
     S->cap = 0;
@@ -465,6 +473,11 @@ cudaError_t ensure_rows(Surrogate* S, long long rows) {
     A((void**)&S->nu, sizeof(float) * cap);
     A((void**)&S->T, sizeof(float) * cap * 8);
     A((void**)&S->Y, sizeof(float) * cap * 8);
+    A((void**)&S->ant2, sizeof(int) * cap);
+    A((void**)&S->az2, sizeof(float) * cap);
+    A((void**)&S->za2, sizeof(float) * cap);
+    A((void**)&S->nu2, sizeof(float) * cap);
+    A((void**)&S->T2, sizeof(float) * cap * 8);
     A((void**)&S->X0, sizeof(bf16) * cap * d.d0p);
     A((void**)&S->dY, sizeof(bf16) * cap * 64);
     A((void**)&S->dZa, sizeof(bf16) * cap * d.H);
@@ -767,6 +780,11 @@ void surrogate_destroy(Surrogate* S) {
     if (!S) return;
     cudaDeviceSynchronize();
     free_rows(S);
+    if (S->side) cudaStreamDestroy(S->side);
+    for (int i = 0; i < 2; ++i) {
+        if (S->ev_ready[i]) cudaEventDestroy(S->ev_ready[i]);
+        if (S->ev_free[i]) cudaEventDestroy(S->ev_free[i]);
+    }
     for (void* q : {(void*)S->p, (void*)S->g, (void*)S->am, (void*)S->av, (void*)S->pb, (void*)S->Bf, (void*)S->loss,
                     (void*)S->err, (void*)S->part, (void*)S->bpart, (void*)S->wout16, (void*)S->woutT})
         sfree(q);
@@ -864,13 +882,52 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
     if (e != cudaSuccess) return e;
     const Dims& d = S->d;
     const double nu_lo = nu0 + 1.0 * dnu, nu_hi = nu0 + (m.n_nu - 3) * dnu * 0.999999;
+    if (!S->side) {
+        e = cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&S->ev_ready[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_free[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    // sample sets: set 0 the arrays forward / backward read, set 1 the second
+    // one; the pointers swap every step
+    int* s_ant[2] = {S->ant, S->ant2};
+    float* s_az[2] = {S->az, S->az2};
+    float* s_za[2] = {S->za, S->za2};
+    float* s_nu[2] = {S->nu, S->nu2};
+    float* s_T[2] = {S->T, S->T2};
+    auto sample = [&](int it) {  // on the side stream, into set it & 1, once the set is free
+        const int k = it & 1;
+        cudaError_t x = cudaSuccess;
+        if (it >= 2) x = cudaStreamWaitEvent(S->side, S->ev_free[k], 0);
+        if (x == cudaSuccess) {
+            k_sample<<<gridsz(4ll * batch * m.n_feed * m.n_ax, 128), 128, 0, S->side>>>(
+                m, grid, nu0, dnu, nu_lo, nu_hi, seed, (unsigned long long)it, batch, d.n_out, s_ant[k], s_az[k],
+                s_za[k], s_nu[k], s_T[k]);
+            ++*L;
+            x = cudaGetLastError();
+        }
+        if (x == cudaSuccess) x = cudaEventRecord(S->ev_ready[k], S->side);
+        return x;
+    };
+    // the side stream starts after the work already queued on st
+    e = cudaEventRecord(S->ev_free[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S->side, S->ev_free[0], 0);
+    if (e == cudaSuccess) e = sample(0);
     for (int it = 0; it < steps && e == cudaSuccess; ++it) {
+        const int k = it & 1;
+        if (it + 1 < steps && (e = sample(it + 1)) != cudaSuccess) break;
+        S->ant = s_ant[k];
+        S->az = s_az[k];
+        S->za = s_za[k];
+        S->nu = s_nu[k];
+        S->T = s_T[k];
         if (it == 0 || it == steps - 1) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
-        k_sample<<<gridsz(4ll * batch * m.n_feed * m.n_ax, 128), 128, 0, st>>>(
-            m, grid, nu0, dnu, nu_lo, nu_hi, seed, (unsigned long long)it, batch, d.n_out, S->ant, S->az, S->za, S->nu,
-            S->T);
-        e = launch_features(d, S->Bf, S->p + S->off_emb, batch, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
-        *L += 2;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, S->ev_ready[k], 0);
+        if (e == cudaSuccess)
+            e = launch_features(d, S->Bf, S->p + S->off_emb, batch, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
+        *L += 1;
         if (e == cudaSuccess) e = forward(S, batch, true, st, L);
         if (e != cudaSuccess) break;
         if (it == 0 || it == steps - 1) {
@@ -882,6 +939,7 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
             if (it == steps - 1) *loss_last = l;
         }
         e = backward(S, batch, false, st, L);
+        if (e == cudaSuccess) e = cudaEventRecord(S->ev_free[k], st);  // set k read for the last time
         if (e != cudaSuccess) break;
         AdamArgs a;
         a.lr = lr1 + 0.5f * (lr0 - lr1) * (1.f + cosf((float)kPi * it / std::max(1, steps - 1)));
@@ -900,6 +958,18 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
         ++*L;
         e = cudaGetLastError();
     }
+    // the arrays back in their places (set 0 first), whatever step ended last
+    S->ant = s_ant[0];
+    S->az = s_az[0];
+    S->za = s_za[0];
+    S->nu = s_nu[0];
+    S->T = s_T[0];
+    S->ant2 = s_ant[1];
+    S->az2 = s_az[1];
+    S->za2 = s_za[1];
+    S->nu2 = s_nu[1];
+    S->T2 = s_T[1];
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->side);
     if (e == cudaSuccess) e = check_err(S, st);
     return e;
 }
