@@ -1096,7 +1096,8 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
     mv_ctx* c = new mv_ctx();
     c->device = device;
     c->n_sms = pr.multiProcessorCount;
-    if (herk_tc_init() != cudaSuccess || mlp_tc_init() != cudaSuccess || gemm_tc_init() != cudaSuccess) {
+    if (herk_tc_init() != cudaSuccess || mlp_tc_init() != cudaSuccess || gemm_tc_init() != cudaSuccess ||
+        mlp_chain_init() != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return fail(MV_ERR_CUDA, "kernel attribute set-up failed");

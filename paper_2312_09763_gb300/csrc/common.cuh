@@ -253,6 +253,41 @@ cudaError_t launch_mlp_wa_tc(const MlpTcArgs& a, const Model& m, LiveTables lt, 
                              float ln_ratio, float2* wa_slot, long long wa_pitch, float* amax, int* d_err,
                              int n_sms, cudaStream_t st, long long* launches);
 
+// ------------------------------ fused training pass (mlp_chain_tc.cu)
+// One training batch of the surrogate through every row-local step in one
+// launch: features, the hidden layers, the output layer with the loss and
+// dL/dy, the input gradients back through the layers with the ReLU masks,
+// and the embedding gradient.  The weight gradients (products over the batch)
+// are left to the tensor-core products below, which read what this pass
+// stores: X0, every H_l, dY and every dZ_l, batch-major.
+constexpr int kChainMaxLayers = 5;  // deeper networks run product by product
+struct ChainArgs {
+    int F, E, H, depth, d0p, n_out;
+    float nu_mid, nu_half;
+    int M;                                       // rows of the batch
+    const float* p;                              // FP32 parameters (biases, embedding)
+    long long off_b[kChainMaxLayers + 1];        // hidden layers, then the output layer
+    long long off_emb;
+    const float* Bf;                             // Fourier matrix [F][3]
+    const __nv_bfloat16* w[kChainMaxLayers];     // W_l [H][kin_l] (BF16)
+    const __nv_bfloat16* wout16;                 // W_out [16][H], rows past n_out zero
+    const __nv_bfloat16* woutT;                  // W_out^T [H][64], columns past n_out zero
+    const __nv_bfloat16* wt[kChainMaxLayers];    // W_l^T [kin_l][H]
+    const int* ant;                              // samples: beam, az, za, nu, targets [M][n_out]
+    const float *az, *za, *nu, *T;
+    __nv_bfloat16* X0;                           // [M][d0p]
+    __nv_bfloat16* Hs[kChainMaxLayers];          // [M][H]
+    __nv_bfloat16* dY;                           // [M][64]: columns [0, 16) written
+    __nv_bfloat16* dZs[kChainMaxLayers];         // [M][H]
+    float gscale;                                // dL/dy = gscale (y - target)
+    double* loss;                                // sum of squared residuals (atomic)
+    float* gemb;                                 // [n_beam][E] embedding gradient (atomic)
+};
+// Whether the fused pass handles this network shape and batch.
+bool mlp_chain_supported(int F, int E, int H, int depth, int d0p, int n_out, int M);
+cudaError_t mlp_chain_init();
+cudaError_t launch_mlp_chain_tc(const ChainArgs& a, int n_sms, int* d_err, cudaStream_t st, long long* launches);
+
 // ------------------------------------- tensor-core products (mlp_train_tc.cu)
 // A BF16 operand of rows (M or N) x kext (K).  K-major (mn = 0): a
 // [rows][ld] array, K contiguous.  MN-major (mn = 1): a [kext][ld] array, the

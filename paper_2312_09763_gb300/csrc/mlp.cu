@@ -431,7 +431,7 @@ struct Surrogate {
     bf16* X0 = nullptr;                      // [cap][d0p]
     std::vector<bf16*> Hs;                   // [cap][H]
     bf16* dY = nullptr;                      // [cap][64] (columns past 16 zero)
-    bf16 *dZa = nullptr, *dZb = nullptr;     // [cap][H]
+    std::vector<bf16*> dZs;                  // [cap][H]: dL/dz of every hidden layer
     double* loss = nullptr;
 };
 
@@ -445,14 +445,15 @@ void sfree(void* p) {
 
 void free_rows(Surrogate* S) {
     for (void* q : {(void*)S->ant, (void*)S->az, (void*)S->za, (void*)S->nu, (void*)S->T, (void*)S->Y, (void*)S->X0,
-                    (void*)S->dY, (void*)S->dZa, (void*)S->dZb, (void*)S->ant2, (void*)S->az2, (void*)S->za2,
-                    (void*)S->nu2, (void*)S->T2})
+                    (void*)S->dY, (void*)S->ant2, (void*)S->az2, (void*)S->za2, (void*)S->nu2, (void*)S->T2})
         sfree(q);
     for (auto* h : S->Hs) sfree(h);
+    for (auto* h : S->dZs) sfree(h);
     S->ant = S->ant2 = nullptr;
     S->az = S->za = S->nu = S->T = S->Y = S->az2 = S->za2 = S->nu2 = S->T2 = nullptr;
-    S->X0 = S->dY = S->dZa = S->dZb = nullptr;
+    S->X0 = S->dY = nullptr;
     S->Hs.assign(S->d.depth, nullptr);
+    S->dZs.assign(S->d.depth, nullptr);
     S->cap = 0;
 }
 
@@ -480,9 +481,8 @@ cudaError_t ensure_rows(Surrogate* S, long long rows) {
     A((void**)&S->T2, sizeof(float) * cap * 8);
     A((void**)&S->X0, sizeof(bf16) * cap * d.d0p);
     A((void**)&S->dY, sizeof(bf16) * cap * 64);
-    A((void**)&S->dZa, sizeof(bf16) * cap * d.H);
-    A((void**)&S->dZb, sizeof(bf16) * cap * d.H);
     for (int l = 0; l < d.depth; ++l) A((void**)&S->Hs[l], sizeof(bf16) * cap * d.H);
+    for (int l = 0; l < d.depth; ++l) A((void**)&S->dZs[l], sizeof(bf16) * cap * d.H);
     if (e == cudaSuccess) S->cap = cap;
     else free_rows(S);
     return e;
@@ -548,36 +548,62 @@ int grad_splits(int rows) {
 // products.
 int bias_rows(const Surrogate*, int rows) { return grad_splits(rows); }
 
-// Backward pass for the batch left by forward(train = true): the embedding
-// gradient into S->g, the weight and bias gradients as k-split partials, and
-// with `reduce` those summed into S->g as well (training sums them in its
-// optimiser step instead, k_reduce_adam).
-cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long long* L) {
+// Input gradients for the batch left by forward(train = true), product by
+// product: dz_{D-1} = (dY W_out) * (h_{D-1} > 0), dz_{l-1} = (dz_l W_l) *
+// (h_{l-1} > 0) into dZs, and the embedding gradient (added into S->g).
+cudaError_t input_grads(Surrogate* S, int rows, cudaStream_t st, long long* L) {
     const Dims& d = S->d;
     const int D = d.depth, H = d.H;
     const long long cap = S->cap;
-    // K extent of the weight-gradient products (the batch; TMA reads rows past
-    // it as zeros), at least one 64-row box
+    cudaError_t e = cudaSuccess;
+    {
+        GemmEpi ep{};
+        ep.kind = GEPI_MASK;
+        ep.out = S->dZs[D - 1];
+        ep.ldo = H;
+        ep.mask = S->Hs[D - 1];
+        ep.ldm = H;
+        e = launch_gemm_tc(opnd(S->dY, 64, cap, 64), opnd(S->woutT, 64, H, 64), rows, H, 1, false, ep, S->n_sms,
+                           S->err, st, L);
+    }
+    for (int l = D - 1; l >= 1 && e == cudaSuccess; --l) {
+        GemmEpi ep{};
+        ep.kind = GEPI_MASK;
+        ep.out = S->dZs[l - 1];
+        ep.ldo = H;
+        ep.mask = S->Hs[l - 1];
+        ep.ldm = H;
+        e = launch_gemm_tc(opnd(S->dZs[l], H, cap, H), opnd(S->wt[l], H, H, H), rows, H, 1, false, ep, S->n_sms,
+                           S->err, st, L);
+    }
+    if (e == cudaSuccess) {
+        // features: only the embedding columns [2F, 2F + E) need a gradient,
+        // added into the embedding of each row's beam
+        GemmEpi ep{};
+        ep.kind = GEPI_EMB;
+        ep.ant = S->ant;
+        ep.gemb = S->g + S->off_emb;
+        ep.emb = d.E;
+        const int erows = (d.E + 15) / 16 * 16;
+        e = launch_gemm_tc(opnd(S->dZs[0], H, cap, H), opnd(S->wt[0] + (long long)2 * d.F * H, H, erows, H), rows, d.E,
+                           1, false, ep, S->n_sms, S->err, st, L);
+    }
+    return e;
+}
+
+// Weight and bias gradients of the batch as k-split partials, from dY, dZs
+// and the layer inputs (X0, Hs), all read batch-major: dW_out = dY^T h_{D-1},
+// dW_l = dz_l^T x_l, the bias gradients as the row sums of dY^T and dz_l^T;
+// with `reduce` the partials are summed into S->g (training sums them in its
+// optimiser step instead, k_reduce_adam).
+cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, cudaStream_t st, long long* L) {
+    const Dims& d = S->d;
+    const int D = d.depth, H = d.H;
+    // K extent of the products (the batch; TMA reads rows past it as zeros), at
+    // least one 64-row box
     const long long kext = std::max(rows, 64);
     const int splits = grad_splits(rows);
-    // the embedding gradient accumulates; the rest is written by the reduction
-    cudaError_t e = reduce ? cudaMemsetAsync(S->g, 0, sizeof(float) * (size_t)S->n_par, st)
-                           : cudaMemsetAsync(S->g + S->off_emb, 0, sizeof(float) * (size_t)(S->n_par - S->off_emb), st);
-    if (e == cudaSuccess && kext > rows) {
-        // a batch below 64 rows: the rows [rows, 64) the box reads must be zero in every operand
-        auto zero = [&](bf16* a, int width) {
-            if (e == cudaSuccess)
-                e = cudaMemsetAsync(a + (long long)rows * width, 0, sizeof(bf16) * (size_t)(kext - rows) * width, st);
-        };
-        zero(S->X0, d.d0p);
-        for (int l = 0; l < D; ++l) zero(S->Hs[l], H);
-        zero(S->dY, 64);
-        zero(S->dZa, H);
-        zero(S->dZb, H);
-    }
-    if (e != cudaSuccess) return e;
-    // output layer: dW_out = dY^T H_D and db_out (the row sums of dY^T), both
-    // operands read batch-major; then dZ_D = (dY W_out) * (H_D > 0)
+    cudaError_t e = cudaSuccess;
     {
         GemmEpi ep{};
         ep.kind = GEPI_F32;
@@ -589,62 +615,84 @@ cudaError_t backward(Surrogate* S, int rows, bool reduce, cudaStream_t st, long 
         e = launch_gemm_tc(opnd(S->dY, 64, 64, kext, 1), opnd(S->Hs[D - 1], H, H, kext, 1), 16, H, splits, false, ep,
                            S->n_sms, S->err, st, L);
     }
-    bf16 *dz = S->dZa, *dz2 = S->dZb;
-    if (e == cudaSuccess) {
-        GemmEpi ep{};
-        ep.kind = GEPI_MASK;
-        ep.out = dz;
-        ep.ldo = H;
-        ep.mask = S->Hs[D - 1];
-        ep.ldm = H;
-        e = launch_gemm_tc(opnd(S->dY, 64, cap, 64), opnd(S->woutT, 64, H, 64), rows, H, 1, false, ep, S->n_sms,
-                           S->err, st, L);
-    }
     for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
         const int kin = l == 0 ? d.d0p : H;
         const bf16* x = l == 0 ? S->X0 : S->Hs[l - 1];
-        // dW_l = dZ_l^T X_l and db_l (the row sums of dZ_l^T), both read batch-major
-        {
-            GemmEpi ep{};
-            ep.kind = GEPI_F32;
-            ep.out = S->part + S->tab.part_off[l];
-            ep.ldo = kin;
-            ep.part_stride = S->tab.part_stride[l];
-            ep.bias_part = S->bpart + S->tab.bias_off[l];
-            ep.ldo_bias = H;
-            e = launch_gemm_tc(opnd(dz, H, H, kext, 1), opnd(x, kin, kin, kext, 1), H, kin, splits, false, ep, S->n_sms,
-                               S->err, st, L);
-        }
-        if (e != cudaSuccess) break;
-        if (l > 0) {
-            // dZ_{l-1} = (dZ_l W_l) * (H_{l-1} > 0)
-            GemmEpi ep{};
-            ep.kind = GEPI_MASK;
-            ep.out = dz2;
-            ep.ldo = H;
-            ep.mask = S->Hs[l - 1];
-            ep.ldm = H;
-            e = launch_gemm_tc(opnd(dz, H, cap, H), opnd(S->wt[l], H, kin, H), rows, kin, 1, false, ep, S->n_sms,
-                               S->err, st, L);
-            std::swap(dz, dz2);
-        } else {
-            // features: only the embedding columns [2F, 2F + E) need a gradient,
-            // added into the embedding of each row's beam
-            GemmEpi ep{};
-            ep.kind = GEPI_EMB;
-            ep.ant = S->ant;
-            ep.gemb = S->g + S->off_emb;
-            ep.emb = d.E;
-            const int erows = (d.E + 15) / 16 * 16;
-            e = launch_gemm_tc(opnd(dz, H, cap, H), opnd(S->wt[0] + (long long)2 * d.F * H, H, erows, H), rows, d.E, 1,
-                               false, ep, S->n_sms, S->err, st, L);
-        }
+        GemmEpi ep{};
+        ep.kind = GEPI_F32;
+        ep.out = S->part + S->tab.part_off[l];
+        ep.ldo = kin;
+        ep.part_stride = S->tab.part_stride[l];
+        ep.bias_part = S->bpart + S->tab.bias_off[l];
+        ep.ldo_bias = H;
+        e = launch_gemm_tc(opnd(S->dZs[l], H, H, kext, 1), opnd(x, kin, kin, kext, 1), H, kin, splits, false, ep,
+                           S->n_sms, S->err, st, L);
     }
     if (e == cudaSuccess && reduce) {
         k_reduce_grads<<<dim3(64, D + 1), 256, 0, st>>>(S->tab, S->part, splits, S->bpart, bias_rows(S, rows), S->g);
         ++*L;
         e = cudaGetLastError();
     }
+    return e;
+}
+
+// One training pass over the `rows` samples in S->ant / az / za / nu / T (loss
+// accumulated into S->loss, which the caller zeroes): the gradients of the
+// loss as k-split partials and the embedding gradient in S->g, with `reduce`
+// every gradient summed into S->g.  Where the network's shape allows, the
+// row-local part (features, forward, loss, input gradients, embedding
+// gradient) is one fused launch (mlp_chain_tc.cu); else it runs product by
+// product.  The weight gradients follow as products over the batch.
+cudaError_t train_rows(Surrogate* S, int rows, bool reduce, cudaStream_t st, long long* L) {
+    const Dims& d = S->d;
+    const int D = d.depth, H = d.H;
+    // the embedding gradient accumulates; the rest is written by the reduction
+    cudaError_t e = reduce ? cudaMemsetAsync(S->g, 0, sizeof(float) * (size_t)S->n_par, st)
+                           : cudaMemsetAsync(S->g + S->off_emb, 0, sizeof(float) * (size_t)(S->n_par - S->off_emb), st);
+    const long long kext = std::max(rows, 64);
+    if (e == cudaSuccess && kext > rows) {
+        // a batch below 64 rows: the rows [rows, 64) the box reads must be zero in every operand
+        auto zero = [&](bf16* a, int width) {
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(a + (long long)rows * width, 0, sizeof(bf16) * (size_t)(kext - rows) * width, st);
+        };
+        zero(S->X0, d.d0p);
+        for (int l = 0; l < D; ++l) zero(S->Hs[l], H);
+        zero(S->dY, 64);
+        for (int l = 0; l < D; ++l) zero(S->dZs[l], H);
+    }
+    if (e != cudaSuccess) return e;
+    if (mlp_chain_supported(d.F, d.E, H, D, d.d0p, d.n_out, rows)) {
+        ChainArgs c{};
+        c.F = d.F; c.E = d.E; c.H = H; c.depth = D; c.d0p = d.d0p; c.n_out = d.n_out;
+        c.nu_mid = d.nu_mid; c.nu_half = d.nu_half;
+        c.M = rows;
+        c.p = S->p;
+        for (int l = 0; l <= D; ++l) c.off_b[l] = S->off_b[l];
+        c.off_emb = S->off_emb;
+        c.Bf = S->Bf;
+        for (int l = 0; l < D; ++l) {
+            c.w[l] = S->pb + S->off_w[l];
+            c.wt[l] = S->wt[l];
+            c.Hs[l] = S->Hs[l];
+            c.dZs[l] = S->dZs[l];
+        }
+        c.wout16 = S->wout16;
+        c.woutT = S->woutT;
+        c.ant = S->ant; c.az = S->az; c.za = S->za; c.nu = S->nu; c.T = S->T;
+        c.X0 = S->X0;
+        c.dY = S->dY;
+        c.gscale = 2.f / (float)((long long)rows * d.n_out);
+        c.loss = S->loss;
+        c.gemb = S->g + S->off_emb;
+        e = launch_mlp_chain_tc(c, S->n_sms, S->err, st, L);
+    } else {
+        e = launch_features(d, S->Bf, S->p + S->off_emb, rows, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
+        ++*L;
+        if (e == cudaSuccess) e = forward(S, rows, true, st, L);
+        if (e == cudaSuccess) e = input_grads(S, rows, st, L);
+    }
+    if (e == cudaSuccess) e = weight_grads(S, rows, reduce, st, L);
     return e;
 }
 
@@ -840,9 +888,7 @@ cudaError_t surrogate_grad(Surrogate* S, int n, const int* ant, const float* az,
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->T, T, sizeof(float) * n * d.n_out, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    e = launch_features(d, S->Bf, S->p + S->off_emb, n, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
-    if (e == cudaSuccess) e = forward(S, n, true, st, &L);
-    if (e == cudaSuccess) e = backward(S, n, true, st, &L);
+    e = train_rows(S, n, true, st, &L);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grads_host, S->g, sizeof(float) * S->n_par, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss, S->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = check_err(S, st);
@@ -925,10 +971,8 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
         S->T = s_T[k];
         if (it == 0 || it == steps - 1) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, S->ev_ready[k], 0);
-        if (e == cudaSuccess)
-            e = launch_features(d, S->Bf, S->p + S->off_emb, batch, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
-        *L += 1;
-        if (e == cudaSuccess) e = forward(S, batch, true, st, L);
+        if (e == cudaSuccess) e = train_rows(S, batch, false, st, L);
+        if (e == cudaSuccess) e = cudaEventRecord(S->ev_free[k], st);  // set k read for the last time
         if (e != cudaSuccess) break;
         if (it == 0 || it == steps - 1) {
             double l = 0;
@@ -938,8 +982,6 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
             if (it == 0) *loss_first = l;
             if (it == steps - 1) *loss_last = l;
         }
-        e = backward(S, batch, false, st, L);
-        if (e == cudaSuccess) e = cudaEventRecord(S->ev_free[k], st);  // set k read for the last time
         if (e != cudaSuccess) break;
         AdamArgs a;
         a.lr = lr1 + 0.5f * (lr0 - lr1) * (1.f + cosf((float)kPi * it / std::max(1, steps - 1)));

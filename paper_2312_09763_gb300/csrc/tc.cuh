@@ -1,6 +1,6 @@
 // tc.cuh -- inline PTX for the sm_103a tensor-core kernels (tcgen05 MMA and
 // TMEM, TMA bulk tensor copies, mbarriers) shared by the HERK (herk_tc.cu)
-// and the learned beam's forward pass (mlp_tc.cu).  Every mbarrier wait is
+// and the learned beam's kernels (mlp_tc.cu, mlp_train_tc.cu, mlp_chain_tc.cu).  Every mbarrier wait is
 // bounded: after 2 s of %globaltimer it records MV device timeout in the
 // status word, raises the block's abort flag and returns false.
 #pragma once
@@ -191,6 +191,22 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+
+// TMA store of a 2D box from shared memory (bulk-group completion): the
+// shared-memory writes it reads must have been made visible to the async
+// proxy (fence.proxy.async by the writers, then a barrier).  x * element size
+// must be a multiple of 16 bytes; boxes past the tensor's extent are clipped.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the committed stores have read their shared-memory sources
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// the committed stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -70,6 +70,30 @@ def test_gradients_match_oracle_network():
     assert np.linalg.norm(g - go) <= 0.1 * np.linalg.norm(go)
 
 
+@pytest.mark.parametrize("n, cfg", [
+    # the fused training pass (one launch for features, forward, loss and input
+    # gradients): the default 4 x 256 network, a batch of 7 full 128-row tiles
+    # and a ragged one
+    (1000, dict()),
+    # a width that is not a multiple of 64: the product-by-product path
+    (600, dict(n_freq=16, emb_dim=8, width=80, depth=3)),
+])
+def test_gradients_match_oracle_network_shapes(n, cfg):
+    w = workload()
+    sim = simulator(w)
+    sim.surrogate_create(**cfg)
+    beam, az, za, nu = points(n, w.n_ant, 5, w)
+    t = np.random.default_rng(6).normal(size=(n, 8)).astype(np.float32)
+    g, loss = sim.surrogate_grad(beam, az, za, nu, t)
+    net = oracle_net(sim, *grid_meta(w))
+    lo, go = mlp.loss_and_grads(net, beam, az, za, nu, t.astype(np.float64))
+    go = flat_grads(sim, go)
+    assert abs(loss - lo) <= 1e-2 * lo
+    cos = float(g @ go / (np.linalg.norm(g) * np.linalg.norm(go)))
+    assert cos >= 0.995, cos
+    assert np.linalg.norm(g - go) <= 0.1 * np.linalg.norm(go)
+
+
 def test_training_fits_the_gridded_beams():
     w = workload()
     sim = simulator(w)
