@@ -286,6 +286,8 @@ struct ChainArgs {
 // Whether the fused pass handles this network shape and batch.
 bool mlp_chain_supported(int F, int E, int H, int depth, int d0p, int n_out, int M);
 cudaError_t mlp_chain_init();
+// n_sms: the SMs the launch may take (one CTA each, as few as keep the same
+// number of tiles per CTA).
 cudaError_t launch_mlp_chain_tc(const ChainArgs& a, int n_sms, int* d_err, cudaStream_t st, long long* launches);
 
 // ------------------------------------- tensor-core products (mlp_train_tc.cu)

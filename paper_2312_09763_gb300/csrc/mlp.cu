@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "sample.cuh"
 
 namespace mv {
 
@@ -238,106 +239,22 @@ __global__ void k_reduce_adam(LayerTab t, const float* __restrict__ part, int sp
 }
 
 // ----------------------------------------------------- training samples
-// splitmix64 (Steele, Lea and Flood 2014): a counter-based stream of 64-bit
-// values; uniform doubles take its top 53 bits.
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
-    x += 0x9E3779B97F4A7C15ull;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-    return x ^ (x >> 31);
-}
-__device__ __forceinline__ double uniform01(unsigned long long seed, unsigned long long ctr) {
-    return (double)(splitmix64(seed ^ splitmix64(ctr)) >> 11) * (1.0 / 9007199254740992.0);
-}
-
-__device__ __forceinline__ float keys_w(float x) {
-    const float t = fabsf(x);
-    if (t <= 1.f) return (1.5f * t - 2.5f) * t * t + 1.f;
-    if (t < 2.f) return ((-0.5f * t + 2.5f) * t - 4.f) * t + 2.f;
-    return 0.f;
-}
-
-// Keys-cubic interpolation in (za, az) of component `comp` of beam `b` of the
-// raw grid at frequency node f (Sec. 2.4; pole and az wrap as in the beam
-// step of the simulator).
-__device__ float2 grid_value_node(const Model& m, const float2* __restrict__ grid, int b, int comp, float az,
-                                  float za, int f) {
-    const long long plane = (long long)m.n_za * m.n_az;
-    const float2* G = grid + (((long long)b * m.n_feed * m.n_ax + comp) * m.n_nu + f) * plane;
-    const float uz = za / m.dza, ua = az / m.daz;
-    const float fz = floorf(uz), fa = floorf(ua);
-    const float tz = uz - fz, ta = ua - fa;
-    const int z0 = (int)fz - 1, a0 = (int)fa - 1;
-    const float wz[4] = {keys_w(tz + 1.f), keys_w(tz), keys_w(1.f - tz), keys_w(2.f - tz)};
-    const float wa[4] = {keys_w(ta + 1.f), keys_w(ta), keys_w(1.f - ta), keys_w(2.f - ta)};
-    const float pole_sign = m.n_ax == 2 ? -1.f : 1.f;
-    float re = 0.f, im = 0.f;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int row = z0 + r, sh = 0;
-        float sg = 1.f;
-        if (row < 0) { row = -row; sh = m.n_az / 2; sg = pole_sign; }
-        if (row > m.n_za - 1) row = m.n_za - 1;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int col = (a0 + q + sh) % m.n_az;
-            if (col < 0) col += m.n_az;
-            const float w2 = wz[r] * wa[q] * sg;
-            const float2 v = G[(long long)row * m.n_az + col];
-            re = fmaf(w2, v.x, re);
-            im = fmaf(w2, v.y, im);
-        }
-    }
-    return make_float2(re, im);
-}
-
 // Draw M training samples (antenna, az, za, nu): beams stratified over the
 // batch, (az, za, nu) uniform (nu inside the grid's cubic margin), and their
-// targets from the gridded beams (Keys cubic in az, za and frequency): four
-// consecutive threads per (sample, component),
-// one per frequency node of the stencil, summed with shuffles; every thread
-// of a sample draws the same values.
-__global__ void k_sample(Model m, const float2* __restrict__ grid, double nu0, double dnu, double nu_lo,
-                         double nu_hi, unsigned long long seed, unsigned long long step, int M, int n_out,
-                         int* __restrict__ ant, float* __restrict__ az, float* __restrict__ za, float* __restrict__ nu,
-                         float* __restrict__ T) {
-    const int ncomp = m.n_feed * m.n_ax;
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int jt = (int)(q & 3);
-    const long long qc = q >> 2;
-    const bool valid = qc < (long long)M * ncomp;
-    const int i = valid ? (int)(qc / ncomp) : 0, c = valid ? (int)(qc % ncomp) : 0;
-    const unsigned long long base = (step * (unsigned long long)M + i) * 4ull;
-    // beams stratified over the batch: rows [b M / n_beam, (b + 1) M / n_beam)
-    // belong to beam b (each beam equally often, its rows together)
-    const int a = min(m.n_beam - 1, (int)(((long long)i * m.n_beam) / M));
-    const double vaz = uniform01(seed, base + 1) * 2.0 * kPi;
-    const double vza = uniform01(seed, base + 2) * 0.5 * kPi;
-    const double vnu = nu_lo + uniform01(seed, base + 3) * (nu_hi - nu_lo);
-    float2 v = make_float2(0.f, 0.f);
-    if (valid && 2 * c < n_out) {
-        const float u = (float)((vnu - nu0) / dnu);
-        const float fu = floorf(u), tu = u - fu;
-        const float w = keys_w(tu + 1.f - (float)jt);
-        v = grid_value_node(m, grid, a, c, (float)vaz, (float)vza, (int)fu - 1 + jt);
-        v.x *= w;
-        v.y *= w;
-    }
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
-    if (!valid || jt != 0) return;
-    if (c == 0) {
-        ant[i] = a;
-        az[i] = (float)vaz;
-        za[i] = (float)vza;
-        nu[i] = (float)vnu;
-    }
-    if (2 * c < n_out) {
-        T[(long long)i * n_out + 2 * c] = v.x;
-        T[(long long)i * n_out + 2 * c + 1] = v.y;
-    }
+// targets from the gridded beams (Keys cubic in az, za and frequency), as
+// sample_item defines them.  A grid-stride loop of 1024-thread blocks (one
+// per SM), so that training can run it beside its own launches on the SMs
+// those leave free.
+constexpr int kSampleThreads = 1024;
+__global__ void __launch_bounds__(kSampleThreads, 1)
+k_sample(Model m, const float2* __restrict__ grid, SampleRange rg, unsigned long long seed, unsigned long long step,
+         int M, int n_out, int* __restrict__ ant, float* __restrict__ az, float* __restrict__ za,
+         float* __restrict__ nu, float* __restrict__ T) {
+    // every lane of a warp takes the same number of turns (the shuffles need all 32)
+    const long long total = (4ll * M * m.n_feed * m.n_ax + 31) / 32 * 32;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride)
+        sample_item(m, grid, rg, seed, step, M, n_out, q, ant, az, za, nu, T);
 }
 
 // Rows (beta, s) of one instance for the surrogate: antenna beta and the live
@@ -423,7 +340,8 @@ struct Surrogate {
     int *ant = nullptr;
     float *az = nullptr, *za = nullptr, *nu = nullptr, *T = nullptr, *Y = nullptr;
     // a second set of training samples: the sampler of step i + 1 runs on a
-    // side stream while step i trains on the other set
+    // side stream, on SMs the training launches leave free, while step i
+    // trains on the other set
     int* ant2 = nullptr;
     float *az2 = nullptr, *za2 = nullptr, *nu2 = nullptr, *T2 = nullptr;
     cudaStream_t side = nullptr;
@@ -596,7 +514,7 @@ cudaError_t input_grads(Surrogate* S, int rows, cudaStream_t st, long long* L) {
 // dW_l = dz_l^T x_l, the bias gradients as the row sums of dY^T and dz_l^T;
 // with `reduce` the partials are summed into S->g (training sums them in its
 // optimiser step instead, k_reduce_adam).
-cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, cudaStream_t st, long long* L) {
+cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, int sms, cudaStream_t st, long long* L) {
     const Dims& d = S->d;
     const int D = d.depth, H = d.H;
     // K extent of the products (the batch; TMA reads rows past it as zeros), at
@@ -613,7 +531,7 @@ cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, cudaStream_t st, l
         ep.bias_part = S->bpart + S->tab.bias_off[D];
         ep.ldo_bias = 16;
         e = launch_gemm_tc(opnd(S->dY, 64, 64, kext, 1), opnd(S->Hs[D - 1], H, H, kext, 1), 16, H, splits, false, ep,
-                           S->n_sms, S->err, st, L);
+                           sms, S->err, st, L);
     }
     for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
         const int kin = l == 0 ? d.d0p : H;
@@ -626,7 +544,7 @@ cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, cudaStream_t st, l
         ep.bias_part = S->bpart + S->tab.bias_off[l];
         ep.ldo_bias = H;
         e = launch_gemm_tc(opnd(S->dZs[l], H, H, kext, 1), opnd(x, kin, kin, kext, 1), H, kin, splits, false, ep,
-                           S->n_sms, S->err, st, L);
+                           sms, S->err, st, L);
     }
     if (e == cudaSuccess && reduce) {
         k_reduce_grads<<<dim3(64, D + 1), 256, 0, st>>>(S->tab, S->part, splits, S->bpart, bias_rows(S, rows), S->g);
@@ -636,14 +554,15 @@ cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, cudaStream_t st, l
     return e;
 }
 
-// One training pass over the `rows` samples in S->ant / az / za / nu / T (loss
-// accumulated into S->loss, which the caller zeroes): the gradients of the
-// loss as k-split partials and the embedding gradient in S->g, with `reduce`
-// every gradient summed into S->g.  Where the network's shape allows, the
-// row-local part (features, forward, loss, input gradients, embedding
-// gradient) is one fused launch (mlp_chain_tc.cu); else it runs product by
-// product.  The weight gradients follow as products over the batch.
-cudaError_t train_rows(Surrogate* S, int rows, bool reduce, cudaStream_t st, long long* L) {
+// One training pass over the `rows` samples in S->ant / az / za / nu / T; the
+// loss is accumulated into S->loss, which the caller zeroes.  Leaves the
+// gradients of the loss as k-split partials and the embedding gradient in
+// S->g, with `reduce` every gradient summed into S->g.  Where the network's
+// shape allows, the row-local part (features, forward, loss, input gradients,
+// embedding gradient) is one fused launch (mlp_chain_tc.cu); else it runs
+// kernel by kernel.  The weight gradients follow as products over the batch.
+// The tensor-core launches take at most `sms` SMs.
+cudaError_t train_rows(Surrogate* S, int rows, bool reduce, int sms, cudaStream_t st, long long* L) {
     const Dims& d = S->d;
     const int D = d.depth, H = d.H;
     // the embedding gradient accumulates; the rest is written by the reduction
@@ -685,14 +604,14 @@ cudaError_t train_rows(Surrogate* S, int rows, bool reduce, cudaStream_t st, lon
         c.gscale = 2.f / (float)((long long)rows * d.n_out);
         c.loss = S->loss;
         c.gemb = S->g + S->off_emb;
-        e = launch_mlp_chain_tc(c, S->n_sms, S->err, st, L);
+        e = launch_mlp_chain_tc(c, sms, S->err, st, L);
     } else {
         e = launch_features(d, S->Bf, S->p + S->off_emb, rows, S->ant, S->az, S->za, S->nu, S->X0, nullptr, 0, st);
         ++*L;
         if (e == cudaSuccess) e = forward(S, rows, true, st, L);
         if (e == cudaSuccess) e = input_grads(S, rows, st, L);
     }
-    if (e == cudaSuccess) e = weight_grads(S, rows, reduce, st, L);
+    if (e == cudaSuccess) e = weight_grads(S, rows, reduce, sms, st, L);
     return e;
 }
 
@@ -888,7 +807,7 @@ cudaError_t surrogate_grad(Surrogate* S, int n, const int* ant, const float* az,
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->T, T, sizeof(float) * n * d.n_out, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
     if (e != cudaSuccess) return e;
-    e = train_rows(S, n, true, st, &L);
+    e = train_rows(S, n, true, S->n_sms, st, &L);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grads_host, S->g, sizeof(float) * S->n_par, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss, S->loss, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = check_err(S, st);
@@ -927,7 +846,8 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
     cudaError_t e = ensure_rows(S, batch);
     if (e != cudaSuccess) return e;
     const Dims& d = S->d;
-    const double nu_lo = nu0 + 1.0 * dnu, nu_hi = nu0 + (m.n_nu - 3) * dnu * 0.999999;
+    // frequencies inside the grid's cubic margin: fractional index in [1, n_nu - 3)
+    const SampleRange rg{1.f, (float)(m.n_nu - 4) * 0.999999f, (float)nu0, (float)dnu};
     if (!S->side) {
         e = cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking);
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
@@ -936,34 +856,39 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
         }
         if (e != cudaSuccess) return e;
     }
-    // sample sets: set 0 the arrays forward / backward read, set 1 the second
+    // SMs: the training launches take at most `sms` (a multiple of 16 near
+    // five sixths of them: one CTA per SM each), the sampler of the next step
+    // one block on each of the others (a 1024-thread block does not fit beside
+    // a training CTA, so neither waits for the other)
+    const int sms = std::max(1, std::min(S->n_sms - 1, (S->n_sms * 5 / 6 + 15) / 16 * 16));
+    // sample sets: set 0 the arrays the training pass reads, set 1 the second
     // one; the pointers swap every step
     int* s_ant[2] = {S->ant, S->ant2};
     float* s_az[2] = {S->az, S->az2};
     float* s_za[2] = {S->za, S->za2};
     float* s_nu[2] = {S->nu, S->nu2};
     float* s_T[2] = {S->T, S->T2};
-    auto sample = [&](int it) {  // on the side stream, into set it & 1, once the set is free
+    auto sample = [&](int it, int blocks) {  // on the side stream, into set it & 1, once the set is free
         const int k = it & 1;
         cudaError_t x = cudaSuccess;
         if (it >= 2) x = cudaStreamWaitEvent(S->side, S->ev_free[k], 0);
         if (x == cudaSuccess) {
-            k_sample<<<gridsz(4ll * batch * m.n_feed * m.n_ax, 128), 128, 0, S->side>>>(
-                m, grid, nu0, dnu, nu_lo, nu_hi, seed, (unsigned long long)it, batch, d.n_out, s_ant[k], s_az[k],
-                s_za[k], s_nu[k], s_T[k]);
+            k_sample<<<blocks, kSampleThreads, 0, S->side>>>(m, grid, rg, seed, (unsigned long long)it, batch,
+                                                             d.n_out, s_ant[k], s_az[k], s_za[k], s_nu[k], s_T[k]);
             ++*L;
             x = cudaGetLastError();
         }
         if (x == cudaSuccess) x = cudaEventRecord(S->ev_ready[k], S->side);
         return x;
     };
-    // the side stream starts after the work already queued on st
+    // the side stream starts after the work already queued on st; the first
+    // samples take every SM
     e = cudaEventRecord(S->ev_free[0], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->side, S->ev_free[0], 0);
-    if (e == cudaSuccess) e = sample(0);
+    if (e == cudaSuccess) e = sample(0, S->n_sms);
     for (int it = 0; it < steps && e == cudaSuccess; ++it) {
         const int k = it & 1;
-        if (it + 1 < steps && (e = sample(it + 1)) != cudaSuccess) break;
+        if (it + 1 < steps && (e = sample(it + 1, S->n_sms - sms)) != cudaSuccess) break;
         S->ant = s_ant[k];
         S->az = s_az[k];
         S->za = s_za[k];
@@ -971,7 +896,7 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
         S->T = s_T[k];
         if (it == 0 || it == steps - 1) e = cudaMemsetAsync(S->loss, 0, sizeof(double), st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, S->ev_ready[k], 0);
-        if (e == cudaSuccess) e = train_rows(S, batch, false, st, L);
+        if (e == cudaSuccess) e = train_rows(S, batch, false, sms, st, L);
         if (e == cudaSuccess) e = cudaEventRecord(S->ev_free[k], st);  // set k read for the last time
         if (e != cudaSuccess) break;
         if (it == 0 || it == steps - 1) {

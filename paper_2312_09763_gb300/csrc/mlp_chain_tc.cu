@@ -20,16 +20,16 @@
 // streamed by TMA in 64-column panels through a ring.  One persistent CTA per
 // SM walks 128-row tiles.  Warp 0 streams the weight panels, warp 1 owns TMEM
 // and issues the MMAs (M = 128, N <= 256, K = 16) into two 256-column
-// accumulators in turn, and warps 2-17 (four per TMEM lane quadrant; thread =
-// one row and 16 columns of every 64-column panel) drain each step's
-// accumulator through its epilogue back into the activation panels, panel by
-// panel: the MMAs of step s + 1 start on panel 0 while the epilogue of step s
-// still writes the later panels, and overlap the rest of it.  The ReLU masks
-// of the forward layers stay in shared memory as bits for the backward steps
+// accumulators in turn, warp 2 stores each step's completed input panels to
+// global memory with TMA (x0, h_l or dz_l), and warps 3-18 (four per TMEM lane
+// quadrant; thread = one row and 16 columns of every 64-column panel) drain
+// each step's accumulator through its epilogue back into the activation
+// panels, panel by panel: the MMAs of step s + 1 start on panel 0 while the
+// epilogue of step s still writes the later panels.  A step's epilogue
+// overwrites the panels once the stores have read them.  The ReLU masks of
+// the forward layers stay in shared memory as bits for the backward steps
 // (the same thread reads back its own bits), so the backward pass reads no
-// activations.  The MMA warp stores each completed set of panels to global
-// memory with TMA (one step's input: x0, h_l or dz_l) and waits for those
-// stores to have read the panels before it releases them to the epilogue.
+// activations.
 // Every mbarrier wait is bounded (tc.cuh): on expiry the kernel records a
 // device timeout, lets copies and MMAs in flight land, frees TMEM and returns.
 #include <cuda_bf16.h>
@@ -52,7 +52,7 @@ constexpr int A_PANEL = TM * 128;            // 16 KB
 constexpr int SMEM_ACT = 4 * A_PANEL;        // 64 KB: up to 256 columns
 constexpr int W_SLOT = 256 * 128;            // 32 KB: a weight panel of up to 256 rows
 constexpr int NEPI = 16;                     // epilogue warps
-constexpr int THREADS = (2 + NEPI) * 32;
+constexpr int THREADS = (3 + NEPI) * 32;    // producer, MMA, storer, epilogue
 constexpr int TMEM_COLS = 512;               // two 256-column accumulators
 constexpr int MAX_SMEM = 227 * 1024;
 
@@ -91,7 +91,7 @@ __host__ __device__ constexpr int bias_off(int nslot, int D) { return mask_off(n
 __host__ __device__ constexpr int fb_off(int nslot, int D) { return bias_off(nslot, D) + (D + 1) * 256 * 4; }
 __host__ __device__ constexpr int bar_off(int nslot, int D, int F) { return fb_off(nslot, D) + F * 16; }
 __host__ __device__ constexpr int smem_bytes(int nslot, int D, int F) {
-    return 1024 + bar_off(nslot, D, F) + (2 * nslot + 8) * 8 + 16;
+    return 1024 + bar_off(nslot, D, F) + (2 * nslot + 9) * 8 + 16;
 }
 
 // Shared-memory address of the 16-byte chunk holding columns [8 j, 8 j + 8)
@@ -157,6 +157,7 @@ __device__ __forceinline__ void arrive_panel(const Epi e, int p) {
     if (e.lane == 0) mbar_arrive(e.afull0 + 8u * (uint32_t)p);
 }
 
+// One row's sample: beam and the network's inputs x.
 struct Row {
     int valid, a;
     float x0, x1, x2;
@@ -214,12 +215,18 @@ __device__ __forceinline__ void write_features(const Job& j, const Epi e, const 
 __device__ __forceinline__ uint32_t emit_relu(const Epi e, int c, const float* bias, const uint32_t (&a)[16]) {
     uint32_t h[8];
     uint32_t bits = 0;
+    const float4* b4 = reinterpret_cast<const float4*>(bias + c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 b = b4[q];
+        h[2 * q] = relu_bf16x2(__uint_as_float(a[4 * q]) + b.x, __uint_as_float(a[4 * q + 1]) + b.y);
+        h[2 * q + 1] = relu_bf16x2(__uint_as_float(a[4 * q + 2]) + b.z, __uint_as_float(a[4 * q + 3]) + b.w);
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        h[k] = relu_bf16x2(__uint_as_float(a[2 * k]) + bias[c + 2 * k], __uint_as_float(a[2 * k + 1]) + bias[c + 2 * k + 1]);
         // a ReLU output is positive exactly when its BF16 bits are not zero
-        bits |= ((h[k] & 0xFFFFu) != 0u ? 1u : 0u) << (2 * k);
-        bits |= ((h[k] >> 16) != 0u ? 1u : 0u) << (2 * k + 1);
+        bits |= (uint32_t)((h[k] & 0xFFFFu) != 0u) << (2 * k);
+        bits |= (uint32_t)(h[k] > 0xFFFFu) << (2 * k + 1);
     }
     st_shared_v4(a_chunk(e.act, e.r, c), h[0], h[1], h[2], h[3]);
     st_shared_v4(a_chunk(e.act, e.r, c + 8), h[4], h[5], h[6], h[7]);
@@ -249,10 +256,11 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
     float* sbias = reinterpret_cast<float*>(smem + bias_off(NSL, D));
     float4* sB = reinterpret_cast<float4*>(smem + fb_off(NSL, D));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off(NSL, D, j.F));
-    // barriers: wfull[NSL], wfree[NSL], afull[4], dfull[2], tempty[2]
+    // barriers: wfull[NSL], wfree[NSL], afull[4], dfull[2], tempty[2], sdone
     const uint32_t b0 = smem_u32(bars);
-    const uint32_t WFULL = b0, WFREE = b0 + 8u * NSL, AFULL = b0 + 16u * NSL, DFULL = AFULL + 32u, TEMPTY = AFULL + 48u;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSL + 8);
+    const uint32_t WFULL = b0, WFREE = b0 + 8u * NSL, AFULL = b0 + 16u * NSL, DFULL = AFULL + 32u, TEMPTY = AFULL + 48u,
+                   SDONE = AFULL + 64u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSL + 9);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NS = j.ns;
@@ -267,6 +275,7 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
         for (int i = 0; i < NSL; ++i) { mbar_init(WFULL + 8u * i, 1); mbar_init(WFREE + 8u * i, 1); }
         for (int p = 0; p < 4; ++p) mbar_init(AFULL + 8u * p, NEPI);
         for (int b = 0; b < 2; ++b) { mbar_init(DFULL + 8u * b, 1); mbar_init(TEMPTY + 8u * b, NEPI); }
+        mbar_init(SDONE, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -301,7 +310,7 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                 }
         }
     } else if (warp == 1) {
-        // ---- MMAs, and the TMA stores of each step's input panels
+        // ---- MMAs
         if (lane == 0) {
             int it = 0, g = 0;
             bool ok = true;
@@ -323,7 +332,6 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                             break;
                         }
                         tc_fence_after();
-                        if (j.store[s]) tma_store_2d(&maps.st[s], p * KP, tile * TM, act + p * A_PANEL);
                         const int sl = it % NSL;
                         if (!wait_bounded_spin(WFULL + 8u * sl, (uint32_t)(it / NSL) & 1u, abort_flag, err)) {
                             ok = false;
@@ -337,12 +345,32 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                         tc_commit(WFREE + 8u * sl);
                     }
                     if (!ok) break;
-                    // the stores have read the panels before the epilogue may overwrite them
+                    tc_commit(DFULL + 8u * buf);
+                }
+        }
+    } else if (warp == 2) {
+        // ---- TMA stores of each step's input panels (x0, h_l, dz_l) as they
+        // complete; a step's epilogue overwrites the panels only once the
+        // stores have read them (sdone, once per step)
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < j.n_tiles && ok; tile += gridDim.x)
+                for (int s = 0; s < NS && ok; ++s, ++g) {
+                    const int np = (j.K[s] + KP - 1) / KP;
+                    for (int p = 0; p < np; ++p) {
+                        if (!wait_bounded_spin(AFULL + 8u * p, (uint32_t)g & 1u, abort_flag, err)) {
+                            ok = false;
+                            break;
+                        }
+                        if (j.store[s]) tma_store_2d(&maps.st[s], p * KP, tile * TM, act + p * A_PANEL);
+                    }
+                    if (!ok) break;
                     if (j.store[s]) {
                         bulk_commit();
                         bulk_wait_read_all();
                     }
-                    tc_commit(DFULL + 8u * buf);
+                    mbar_arrive(SDONE);
                 }
             bulk_commit();
             bulk_wait_all();
@@ -350,7 +378,7 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
     } else {
         // ---- epilogue warps: TMEM lane quadrant q, columns [16 cg, 16 cg + 16)
         // of every 64-column panel; thread = row r of the tile
-        const int q = warp & 3, cg = (warp - 2) >> 2;
+        const int q = warp & 3, cg = (warp - 3) >> 2;
         const int r = q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         const Epi e{act, AFULL, r, cg, lane, sB};
@@ -362,10 +390,11 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
         if (tile < j.n_tiles) write_features(j, e, cur);
         for (; tile < j.n_tiles && ok; tile += gridDim.x) {
             const long long m = (long long)tile * TM + r;
-            const Row nxt = load_row(j, tile + gridDim.x, r);
+            Row nxt{};
             for (int s = 0; s < NS; ++s, ++g) {
                 const int buf = g & 1;
-                if (!wait_bounded_spin(DFULL + 8u * buf, (uint32_t)(g >> 1) & 1u, abort_flag, err)) {
+                if (!wait_bounded(DFULL + 8u * buf, (uint32_t)(g >> 1) & 1u, abort_flag, err, kTimeoutNs, 1000u) ||
+                    !wait_bounded_spin(SDONE, (uint32_t)g & 1u, abort_flag, err)) {
                     ok = false;
                     break;
                 }
@@ -399,38 +428,34 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                     if (lane == 0) mbar_arrive(TEMPTY + 8u * buf);
                     for (int p = np; p < 4; ++p) arrive_panel(e, p);
                 } else if (kind == K_LOSS) {
-                    // columns [0, 16): outputs n < n_out, zero gradient past them
+                    // warp cg: outputs 2 cg and 2 cg + 1 (component cg), residual
+                    // against the target, dL/dy into column 2 cg of panel 0 (the
+                    // next step's K = 16 input) and into dY
                     float lsum = 0.f;
-                    if (cg == 0) {
-                        uint32_t a[16];
-                        tmem_ld16(tb, a);
-                        tmem_wait_ld16(a);
-                        float gq[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            gq[i] = 0.f;
-                            if (cur.valid && i < j.n_out) {
-                                const float rr = __uint_as_float(a[i]) + sbias[D * 256 + i] - j.T[m * j.n_out + i];
-                                lsum += rr * rr;
-                                gq[i] = j.gscale * rr;
-                            }
-                        }
-                        uint32_t h[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) h[k] = pack_bf16(gq[2 * k], gq[2 * k + 1]);
-                        st_shared_v4(a_chunk(act, r, 0), h[0], h[1], h[2], h[3]);
-                        st_shared_v4(a_chunk(act, r, 8), h[4], h[5], h[6], h[7]);
+                    if (2 * cg < j.n_out) {
+                        uint32_t a2[2];
+                        tmem_ld2(tb + 2 * cg, a2);
+                        tmem_wait_ld2(a2);
+                        float g0 = 0.f, g1 = 0.f;
                         if (cur.valid) {
-                            bf16* o = j.dY + m * 64;
-                            st_global_v4(o, h[0], h[1], h[2], h[3]);
-                            st_global_v4(o + 8, h[4], h[5], h[6], h[7]);
+                            const float t0 = j.T[m * j.n_out + 2 * cg], t1 = j.T[m * j.n_out + 2 * cg + 1];
+                            const float r0 = __uint_as_float(a2[0]) + sbias[D * 256 + 2 * cg] - t0;
+                            const float r1 = __uint_as_float(a2[1]) + sbias[D * 256 + 2 * cg + 1] - t1;
+                            lsum = r0 * r0 + r1 * r1;
+                            g0 = j.gscale * r0;
+                            g1 = j.gscale * r1;
                         }
+                        const uint32_t h = pack_bf16(g0, g1);
+                        asm volatile("st.shared.b32 [%0], %1;" ::"r"(a_chunk(act, r, 2 * cg) + 4u * (uint32_t)cg),
+                                     "r"(h)
+                                     : "memory");
+                        if (cur.valid) *reinterpret_cast<uint32_t*>(j.dY + m * 64 + 2 * cg) = h;
                     }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(TEMPTY + 8u * buf);
                     for (int p = 0; p < 4; ++p) arrive_panel(e, p);
-                    if (cg == 0) {
+                    if (2 * cg < j.n_out) {
                         for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
                         if (lane == 0 && lsum != 0.f) atomicAdd(j.loss, (double)lsum);
                     }
@@ -439,6 +464,7 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                     // them; it accumulates in the other TMEM buffer), then the
                     // embedding gradient, rows of one beam summed over the warp
                     // before the atomic add (each beam's rows lie together)
+                    nxt = load_row(j, tile + gridDim.x, r);
                     if (tile + (int)gridDim.x < j.n_tiles) write_features(j, e, nxt);
                     for (int p = 0; p < 4; ++p) {
                         const int c = p * KP + 16 * cg;
@@ -564,7 +590,9 @@ cudaError_t launch_mlp_chain_tc(const ChainArgs& a, int n_sms, int* d_err, cudaS
              make_map(&maps.st[s], a.dZs[0], H, a.M, H, TM);
     }
     if (!ok) return cudaErrorInvalidValue;
-    const int grid = std::max(1, std::min(n_sms, j.n_tiles));
+    // as few CTAs as keep the most tiles any CTA walks (the others' SMs stay free)
+    const int per_cta = (j.n_tiles + std::max(1, n_sms) - 1) / std::max(1, n_sms);
+    const int grid = std::max(1, (j.n_tiles + per_cta - 1) / per_cta);
     k_mlp_chain<<<grid, THREADS, smem_bytes(j.nslot, D, a.F), st>>>(maps, j, d_err);
     *launches += 1;
     return cudaGetLastError();
