@@ -1097,7 +1097,7 @@ mv_status mv_create(mv_ctx** out, int device, const mv_options* opt) {
     c->device = device;
     c->n_sms = pr.multiProcessorCount;
     if (herk_tc_init() != cudaSuccess || mlp_tc_init() != cudaSuccess || gemm_tc_init() != cudaSuccess ||
-        mlp_chain_init() != cudaSuccess) {
+        mlp_chain_init() != cudaSuccess || wgrad_tc_init() != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return fail(MV_ERR_CUDA, "kernel attribute set-up failed");

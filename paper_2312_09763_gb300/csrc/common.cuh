@@ -290,6 +290,32 @@ cudaError_t mlp_chain_init();
 // number of tiles per CTA).
 cudaError_t launch_mlp_chain_tc(const ChainArgs& a, int n_sms, int* d_err, cudaStream_t st, long long* launches);
 
+// ------------------------------- weight gradients in one launch (mlp_wgrad_tc.cu)
+// dW = A^T X and db = A^T 1 over a batch of kext rows for several layers at
+// once, as FP32 partials per k-split (the batch cut into `splits` ranges).
+// A: dL/dz [kext][lda] (a_rows columns, at least M and 64); X: the layer's
+// input [kext][ldb] (b_rows columns, at least N and 64, N <= 256); BF16,
+// 16-byte aligned rows; rows of either past kext read as zero.  Partial s of
+// dW[m][n] at out + s part_stride + m ldo + n, of db[m] at bias_part + s
+// ldo_bias + m.
+constexpr int kWgradMaxProducts = kChainMaxLayers + 1;
+struct WgradProduct {
+    const __nv_bfloat16* A;
+    long long lda;
+    int a_rows;
+    const __nv_bfloat16* X;
+    long long ldb;
+    int b_rows;
+    int M, N;
+    float* out;
+    long long ldo, part_stride;
+    float* bias_part;
+    long long ldo_bias;
+};
+cudaError_t wgrad_tc_init();
+cudaError_t launch_wgrad_tc(const WgradProduct* p, int n_prod, long long kext, int splits, int n_sms, int* d_err,
+                            cudaStream_t st, long long* launches);
+
 // ------------------------------------- tensor-core products (mlp_train_tc.cu)
 // A BF16 operand of rows (M or N) x kext (K).  K-major (mn = 0): a
 // [rows][ld] array, K contiguous.  MN-major (mn = 1): a [kext][ld] array, the

@@ -455,16 +455,13 @@ cudaError_t forward(Surrogate* S, int rows, bool train, cudaStream_t st, long lo
                           S->n_sms, S->err, st, L);
 }
 
-// k-splits of a weight-gradient product over `rows` rows: pieces of at least
-// 512 rows, at most kMaxSplits.
-int grad_splits(int rows) {
-    const int kb = (rows + 63) / 64;
-    return std::max(1, std::min(kMaxSplits, (kb + 7) / 8));
+// k-splits of the weight-gradient products over `rows` rows on `sms` SMs:
+// one unit (128-row tile of a product, k-split) per SM, at most kMaxSplits.
+int grad_splits(const Surrogate* S, int rows, int sms) {
+    const int tiles = 1 + S->d.depth * ((S->d.H + 127) / 128);
+    const int kb = (std::max(rows, 64) + 63) / 64;
+    return std::max(1, std::min({kMaxSplits, kb, sms / tiles}));
 }
-
-// Partial rows of the bias gradients: one per k-split of the weight-gradient
-// products.
-int bias_rows(const Surrogate*, int rows) { return grad_splits(rows); }
 
 // Input gradients for the batch left by forward(train = true), product by
 // product: dz_{D-1} = (dY W_out) * (h_{D-1} > 0), dz_{l-1} = (dz_l W_l) *
@@ -520,9 +517,21 @@ cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, int sms, cudaStrea
     // K extent of the products (the batch; TMA reads rows past it as zeros), at
     // least one 64-row box
     const long long kext = std::max(rows, 64);
-    const int splits = grad_splits(rows);
+    const int splits = grad_splits(S, rows, sms);
     cudaError_t e = cudaSuccess;
-    {
+    if (D + 1 <= kWgradMaxProducts && H <= 256) {
+        // every product in one launch
+        WgradProduct w[kWgradMaxProducts];
+        w[0] = WgradProduct{S->dY, 64, 64, S->Hs[D - 1], H, H, 16, H, S->part + S->tab.part_off[D], H,
+                            S->tab.part_stride[D], S->bpart + S->tab.bias_off[D], 16};
+        for (int l = 0; l < D; ++l) {
+            const int kin = l == 0 ? d.d0p : H;
+            w[1 + l] = WgradProduct{S->dZs[l], H, H, l == 0 ? S->X0 : S->Hs[l - 1], kin, kin, H, kin,
+                                    S->part + S->tab.part_off[l], kin, S->tab.part_stride[l],
+                                    S->bpart + S->tab.bias_off[l], H};
+        }
+        e = launch_wgrad_tc(w, D + 1, kext, splits, sms, S->err, st, L);
+    } else {
         GemmEpi ep{};
         ep.kind = GEPI_F32;
         ep.out = S->part + S->tab.part_off[D];
@@ -532,22 +541,22 @@ cudaError_t weight_grads(Surrogate* S, int rows, bool reduce, int sms, cudaStrea
         ep.ldo_bias = 16;
         e = launch_gemm_tc(opnd(S->dY, 64, 64, kext, 1), opnd(S->Hs[D - 1], H, H, kext, 1), 16, H, splits, false, ep,
                            sms, S->err, st, L);
-    }
-    for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
-        const int kin = l == 0 ? d.d0p : H;
-        const bf16* x = l == 0 ? S->X0 : S->Hs[l - 1];
-        GemmEpi ep{};
-        ep.kind = GEPI_F32;
-        ep.out = S->part + S->tab.part_off[l];
-        ep.ldo = kin;
-        ep.part_stride = S->tab.part_stride[l];
-        ep.bias_part = S->bpart + S->tab.bias_off[l];
-        ep.ldo_bias = H;
-        e = launch_gemm_tc(opnd(S->dZs[l], H, H, kext, 1), opnd(x, kin, kin, kext, 1), H, kin, splits, false, ep,
-                           sms, S->err, st, L);
+        for (int l = D - 1; l >= 0 && e == cudaSuccess; --l) {
+            const int kin = l == 0 ? d.d0p : H;
+            const bf16* x = l == 0 ? S->X0 : S->Hs[l - 1];
+            GemmEpi epl{};
+            epl.kind = GEPI_F32;
+            epl.out = S->part + S->tab.part_off[l];
+            epl.ldo = kin;
+            epl.part_stride = S->tab.part_stride[l];
+            epl.bias_part = S->bpart + S->tab.bias_off[l];
+            epl.ldo_bias = H;
+            e = launch_gemm_tc(opnd(S->dZs[l], H, H, kext, 1), opnd(x, kin, kin, kext, 1), H, kin, splits, false, epl,
+                               sms, S->err, st, L);
+        }
     }
     if (e == cudaSuccess && reduce) {
-        k_reduce_grads<<<dim3(64, D + 1), 256, 0, st>>>(S->tab, S->part, splits, S->bpart, bias_rows(S, rows), S->g);
+        k_reduce_grads<<<dim3(64, D + 1), 256, 0, st>>>(S->tab, S->part, splits, S->bpart, splits, S->g);
         ++*L;
         e = cudaGetLastError();
     }
@@ -918,10 +927,10 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
         a.c2 = 1.f - powf(0.999f, (float)S->adam_k);
         const long long n_emb = S->n_par - S->off_emb;
         const long long max_layer = (long long)std::max(d.d0p, d.H) * (d.H + 1);
-        k_reduce_adam<<<dim3(gridsz(std::max(max_layer, n_emb), 256), d.depth + 2), 256, 0, st>>>(S->tab, S->part, grad_splits(batch), S->bpart,
-                                                              bias_rows(S, batch), S->g, S->off_emb,
-                                                              n_emb, S->p, S->am, S->av, S->pb, d.H, S->wout16,
-                                                              S->woutT, a);
+        const int splits = grad_splits(S, batch, sms);
+        k_reduce_adam<<<dim3(gridsz(std::max(max_layer, n_emb), 256), d.depth + 2), 256, 0, st>>>(
+            S->tab, S->part, splits, S->bpart, splits, S->g, S->off_emb, n_emb, S->p, S->am, S->av, S->pb, d.H,
+            S->wout16, S->woutT, a);
         ++*L;
         e = cudaGetLastError();
     }
