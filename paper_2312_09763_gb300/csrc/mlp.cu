@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "common.cuh"
@@ -346,6 +347,8 @@ struct Surrogate {
     float *az2 = nullptr, *za2 = nullptr, *nu2 = nullptr, *T2 = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_time[2] = {nullptr, nullptr};  // timing of the SM splits (surrogate_train)
+    std::map<int, int> split_of_batch;             // the split timed fastest, per batch size
     bf16* X0 = nullptr;                      // [cap][d0p]
     std::vector<bf16*> Hs;                   // [cap][H]
     bf16* dY = nullptr;                      // [cap][64] (columns past 16 zero)
@@ -760,6 +763,7 @@ void surrogate_destroy(Surrogate* S) {
     for (int i = 0; i < 2; ++i) {
         if (S->ev_ready[i]) cudaEventDestroy(S->ev_ready[i]);
         if (S->ev_free[i]) cudaEventDestroy(S->ev_free[i]);
+        if (S->ev_time[i]) cudaEventDestroy(S->ev_time[i]);
     }
     for (void* q : {(void*)S->p, (void*)S->g, (void*)S->am, (void*)S->av, (void*)S->pb, (void*)S->Bf, (void*)S->loss,
                     (void*)S->err, (void*)S->part, (void*)S->bpart, (void*)S->wout16, (void*)S->woutT})
@@ -863,13 +867,32 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
             e = cudaEventCreateWithFlags(&S->ev_ready[i], cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_free[i], cudaEventDisableTiming);
         }
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreate(&S->ev_time[i]);
         if (e != cudaSuccess) return e;
     }
-    // SMs: the training launches take at most `sms` (a multiple of 16 near
-    // five sixths of them: one CTA per SM each), the sampler of the next step
-    // one block on each of the others (a 1024-thread block does not fit beside
-    // a training CTA, so neither waits for the other)
-    const int sms = std::max(1, std::min(S->n_sms - 1, (S->n_sms * 5 / 6 + 15) / 16 * 16));
+    // SMs: the training launches take at most `sms` (one CTA per SM each), the
+    // sampler of the next step one block on each of the others (a 1024-thread
+    // block does not fit beside a training CTA, so neither waits for the
+    // other).  Candidate splits: the fewest SMs that walk the batch's 128-row
+    // tiles in the fewest rounds (leaving at least 8 to the sampler), every SM
+    // but 8, and the fewest for one round more (more SMs for the sampler).
+    // With enough steps each runs three steps, the last two timed (their
+    // samples drawn beside the same split), and the fastest stays (and is
+    // kept for later calls with this batch size).
+    const int tiles = (batch + 127) / 128;
+    const int most = std::max(1, S->n_sms - 8);
+    auto split_for = [&](int rounds) { return std::min(most, std::max(1, (tiles + rounds - 1) / rounds)); };
+    const int r0 = (tiles + most - 1) / most;
+    int cand[3], nc = 0;
+    for (int b : {split_for(r0), most, split_for(r0 + 1)}) {
+        bool seen = false;
+        for (int i = 0; i < nc; ++i) seen = seen || cand[i] == b;
+        if (!seen) cand[nc++] = b;
+    }
+    const auto known = S->split_of_batch.find(batch);
+    const bool tune = known == S->split_of_batch.end() && nc > 1 && steps >= 3 * nc + 3;
+    int sms = known != S->split_of_batch.end() ? known->second : cand[0], best = 0;
+    float t_best = 0.f;
     // sample sets: set 0 the arrays the training pass reads, set 1 the second
     // one; the pointers swap every step
     int* s_ant[2] = {S->ant, S->ant2};
@@ -897,6 +920,22 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
     if (e == cudaSuccess) e = sample(0, S->n_sms);
     for (int it = 0; it < steps && e == cudaSuccess; ++it) {
         const int k = it & 1;
+        if (tune && it > 0 && it <= 3 * nc && it % 3 == 0) {
+            // steps it - 2 and it - 1 ran candidate it / 3 - 1, timed
+            const int c = it / 3 - 1;
+            float ms = 0.f;
+            e = cudaEventSynchronize(S->ev_time[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, S->ev_time[0], S->ev_time[1]);
+            if (c == 0 || ms < t_best) {
+                t_best = ms;
+                best = c;
+            }
+            sms = it < 3 * nc ? cand[it / 3] : cand[best];
+            if (it == 3 * nc) S->split_of_batch[batch] = sms;
+        }
+        if (e == cudaSuccess && tune && it < 3 * nc && it % 3 == 1) e = cudaEventRecord(S->ev_time[0], st);
+        if (e != cudaSuccess) break;
+        // the next step's sampler runs beside this step's training launches
         if (it + 1 < steps && (e = sample(it + 1, S->n_sms - sms)) != cudaSuccess) break;
         S->ant = s_ant[k];
         S->az = s_az[k];
@@ -933,6 +972,7 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
             S->wout16, S->woutT, a);
         ++*L;
         e = cudaGetLastError();
+        if (e == cudaSuccess && tune && it < 3 * nc && it % 3 == 2) e = cudaEventRecord(S->ev_time[1], st);
     }
     // the arrays back in their places (set 0 first), whatever step ended last
     S->ant = s_ant[0];
