@@ -177,37 +177,39 @@ __device__ __forceinline__ Row load_row(const Job& j, int tile, int r) {
 }
 
 // Features of one row, [sin 2 pi B x, cos 2 pi B x, e_a, 0 ...], into the
-// activation panels; every panel released.  The phase is reduced to [-1/2,
-// 1/2] turn, where the fast sine and cosine are accurate to ~1e-6, far below
-// the BF16 rounding of the features.
+// activation panels; every panel released.  The row's four threads (column
+// groups cg) share it by 8-column chunks: chunk k of the sines and chunk k of
+// the cosines (one sincos per phase) for k = cg, cg + 4, ..., then the
+// embedding and zero chunks likewise.  The phase is reduced to [-1/2, 1/2]
+// turn, where the fast sine and cosine are accurate to ~1e-6, far below the
+// BF16 rounding of the features.
 __device__ __forceinline__ void write_features(const Job& j, const Epi e, const Row w) {
-    for (int p = 0; p < 4; ++p) {
-        const int c = p * KP + 16 * e.cg;
-        if (c < j.d0p) {
-            float v[16];
+    for (int k = e.cg; k < j.F / 8; k += 4) {
+        float sv[8], cv[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int col = c + i;
-                float x = 0.f;
-                if (w.valid) {
-                    if (col < 2 * j.F) {
-                        const float4 b = e.sB[col < j.F ? col : col - j.F];
-                        float ph = b.x * w.x0 + b.y * w.x1 + b.z * w.x2;
-                        ph -= rintf(ph);
-                        x = col < j.F ? __sinf(6.283185307179586f * ph) : __cosf(6.283185307179586f * ph);
-                    } else if (col < 2 * j.F + j.E) {
-                        x = j.p[j.off_emb + (long long)w.a * j.E + (col - 2 * j.F)];
-                    }
-                }
-                v[i] = x;
-            }
-            st_shared_v4(a_chunk(e.act, e.r, c), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                         pack_bf16(v[6], v[7]));
-            st_shared_v4(a_chunk(e.act, e.r, c + 8), pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]),
-                         pack_bf16(v[12], v[13]), pack_bf16(v[14], v[15]));
+        for (int i = 0; i < 8; ++i) {
+            const float4 b = e.sB[8 * k + i];
+            float ph = b.x * w.x0 + b.y * w.x1 + b.z * w.x2;
+            ph -= rintf(ph);
+            __sincosf(6.283185307179586f * ph, &sv[i], &cv[i]);
+            if (!w.valid) sv[i] = cv[i] = 0.f;
         }
-        arrive_panel(e, p);
+        st_shared_v4(a_chunk(e.act, e.r, 8 * k), pack_bf16(sv[0], sv[1]), pack_bf16(sv[2], sv[3]),
+                     pack_bf16(sv[4], sv[5]), pack_bf16(sv[6], sv[7]));
+        st_shared_v4(a_chunk(e.act, e.r, j.F + 8 * k), pack_bf16(cv[0], cv[1]), pack_bf16(cv[2], cv[3]),
+                     pack_bf16(cv[4], cv[5]), pack_bf16(cv[6], cv[7]));
     }
+    for (int k = 2 * j.F / 8 + e.cg; k < j.d0p / 8; k += 4) {
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int ce = 8 * k + i - 2 * j.F;  // embedding column
+            v[i] = w.valid && ce < j.E ? j.p[j.off_emb + (long long)w.a * j.E + ce] : 0.f;
+        }
+        st_shared_v4(a_chunk(e.act, e.r, 8 * k), pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                     pack_bf16(v[6], v[7]));
+    }
+    for (int p = 0; p < 4; ++p) arrive_panel(e, p);
 }
 
 // One 16-column chunk of a hidden layer's accumulator: bias and ReLU into the
@@ -222,12 +224,14 @@ __device__ __forceinline__ uint32_t emit_relu(const Epi e, int c, const float* b
         h[2 * q] = relu_bf16x2(__uint_as_float(a[4 * q]) + b.x, __uint_as_float(a[4 * q + 1]) + b.y);
         h[2 * q + 1] = relu_bf16x2(__uint_as_float(a[4 * q + 2]) + b.z, __uint_as_float(a[4 * q + 3]) + b.w);
     }
+    // a ReLU output is positive exactly when its BF16 bits, sign cleared, are
+    // not zero: adding 0x7FFF to each 16-bit half then sets its top bit (no
+    // carry between the halves), which lands at bit 2k (low half) or 16 + 2k
+    // (high half) of `lo`
+    uint32_t lo = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        // a ReLU output is positive exactly when its BF16 bits are not zero
-        bits |= (uint32_t)((h[k] & 0xFFFFu) != 0u) << (2 * k);
-        bits |= (uint32_t)(h[k] > 0xFFFFu) << (2 * k + 1);
-    }
+    for (int k = 0; k < 8; ++k) lo |= (((h[k] & 0x7FFF7FFFu) + 0x7FFF7FFFu) & 0x80008000u) >> (15 - 2 * k);
+    bits = (lo & 0x5555u) | ((lo >> 15) & 0xAAAAu);
     st_shared_v4(a_chunk(e.act, e.r, c), h[0], h[1], h[2], h[3]);
     st_shared_v4(a_chunk(e.act, e.r, c + 8), h[4], h[5], h[6], h[7]);
     return bits;
@@ -295,6 +299,7 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
         if (lane == 0) {
             int it = 0;
             bool ok = true;
+            const uint64_t keep = policy_evict_last();  // the weights stay in L2 for every tile
             for (int tile = blockIdx.x; tile < j.n_tiles && ok; tile += gridDim.x)
                 for (int s = 0; s < NS && ok; ++s) {
                     const int np = (j.K[s] + KP - 1) / KP;
@@ -305,7 +310,7 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                             break;
                         }
                         mbar_expect_tx(WFULL + 8u * sl, (uint32_t)(j.wrows[s] * 128));
-                        tma_load_2d(ring + sl * W_SLOT, &maps.w[s], p * KP, 0, WFULL + 8u * sl);
+                        tma_load_2d_hint(ring + sl * W_SLOT, &maps.w[s], p * KP, 0, WFULL + 8u * sl, keep);
                     }
                 }
         }
@@ -390,7 +395,16 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
         if (tile < j.n_tiles) write_features(j, e, cur);
         for (; tile < j.n_tiles && ok; tile += gridDim.x) {
             const long long m = (long long)tile * TM + r;
-            Row nxt{};
+            // read ahead: the next tile's sample (its features are written at this
+            // tile's last step; its embedding row fetched into L1 now) and this
+            // row's targets (the loss step)
+            const Row nxt = load_row(j, tile + gridDim.x, r);
+            if (nxt.valid) asm volatile("prefetch.global.L1 [%0];" ::"l"(j.p + j.off_emb + (long long)nxt.a * j.E));
+            float tg0 = 0.f, tg1 = 0.f;
+            if (cur.valid && 2 * cg < j.n_out) {
+                tg0 = j.T[m * j.n_out + 2 * cg];
+                tg1 = j.T[m * j.n_out + 2 * cg + 1];
+            }
             for (int s = 0; s < NS; ++s, ++g) {
                 const int buf = g & 1;
                 if (!wait_bounded(DFULL + 8u * buf, (uint32_t)(g >> 1) & 1u, abort_flag, err, kTimeoutNs, 1000u) ||
@@ -438,9 +452,8 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                         tmem_wait_ld2(a2);
                         float g0 = 0.f, g1 = 0.f;
                         if (cur.valid) {
-                            const float t0 = j.T[m * j.n_out + 2 * cg], t1 = j.T[m * j.n_out + 2 * cg + 1];
-                            const float r0 = __uint_as_float(a2[0]) + sbias[D * 256 + 2 * cg] - t0;
-                            const float r1 = __uint_as_float(a2[1]) + sbias[D * 256 + 2 * cg + 1] - t1;
+                            const float r0 = __uint_as_float(a2[0]) + sbias[D * 256 + 2 * cg] - tg0;
+                            const float r1 = __uint_as_float(a2[1]) + sbias[D * 256 + 2 * cg + 1] - tg1;
                             lsum = r0 * r0 + r1 * r1;
                             g0 = j.gscale * r0;
                             g1 = j.gscale * r1;
@@ -464,7 +477,6 @@ k_mlp_chain(const __grid_constant__ Maps maps, const __grid_constant__ Job j, in
                     // them; it accumulates in the other TMEM buffer), then the
                     // embedding gradient, rows of one beam summed over the warp
                     // before the atomic add (each beam's rows lie together)
-                    nxt = load_row(j, tile + gridDim.x, r);
                     if (tile + (int)gridDim.x < j.n_tiles) write_features(j, e, nxt);
                     for (int p = 0; p < 4; ++p) {
                         const int c = p * KP + 16 * cg;
