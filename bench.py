@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=611,
                     help="learned workload: Adam steps (default 611 of 16384 samples, i.e. 1e7 samples)")
     ap.add_argument("--train-batch", type=int, default=16384, help="learned workload: samples per Adam step")
+    ap.add_argument("--train-peak-batch", type=int, default=65536,
+                    help="learned workload: batch of the training-throughput measurement (100 steps, learning rate 1e-12)")
     ap.add_argument("--no-fuse", action="store_true", help="Z build as its own launch (mv_options.fuse_zbuild = 0)")
     ap.add_argument("--herk-config", default=None, metavar="BN,SPLIT,FLUSH",
                     help="fix the tensor-core HERK tile width, split-K and flush interval (skips autotune)")
@@ -131,6 +133,12 @@ def workload(args):
         return synth.polarised_diffuse()
     if args.workload == "uneven":
         return synth.batched_uneven()
+    if args.workload == "learned" and args.small:
+        # profiling captures: 2 channels, grids over 148-152 MHz (~1.1 GB)
+        w = synth.learned_beam(n_chan=2, n_times=1, nu_lo=148e6, nu_hi=152e6)
+        w.freqs = 149.5e6 + np.arange(2) * 1e6
+        w.name = w.name.replace("x 2 ch x 1 t", "x 2 ch (149.5-150.5 MHz) x 1 t")
+        return w
     if args.workload == "learned":
         # one LST x 8 channels (146.5-153.5 MHz) of the learned-beam workload;
         # per-antenna grids over 143-157 MHz cover the cubic stencil
@@ -364,10 +372,22 @@ def main():
         torch.cuda.synchronize()
         grid_ms = g0.elapsed_time(g1) / 2
         grid_bytes, sur_bytes = sim.beam_model_bytes()
+        # training throughput at a large batch: the same training steps with a
+        # vanishing learning rate (the trained network stays as it is); the
+        # first call picks the SM split between the training launches and the
+        # sampler
+        pb = args.train_peak_batch
+        sim.surrogate_train(steps=12, batch=pb, lr0=1e-12, lr1=0.0, seed=5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.surrogate_train(steps=100, batch=pb, lr0=1e-12, lr1=0.0, seed=6)
+        torch.cuda.synchronize()
+        t_peak = time.perf_counter() - t0
         sim.set_beam_surrogate(True)
         n_samp = args.train_steps * args.train_batch
         learned = {"train_samples": n_samp, "train_batch": args.train_batch, "train_s": t_train,
                    "train_samples_per_s": n_samp / t_train, "loss_first": l0, "loss_last": l1,
+                   "train_peak_batch": pb, "train_peak_samples_per_s": 100 * pb / t_peak,
                    "grid_ms_per_instance": grid_ms / n_instances(w, pairs),
                    "grid_beam_bytes": grid_bytes, "surrogate_beam_bytes": sur_bytes}
     N = w.n_ant

@@ -11,11 +11,15 @@
 //   f = [sin(2 pi B x), cos(2 pi B x), e_a]  (B: F x 3, az column integer)
 //   h_l = relu(W_l h_{l-1} + b_l), y = W_out h_L + b_out;  MSE loss; Adam.
 // Every matrix product of a training step runs on the tcgen05 tensor cores
-// (mlp_train_tc.cu: BF16 operands staged by TMA, FP32 accumulation in TMEM,
-// fused epilogues); master weights and Adam state are FP32.  The weight
-// gradients dW = dZ^T X read dZ and X batch-major (MN-major operands) and get
-// the bias gradients as row sums of dZ^T from an extra MMA; the input
-// gradients read BF16 copies of W^T that the optimiser keeps.
+// (BF16 operands staged by TMA, FP32 accumulation in TMEM); master weights and
+// Adam state are FP32.  A step is one fused launch for the row-local part
+// (mlp_chain_tc.cu: features, forward, loss, input gradients, embedding
+// gradient), one for every weight and bias gradient (mlp_wgrad_tc.cu: dW =
+// dZ^T X with dZ and X read batch-major, the bias gradients as row sums of
+// dZ^T from an extra MMA) and the optimiser step, while the next step's
+// samples are drawn on a side stream (networks the fused launch does not
+// cover run product by product, mlp_train_tc.cu); the input gradients read
+// BF16 copies of W^T that the optimiser keeps.
 #include <cuda_bf16.h>
 
 #include <algorithm>
