@@ -1,5 +1,7 @@
-// mlp_train_tc.cu -- the matrix products of the learned beam's training (and
-// of its batched evaluation) on the sm_103a tensor cores.
+// mlp_train_tc.cu -- the learned beam's network one matrix product per launch
+// on the sm_103a tensor cores: its batched evaluation, and the training of
+// network shapes that the fused training pass (mlp_chain_tc.cu) and the
+// one-launch weight gradients (mlp_wgrad_tc.cu) do not cover.
 //
 // Every product of the network's forward and backward pass is written as
 //     D[M][N] = A[M][K] B[N][K]^T
