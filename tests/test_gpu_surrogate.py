@@ -77,6 +77,13 @@ def test_gradients_match_oracle_network():
     (1000, dict()),
     # a width that is not a multiple of 64: the product-by-product path
     (600, dict(n_freq=16, emb_dim=8, width=80, depth=3)),
+    # the fused pass at its edges: one full tile plus 8 rows, width 128, one
+    # hidden layer, 24 frequencies (sine and cosine chunks unevenly spread);
+    # width 192 and the deepest fused network (5 layers: 6 weight-gradient
+    # products in one launch); exactly one tile
+    (136, dict(n_freq=24, emb_dim=8, width=128, depth=1)),
+    (304, dict(n_freq=32, emb_dim=16, width=192, depth=5)),
+    (128, dict()),
 ])
 def test_gradients_match_oracle_network_shapes(n, cfg):
     w = workload()
