@@ -34,21 +34,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) per instance of k_herk_tc<128> on the 350-antenna,
-# 1e5-source workload in FP16x3: one ncu capture of 16 instances (2.4458 GB),
+# 1e5-source workload in FP16x3: one ncu capture of 16 instances (2.4452 GB),
 # summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
-HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0178e9) / 16
+HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0172e9) / 16
 # The same for the HERK launch that also builds the next batch's U planes
-# (k_herk_tc<128, 2, 1, 1>): 2.5140 GB read + 2.2649 GB written for 16 + 16
+# (k_herk_tc<128, 2, 1, 1>): 2.5160 GB read + 2.2651 GB written for 16 + 16
 # instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
-FUSED_DRAM_BYTES_PER_INSTANCE = (2.5140e9 + 2.2649e9) / 16
+FUSED_DRAM_BYTES_PER_INSTANCE = (2.5160e9 + 2.2651e9) / 16
 # k_mlp_wa on the learned-beam sample (one launch = one instance of 350 beams x
-# 50,013 live sources): 2.9 MB read + 501.5 MB written, summarised in
+# 50,013 live sources): 3.4 MB read + 500.3 MB written, summarised in
 # profiles/k_mlp_wa_learned_350beams_1e5src.txt.
-MLP_DRAM_BYTES_PER_LAUNCH = 2.920e6 + 501.452e6
-# k_herk_tc<128> over the redundant-group cover of the same workload: 2.3151 GB
-# read + 43.1 MB written for 16 instances, summarised in
+MLP_DRAM_BYTES_PER_LAUNCH = 3.421e6 + 500.320e6
+# k_herk_tc<128> over the redundant-group cover of the same workload: 2.3149 GB
+# read + 43.3 MB written for 16 instances, summarised in
 # profiles/k_herk_tc_redundant_cover_350ant_1e5src_16ch.txt.
-UNIQUE_DRAM_BYTES_PER_INSTANCE = (2.3151e9 + 0.0431e9) / 16
+UNIQUE_DRAM_BYTES_PER_INSTANCE = (2.3149e9 + 0.0433e9) / 16
 METRIC = "vis/s (bl·chan·time) at 350 ant×1e5 src; split-prec TC vs FP32 @1e-5 rel err"
 UNIT = "vis/s"
 

@@ -1,9 +1,9 @@
 // sample.cuh -- the training samples of the learned beam: where a sample
 // lies (beam, az, za, nu) and its target, the gridded beam's own Keys-cubic
-// interpolation (Sec. 2.4 of arXiv:2312.09763).  Shared by the stand-alone
-// sampler (mlp.cu) and the fused training pass (mlp_chain_tc.cu, whose
-// sampler warps draw the next step's samples), which draw the same samples
-// from the same counters.
+// interpolation (Sec. 2.4 of arXiv:2312.09763).  Used by the sampler kernel
+// of mlp.cu, which draws the next training step's samples on the SMs the
+// fused training pass leaves free; every sample comes from its own counters,
+// so a batch is the same whichever SMs draw it.
 #pragma once
 #include "common.cuh"
 
