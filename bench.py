@@ -42,9 +42,9 @@ HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0172e9) / 16
 # instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
 FUSED_DRAM_BYTES_PER_INSTANCE = (2.5160e9 + 2.2651e9) / 16
 # k_mlp_wa on the learned-beam sample (one launch = one instance of 350 beams x
-# 50,013 live sources): 3.4 MB read + 500.3 MB written, summarised in
-# profiles/k_mlp_wa_learned_350beams_1e5src.txt.
-MLP_DRAM_BYTES_PER_LAUNCH = 3.421e6 + 500.320e6
+# 50,013 live sources): None until the counters of the current kernel are
+# taken (profiles/k_mlp_wa_learned_350beams_1e5src.txt).
+MLP_DRAM_BYTES_PER_LAUNCH = None
 # k_herk_tc<128> over the redundant-group cover of the same workload: 2.3149 GB
 # read + 43.3 MB written for 16 instances, summarised in
 # profiles/k_herk_tc_redundant_cover_350ant_1e5src_16ch.txt.
@@ -517,23 +517,29 @@ def main():
                        "unique_vis_per_s": world * n_unique * nf * nf * n_instances(w, pairs) * args.steps
                        / (ms_max / 1e3)}
     if learned is not None:
-        # the surrogate's forward pass dominates: 2 x multiply-adds per row of
-        # the network, one row per (antenna beam, live source) of each instance
+        # the surrogate's forward pass dominates: one row of the network per
+        # (antenna beam, live source) of each instance.  The first layer's
+        # Fourier part is the same for every beam and is computed once per
+        # live source (k_src_first); the rest of the network per row (k_mlp_wa)
         _, _, lay = sim.surrogate_params()
         F, E, H, D = (sim._mlp[k] for k in ("n_freq", "emb_dim", "width", "depth"))
         d0p = int(lay[-1])
-        macs = d0p * H + (D - 1) * H * H + H * 8
+        macs_row = (D - 1) * H * H + H * 8
+        macs_src = 2 * F * H
         rows_step = float(np.sum(live.astype(np.float64) * w.n_ant))
+        src_step = float(np.sum(live.astype(np.float64)))
         n_b, ms_b = prof["beam"]
-        mlp_tf = 2.0 * macs * rows_step * args.steps / (ms_b / 1e3) / 1e12
+        mlp_tf = 2.0 * (macs_row * rows_step + macs_src * src_step) * args.steps / (ms_b / 1e3) / 1e12
         err = float((V - Vg).abs().max() / Vg.abs().max())
-        learned.update({"network_rows_per_step": rows_step, "flop_per_row": 2 * macs,
+        learned.update({"network_rows_per_step": rows_step, "flop_per_row": 2 * macs_row,
+                        "flop_per_source": 2 * macs_src,
+                        "flop_per_row_unshared": 2 * (d0p * H + (D - 1) * H * H + H * 8),
                         "surrogate_vs_grid_rel_err": err,
                         "surrogate_ms_per_instance": ms_max / args.steps / n_instances(w, pairs)})
         roof = {"bound": "tensor", "achieved": mlp_tf, "peak": sustained, "unit": "TFLOP/s",
                 "frac": mlp_tf / sustained,
                 "traffic": MLP_DRAM_BYTES_PER_LAUNCH, "traffic_unit": "B per launch",
-                "kernel": "k_mlp_wa (learned-beam forward + WA, tcgen05)",
+                "kernel": "k_mlp_wa (learned-beam forward + WA, tcgen05; FLOPs as executed, with k_src_first)",
                 "launches": n_b, "avg_launch_ms": ms_b / max(n_b, 1),
                 "peak_source": f"{src} bf16 sustained (kernels timed inside a long step)"}
     metric = METRIC if n_unique is None else \

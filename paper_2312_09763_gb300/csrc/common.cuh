@@ -243,12 +243,20 @@ struct MlpTcArgs {
     long long off_w[9], off_b[9];  // per layer: hidden layers, then the output layer
     long long off_emb;
     const float* Bf;              // Fourier matrix [F][3]
+    float* P;                     // per live source: W_0's Fourier columns times the features
+                                  // (mlp_tc_first_floats(H, live count) floats)
+    float* C;                     // per beam: W_0's embedding columns times e_b, plus b_0 ([n_beam][H])
 };
 // Whether the tensor-core forward pass handles this network shape.
 bool mlp_tc_supported(int F, int E, int H, int depth, int d0p, int n_out);
 cudaError_t mlp_tc_init();
+// Floats of MlpTcArgs::P for instances of up to max_live live sources.
+long long mlp_tc_first_floats(int H, long long max_live);
+// MlpTcArgs::C from the current parameters (once per set of parameters).
+cudaError_t launch_mlp_beam_first(const MlpTcArgs& a, cudaStream_t st, long long* launches);
 // WA of one instance (live count K at time index t, frequency nu) from the
 // network: rows (beam b, source s), b < n_beam; WA[b][comp][s] as launch_wa.
+// Computes the instance's P, then runs the fused pass; C must be current.
 cudaError_t launch_mlp_wa_tc(const MlpTcArgs& a, const Model& m, LiveTables lt, int t, int K, float nu,
                              float ln_ratio, float2* wa_slot, long long wa_pitch, float* amax, int* d_err,
                              int n_sms, cudaStream_t st, long long* launches);

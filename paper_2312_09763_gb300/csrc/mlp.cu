@@ -353,6 +353,11 @@ struct Surrogate {
     cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     cudaEvent_t ev_time[2] = {nullptr, nullptr};  // timing of the SM splits (surrogate_train)
     std::map<int, int> split_of_batch;             // the split timed fastest, per batch size
+    // the fused forward pass's first-layer products (mlp_tc.cu): per live
+    // source of one instance (capacity first_cap floats) and per beam
+    float* first_P = nullptr;
+    float* first_C = nullptr;
+    long long first_cap = 0;
     bf16* X0 = nullptr;                      // [cap][d0p]
     std::vector<bf16*> Hs;                   // [cap][H]
     bf16* dY = nullptr;                      // [cap][64] (columns past 16 zero)
@@ -770,7 +775,8 @@ void surrogate_destroy(Surrogate* S) {
         if (S->ev_time[i]) cudaEventDestroy(S->ev_time[i]);
     }
     for (void* q : {(void*)S->p, (void*)S->g, (void*)S->am, (void*)S->av, (void*)S->pb, (void*)S->Bf, (void*)S->loss,
-                    (void*)S->err, (void*)S->part, (void*)S->bpart, (void*)S->wout16, (void*)S->woutT})
+                    (void*)S->err, (void*)S->part, (void*)S->bpart, (void*)S->wout16, (void*)S->woutT,
+                    (void*)S->first_P, (void*)S->first_C})
         sfree(q);
     for (auto* w : S->wt) sfree(w);
     delete S;
@@ -1003,18 +1009,37 @@ cudaError_t surrogate_wa(Surrogate* S, const Model& m, const std::vector<Inst>& 
     const Dims& d = S->d;
     const int ncomp = m.n_feed * m.n_ax;
     const long long chunk = 1 << 19;
-    // the fused tensor-core forward pass (features, layers and WA in one
-    // launch per instance) where the network shape allows, else the network's
+    // the fused tensor-core forward pass (the first layer's source and beam
+    // parts computed once each, then the layers and WA in one launch per
+    // instance) where the network shape allows, else the network's
     // layer-by-layer tensor-core products
     const bool tc = mlp_tc_supported(d.F, d.E, d.H, d.depth, d.d0p, d.n_out);
     MlpTcArgs ta{};
+    cudaError_t e = cudaSuccess;
     if (tc) {
         ta.F = d.F; ta.E = d.E; ta.H = d.H; ta.depth = d.depth; ta.d0p = d.d0p; ta.n_beam = d.n_ant;
         ta.n_out = d.n_out; ta.nu_mid = d.nu_mid; ta.nu_half = d.nu_half;
         ta.p = S->p; ta.pb = S->pb; ta.off_emb = S->off_emb; ta.Bf = S->Bf;
         for (int l = 0; l <= d.depth; ++l) { ta.off_w[l] = S->off_w[l]; ta.off_b[l] = S->off_b[l]; }
+        // the first-layer products: P per live source (grown to the largest
+        // live count of the call), C per beam from the current parameters
+        long long max_live = 0;
+        for (int j = 0; j < n_inst; ++j) max_live = std::max(max_live, (long long)h_nlive[h_inst[inst0 + j].t]);
+        const long long need = mlp_tc_first_floats(d.H, max_live);
+        if (need > S->first_cap) {
+            sfree(S->first_P);
+            S->first_P = nullptr;
+            S->first_cap = 0;
+            e = cudaMalloc((void**)&S->first_P, sizeof(float) * (size_t)need);
+            if (e == cudaSuccess) S->first_cap = need;
+        }
+        if (e == cudaSuccess && !S->first_C) e = cudaMalloc((void**)&S->first_C, sizeof(float) * (size_t)d.n_ant * d.H);
+        ta.P = S->first_P;
+        ta.C = S->first_C;
+        if (e == cudaSuccess) e = launch_mlp_beam_first(ta, st, L);
+    } else {
+        e = ensure_rows(S, chunk);
     }
-    cudaError_t e = tc ? cudaSuccess : ensure_rows(S, chunk);
     for (int j = 0; j < n_inst && e == cudaSuccess; ++j) {
         const Inst& in = h_inst[inst0 + j];
         const int K = h_nlive[in.t];
