@@ -207,55 +207,49 @@ __global__ void k_beam_first(SrcArgs a, int E, const float* __restrict__ p, long
 // loads its source's 16 values of P once (a warp reads 512 contiguous bytes
 // per float4 column group, and the tile's P block is read once) and adds the
 // beams' C values, which are the same for every lane (broadcast loads).
-// first_load issues the P loads while the previous tile's output layer
-// runs; first_stage copies the warp's slices of the beams' C rows into
-// shared memory (a tile ahead, with cp.async: one 16-byte piece per lane);
-// first_store writes the panels.
-struct FirstSlice {
-    int g, j0, dj;  // column group, first beam and beam stride of an epilogue warp
-};
-__device__ __forceinline__ FirstSlice first_slice(int ew, int H) {
-    const int ng = H / 16;
-    return FirstSlice{ew % ng, ew / ng, 16 / ng};
-}
-__device__ __forceinline__ void first_load(FirstSlice f, int lane, int H, int s0, int K, const float* __restrict__ P,
-                                           float4 (&pv)[4]) {
-    const int c0 = 16 * f.g;
-    const bool svalid = s0 + lane < K;
-    const float* pr = P + ((long long)(s0 / SRC_BLK) * H * SRC_BLK + lane * 4);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        pv[i] = svalid ? __ldg(reinterpret_cast<const float4*>(pr + (long long)(c0 / 4 + i) * (SRC_BLK * 4)))
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-}
-// cs: C rows in shared memory, [8][256] floats
-__device__ __forceinline__ void first_stage(FirstSlice f, int lane, int H, int b0, int n_beam,
+// Each sub-tile's 8 epilogue warps write its h_1 (4 beams x 32 sources):
+// warp w (0..7) takes the 16-column groups g = w, w + 8, ... below H / 16,
+// for the sub-tile's 4 beams.  first_stage copies the warp's slices of the
+// beams' C rows into shared memory a tile ahead (cp.async, 16 bytes per
+// lane); first_store loads the sources' P values per group (a warp reads 512
+// contiguous bytes per float4 column group) and writes the panels.
+// cs: C rows of the tile's 8 beams in shared memory, [8][256] floats.
+__device__ __forceinline__ void first_stage(int w, int u, int lane, int H, int b0, int n_beam,
                                             const float* __restrict__ C, float* cs) {
-    const int j = f.j0 + (lane >> 2) * f.dj, c = 16 * f.g + 4 * (lane & 3);
-    if (j < 8 && b0 + j < n_beam)
+    const int g = w + 8 * (lane >> 4), jj = (lane >> 2) & 3, c = 16 * g + 4 * (lane & 3);
+    const int j = 4 * u + jj;
+    if (16 * g < H && b0 + j < n_beam)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(cs + j * 256 + c)),
                      "l"(C + (long long)(b0 + j) * H + c)
                      : "memory");
 }
-__device__ __forceinline__ void first_store(FirstSlice f, uint32_t a_base, int lane, int b0, int n_beam, int s0,
-                                            int K, const float* cs, const float4 (&pv)[4]) {
-    const int c0 = 16 * f.g;
+__device__ __forceinline__ void first_store(int w, int u, uint32_t ab, int lane, int H, int b0, int n_beam, int s0,
+                                            int K, const float* __restrict__ P, const float* cs) {
     const bool svalid = s0 + lane < K;
-    for (int j = f.j0; j < 8; j += f.dj) {
-        const bool valid = svalid && b0 + j < n_beam;
-        const float4* cr = reinterpret_cast<const float4*>(cs + j * 256 + c0);
-        // row j * 32 + lane of the tile: sub-tile j / 4, row (j % 4) * 32 + lane
-        const uint32_t ab = a_base + (j / 4) * SUB_A;
-        const int r = (j % 4) * 32 + lane;
+    const float* pr = P + ((long long)(s0 / SRC_BLK) * H * SRC_BLK + lane * 4);
+    for (int g = w; 16 * g < H; g += 8) {
+        const int c0 = 16 * g;
+        float4 pv[4];
 #pragma unroll
-        for (int h8 = 0; h8 < 2; ++h8) {
-            const float4 p0 = pv[2 * h8], p1 = pv[2 * h8 + 1];
-            const float4 k0 = valid ? cr[2 * h8] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 k1 = valid ? cr[2 * h8 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            uint32_t w0 = relu_bf16x2(p0.x + k0.x, p0.y + k0.y), w1 = relu_bf16x2(p0.z + k0.z, p0.w + k0.w);
-            uint32_t w2 = relu_bf16x2(p1.x + k1.x, p1.y + k1.y), w3 = relu_bf16x2(p1.z + k1.z, p1.w + k1.w);
-            if (!valid) w0 = w1 = w2 = w3 = 0u;
-            st_shared_v4(a_chunk(ab, r, c0 + 8 * h8), w0, w1, w2, w3);
+        for (int i = 0; i < 4; ++i)
+            pv[i] = svalid ? __ldg(reinterpret_cast<const float4*>(pr + (long long)(c0 / 4 + i) * (SRC_BLK * 4)))
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * u + jj;
+            const bool valid = svalid && b0 + j < n_beam;
+            const float4* cr = reinterpret_cast<const float4*>(cs + j * 256 + c0);
+            const int r = jj * 32 + lane;  // row of the sub-tile
+#pragma unroll
+            for (int h8 = 0; h8 < 2; ++h8) {
+                const float4 p0 = pv[2 * h8], p1 = pv[2 * h8 + 1];
+                const float4 k0 = valid ? cr[2 * h8] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 k1 = valid ? cr[2 * h8 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t w0 = relu_bf16x2(p0.x + k0.x, p0.y + k0.y), w1 = relu_bf16x2(p0.z + k0.z, p0.w + k0.w);
+                uint32_t w2 = relu_bf16x2(p1.x + k1.x, p1.y + k1.y), w3 = relu_bf16x2(p1.z + k1.z, p1.w + k1.w);
+                if (!valid) w0 = w1 = w2 = w3 = 0u;
+                st_shared_v4(a_chunk(ab, r, c0 + 8 * h8), w0, w1, w2, w3);
+            }
         }
     }
 }
@@ -303,13 +297,14 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     float* g_alpha = reinterpret_cast<float*>(sgather + TILE * 16);       // [row of the tile]
     float* c_rows = reinterpret_cast<float*>(sgather + SMEM_GATHER);     // [beam of the tile][256]
     uint64_t* bars = reinterpret_cast<uint64_t*>(sgather + SMEM_GATHER + SMEM_C);
-    // wfull[NSLOT], wfree[NSLOT], afull, dfull, ofull
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT + 3);
+    // wfull[NSLOT], wfree[NSLOT], afull[2], dfull[2], ofull (afull / dfull per sub-tile)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NSLOT + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     auto wfull = [&](int i) { return smem_u32(&bars[i]); };
     auto wfree = [&](int i) { return smem_u32(&bars[NSLOT + i]); };
-    const uint32_t afull = smem_u32(&bars[2 * NSLOT]), dfull = smem_u32(&bars[2 * NSLOT + 1]),
-                   ofull = smem_u32(&bars[2 * NSLOT + 2]);
+    auto afull = [&](int u) { return smem_u32(&bars[2 * NSLOT + u]); };
+    auto dfull = [&](int u) { return smem_u32(&bars[2 * NSLOT + 2 + u]); };
+    const uint32_t ofull = smem_u32(&bars[2 * NSLOT + 4]);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int H = net.H, D = net.depth;
@@ -329,8 +324,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
     }
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSLOT; ++i) { mbar_init(wfull(i), 1); mbar_init(wfree(i), 1); }
-        mbar_init(afull, NEPI);
-        mbar_init(dfull, 1);
+        for (int u = 0; u < 2; ++u) { mbar_init(afull(u), NEPI / 2); mbar_init(dfull(u), 1); }
         mbar_init(ofull, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -351,57 +345,68 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             // output layer once: its 8 rows (one 1 KB swizzle atom per panel)
             mbar_expect_tx(ofull, (uint32_t)(np * (O_PANEL / 2)));
             for (int pnl = 0; pnl < np; ++pnl) tma_load_2d(o_base + pnl * O_PANEL, &maps.w[D], pnl * KP, 0, ofull);
+            // the hidden layers' panels, once for each sub-tile (in the MMA
+            // warp's order), kept in L2 (evict-last) under the stream of WA
+            // stores
+            const uint64_t pol = policy_evict_last();
             int it = 0;  // weight panels streamed so far (ring position)
             bool ok = true;
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
                 for (int l = 1; l < D && ok; ++l)
-                    for (int pnl = 0; pnl < np; ++pnl, ++it) {
-                        const int sl = it % NSLOT;
-                        if (!wait_bounded_spin(wfree(sl), ((uint32_t)(it / NSLOT) & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
-                        mbar_expect_tx(wfull(sl), (uint32_t)w_panel);
-                        tma_load_2d(w_base + sl * W_PANEL_MAX, &maps.w[l], pnl * KP, 0, wfull(sl));
-                    }
+                    for (int u = 0; u < 2 && ok; ++u)
+                        for (int pnl = 0; pnl < np; ++pnl, ++it) {
+                            const int sl = it % NSLOT;
+                            if (!wait_bounded_spin(wfree(sl), ((uint32_t)(it / NSLOT) & 1u) ^ 1u, abort_flag, err)) { ok = false; break; }
+                            mbar_expect_tx(wfull(sl), (uint32_t)w_panel);
+                            tma_load_2d_hint(w_base + sl * W_PANEL_MAX, &maps.w[l], pnl * KP, 0, wfull(sl), pol);
+                        }
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            // layer by layer, sub-tile 0 then sub-tile 1: while one sub-tile's
+            // epilogue drains a layer, the other's MMAs run
             const uint32_t id_hidden = idesc_f16(false, TM, H), id_out = idesc_f16(false, TM, 16);
             int it = 0;
-            int na = 0;
+            int na0 = 0, na1 = 0;
             bool ok = wait_bounded_spin(ofull, 0u, abort_flag, err);
             for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
                 for (int l = 1; l <= D && ok; ++l) {
-                    if (!wait_bounded_spin(afull, (uint32_t)(na++) & 1u, abort_flag, err)) { ok = false; break; }
-                    tc_fence_after();
                     const bool out = l == D;
-                    for (int pnl = 0; pnl < np; ++pnl) {
-                        const int sl = it % NSLOT;
-                        if (!out) {
-                            if (!wait_bounded_spin(wfull(sl), (uint32_t)(it / NSLOT) & 1u, abort_flag, err)) { ok = false; break; }
-                            tc_fence_after();
-                        }
-                        const uint32_t b0 = out ? o_base + pnl * O_PANEL : w_base + sl * W_PANEL_MAX;
-                        // both sub-tiles from the same weight panel (accumulators at columns 0 and 256)
-                        for (int u = 0; u < 2; ++u)
+                    for (int u = 0; u < 2 && ok; ++u) {
+                        const int na = u ? na1++ : na0++;
+                        if (!wait_bounded_spin(afull(u), (uint32_t)na & 1u, abort_flag, err)) { ok = false; break; }
+                        tc_fence_after();
+                        for (int pnl = 0; pnl < np; ++pnl) {
+                            const int sl = it % NSLOT;
+                            if (!out) {
+                                if (!wait_bounded_spin(wfull(sl), (uint32_t)(it / NSLOT) & 1u, abort_flag, err)) { ok = false; break; }
+                                tc_fence_after();
+                            }
+                            const uint32_t b0 = out ? o_base + pnl * O_PANEL : w_base + sl * W_PANEL_MAX;
                             for (int kk = 0; kk < KP / 16; ++kk)
                                 tc_mma(tmem + (uint32_t)(u * 256), sdesc(a_base + u * SUB_A + pnl * A_PANEL + kk * 32),
                                        sdesc(b0 + kk * 32), out ? id_out : id_hidden, (pnl | kk) != 0 ? 1u : 0u);
-                        if (!out) {
-                            tc_commit(wfree(sl));
-                            ++it;
+                            if (!out) {
+                                tc_commit(wfree(sl));
+                                ++it;
+                            }
                         }
+                        if (!ok) break;
+                        tc_commit(dfull(u));
                     }
-                    if (!ok) break;
-                    tc_commit(dfull);
                 }
             }
         }
     } else {
-        // epilogue warps: lane quadrant q, sub-tile u, column half h
+        // epilogue warps: lane quadrant q, sub-tile u, column half h; the
+        // sub-tile's 8 warps are numbered w = (q, h)
         const int q = warp & 3, u = ((warp - 2) >> 2) & 1, h = (warp - 2) >> 3;
+        const int w = ((warp - 2) & 3) + 4 * h;
         const int r_loc = q * 32 + lane;  // row within the sub-tile
         const int row = u * TM + r_loc;   // row within the tile
         const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(u * 256);
         const uint32_t ab = a_base + u * SUB_A;
+        const uint32_t my_afull = afull(u), my_dfull = dfull(u);
         const int half = H / 2, c_beg = h * half;
         const int ncomp = net.n_out / 2;
         int nd = 0;
@@ -414,33 +419,28 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             valid = b < net.n_beam && s < K;
             if (!valid) b = s = 0;
         };
-        // h_1 of a tile into the activation panels (its P values already
-        // loaded into pv), then the MMA warp may go
-        const FirstSlice fsl = first_slice(warp - 2, H);
-        float4 pv[4];
-        auto load_tile = [&](int tile) { first_load(fsl, lane, H, (tile / n_bg) * SRC_BLK, K, net.P, pv); };
         auto stage_tile = [&](int tile) {
-            first_stage(fsl, lane, H, (tile % n_bg) * 8, net.n_beam, net.C, c_rows);
+            first_stage(w, u, lane, H, (tile % n_bg) * 8, net.n_beam, net.C, c_rows);
             cp_async_commit();
         };
-        // (the caller has waited for the tile's staged C rows)
+        // h_1 of the sub-tile into its activation panels, then the MMA warp
+        // may go (the caller has waited for the tile's staged C rows)
         auto start_tile = [&](int tile) {
             __syncwarp();
-            first_store(fsl, a_base, lane, (tile % n_bg) * 8, net.n_beam, (tile / n_bg) * SRC_BLK, K, c_rows, pv);
+            first_store(w, u, ab, lane, H, (tile % n_bg) * 8, net.n_beam, (tile / n_bg) * SRC_BLK, K, net.P, c_rows);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(afull);
+            if (lane == 0) mbar_arrive(my_afull);
         };
         // Per tile: the WA writers (half 0) request their source's flux,
-        // spectral index (and coherency root) once the tile's first product
-        // is done; they land in shared memory while the layers run.  After the
-        // output layer the warps read its accumulator, write the next tile's
-        // h_1 (the MMA warp starts on it), and then scale and store this
-        // tile's WA.
+        // spectral index (and coherency root) once the sub-tile's first
+        // product is done; they land in shared memory while the layers run.
+        // After the output layer the warps read its accumulator, write the
+        // next tile's h_1 (the MMA warp starts on it), and then scale and
+        // store this tile's WA.
         int tile = blockIdx.x;
         if (tile < n_tiles) {
             stage_tile(tile);
-            load_tile(tile);
             cp_async_wait_all();
             start_tile(tile);
         }
@@ -464,21 +464,19 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
             };
             // ---- hidden layers 1 ..: accumulator -> bias, ReLU -> BF16 activations
             for (int l = 1; l < D; ++l) {
-                if (!wait_bounded_spin(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
+                if (!wait_bounded_spin(my_dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
                 tc_fence_after();
                 if (l == 1) gather();
                 drain_layer(trow, ab, r_loc, c_beg, half, sbias + l * 256);
                 tc_fence_before();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(afull);
+                if (lane == 0) mbar_arrive(my_afull);
             }
             if (!ok) break;
-            // ---- output layer: the next tile's P loads go out while its MMAs
-            // run; accumulator -> registers, then the next tile's h_1 (the
-            // accumulator columns are free again), then WA
-            if (next < n_tiles) load_tile(next);
-            if (!wait_bounded_spin(dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
+            // ---- output layer: accumulator -> registers, then the next tile's
+            // h_1 (the accumulator columns are free again), then WA
+            if (!wait_bounded_spin(my_dfull, (uint32_t)(nd++) & 1u, abort_flag, err)) { ok = false; break; }
             tc_fence_after();
             if (D == 1) gather();
             float y[8];
@@ -505,7 +503,7 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                         for (int c = 0; c < 4; ++c)
                             if (c < ncomp) {
                                 const float2 v = make_float2(w * y[2 * c], w * y[2 * c + 1]);
-                                wb[(long long)c * wa_pitch] = v;
+                                __stcs(wb + (long long)c * wa_pitch, v);
                                 mx = fmaxf(mx, hypotf(v.x, v.y));
                             }
                     } else {  // two axes per feed: z = A M (eq. "fullz")
@@ -515,8 +513,8 @@ k_mlp_wa(const __grid_constant__ Maps maps, const __grid_constant__ Net net, Mod
                                 float2 z0, z1;
                                 apply_sky_sqrt(make_float2(y[2 * c], y[2 * c + 1]),
                                                make_float2(y[2 * c + 2], y[2 * c + 3]), gm, spec, z0, z1);
-                                wb[(long long)c * wa_pitch] = z0;
-                                wb[(long long)(c + 1) * wa_pitch] = z1;
+                                __stcs(wb + (long long)c * wa_pitch, z0);
+                                __stcs(wb + (long long)(c + 1) * wa_pitch, z1);
                                 mx = fmaxf(mx, fmaxf(hypotf(z0.x, z0.y), hypotf(z1.x, z1.y)));
                             }
                     }
