@@ -42,9 +42,9 @@ HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0172e9) / 16
 # instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
 FUSED_DRAM_BYTES_PER_INSTANCE = (2.5160e9 + 2.2651e9) / 16
 # k_mlp_wa on the learned-beam sample (one launch = one instance of 350 beams x
-# 50,013 live sources): None until the counters of the current kernel are
-# taken (profiles/k_mlp_wa_learned_350beams_1e5src.txt).
-MLP_DRAM_BYTES_PER_LAUNCH = None
+# 50,013 live sources): 53.7 MB read + 500.0 MB written, summarised in
+# profiles/k_mlp_wa_learned_350beams_1e5src.txt.
+MLP_DRAM_BYTES_PER_LAUNCH = 53.68e6 + 499.97e6
 # k_herk_tc<128> over the redundant-group cover of the same workload: 2.3149 GB
 # read + 43.3 MB written for 16 instances, summarised in
 # profiles/k_herk_tc_redundant_cover_350ant_1e5src_16ch.txt.
