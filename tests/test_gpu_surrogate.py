@@ -181,9 +181,9 @@ def test_surrogate_with_a_polarised_sky():
 
 @pytest.mark.parametrize("polarised", [False, True])
 def test_surrogate_several_tiles_per_sm(polarised):
-    # 48 beams x ~3000 live sources: ~570 tiles of 256 network rows, several per
-    # persistent CTA, so each CTA carries a tile's gathered source data and the
-    # next tile's features across the tile boundary
+    # 48 beams x ~3000 live sources: ~570 tiles of 256 network rows (8 beams x
+    # 32 sources), several per persistent CTA, so each CTA carries a tile's
+    # gathered source data and the next tile's C rows across the tile boundary
     w = workload(n_ant=48, n_src=6000)
     if polarised:
         g = np.random.default_rng(8)
@@ -209,6 +209,37 @@ def test_surrogate_several_tiles_per_sm(polarised):
         return out
     Vo = oracle.vis_with_beam_fn(P, w.lsts[0], f, beam_fn)
     assert rel_err(V[0, 1], Vo) <= 3e-2
+
+
+@pytest.mark.parametrize("n_ant,cfg", [
+    # one hidden layer: the fused pass goes from h_1 = relu(P + C) straight to
+    # the output layer; width 128 (two 64-column halves per warp)
+    (13, dict(n_freq=16, emb_dim=8, width=128, depth=1)),
+    # width 128 with three hidden layers; 13 beams: a partly filled 8-beam group
+    (13, dict(n_freq=24, emb_dim=8, width=128, depth=3)),
+])
+def test_simulate_with_other_network_shapes(n_ant, cfg):
+    w = workload(n_ant=n_ant, n_src=3000)
+    sim = simulator(w)
+    sim.surrogate_create(**cfg)
+    sim.surrogate_train(steps=100, batch=4096, lr0=2e-3, lr1=1e-4, seed=2)
+    net = oracle_net(sim, *grid_meta(w))
+    sim.set_beam_surrogate(True)
+    V = sim.simulate(w.lsts, w.freqs, "fp16x3").cpu().numpy()
+    live = int(sim.last_live_counts(len(w.lsts) * len(w.freqs))[0])
+    assert live % 32 != 0  # a partly filled 32-source block
+    P = oracle_problem(w)
+    f = w.freqs[0]
+
+    def beam_fn(az, za, nu):
+        n = az.size
+        out = np.empty((w.n_ant, 2, 2, n), dtype=np.complex128)
+        for b in range(w.n_ant):
+            y = mlp.forward(net, np.full(n, b), az, za, np.full(n, nu))
+            out[b] = (y[:, 0::2] + 1j * y[:, 1::2]).T.reshape(2, 2, n)
+        return out
+    Vo = oracle.vis_with_beam_fn(P, w.lsts[0], f, beam_fn)
+    assert rel_err(V[0, 0], Vo) <= 3e-2
 
 
 def test_what_the_surrogate_gains_over_per_antenna_grids():
