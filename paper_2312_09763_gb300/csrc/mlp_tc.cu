@@ -21,19 +21,22 @@
 // C_b): the Fourier features and the first layer's products are not
 // repeated for each of the n_beam beams.
 //
-// One persistent CTA per SM walks 256-row tiles made of two 128-row
-// sub-tiles with their own activation panels and TMEM accumulators (columns 0
-// and 256), so that every weight panel feeds the MMAs of both.  A tile holds
-// 8 beams x 32 consecutive live sources (one beam per warp of 32 rows): the
-// warps of a tile read the same 32 sources' P (from L1 after the first), and
-// each warp's WA rows are 32 consecutive sources of one beam.  Warp 0 streams
-// the weight panels of layers 1.. (64 input columns x H rows, 128-byte
-// swizzle) with TMA through a ring of two slots; warp 1 owns TMEM and issues
-// the MMAs (M = 128, N = H, K = 16); warps 2..17 (one per TMEM lane quadrant,
-// sub-tile and half of the columns) write h_1 from P and C, drain each later
-// layer's accumulator through bias and ReLU back into the shared-memory
-// activation panels, and write WA from the output layer.  Every mbarrier wait
-// is bounded (tc.cuh).
+// One persistent CTA per SM walks 256-row tiles of 8 beams x 32 consecutive
+// live sources (one beam per 32 rows), held as two 128-row sub-tiles with
+// their own activation panels, TMEM accumulators (columns 0 and 256) and
+// barriers.  The sub-tiles take turns on the tensor pipe: warp 1 (which owns
+// TMEM) issues one sub-tile's layer (M = 128, N = H, K = 16) while the other
+// sub-tile's 8 epilogue warps drain its previous layer through bias and ReLU
+// back into its shared-memory activation panels, so the tensor pipe does not
+// wait for an epilogue.  Warp 0 streams each layer's weight panels (64 input
+// columns x H rows, 128-byte swizzle, kept in L2) with TMA through a ring of
+// two slots, once per sub-tile.  A sub-tile's 8 warps (one per TMEM lane
+// quadrant and half of the columns) also write its h_1 -- split by 16-column
+// groups, each lane loading its source's P values once for the sub-tile's 4
+// beams and the beams' C from shared memory, where it was staged a tile
+// ahead -- and, after the output layer, its WA: 32 consecutive sources of one
+// beam per warp, with streaming stores.  Every mbarrier wait is bounded
+// (tc.cuh).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -46,7 +49,7 @@ namespace {
 using namespace tc;
 
 constexpr int TM = 128;          // rows per sub-tile (one TMEM accumulator)
-constexpr int TILE = 2 * TM;     // rows per tile: two sub-tiles share every weight panel
+constexpr int TILE = 2 * TM;     // rows per tile: two sub-tiles
 constexpr int KP = 64;           // input columns per swizzled panel (128 B of BF16)
 constexpr int MAXL = 8;          // hidden layers at most
 constexpr int A_PANEL = TM * 128;                // 16 KB
