@@ -38,9 +38,11 @@ sys.path.insert(0, ROOT)
 # summarised in profiles/k_herk_tc_350ant_1e5src_16ch.txt.
 HERK_DRAM_BYTES_PER_INSTANCE = (2.4280e9 + 0.0172e9) / 16
 # The same for the HERK launch that also builds the next batch's U planes
-# (k_herk_tc<128, 2, 1, 1>): 2.5160 GB read + 2.2651 GB written for 16 + 16
-# instances, summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
-FUSED_DRAM_BYTES_PER_INSTANCE = (2.5160e9 + 2.2651e9) / 16
+# (k_herk_tc<128, 2, 1, 1>) in the configuration the autotuner keeps on the
+# 350-antenna workload (128 columns, split 4, flush 16): 2.5270 GB read +
+# 2.3306 GB written for 16 + 16 instances (split-K partial tiles included),
+# summarised in profiles/k_herk_tc_fused_zbuild_350ant_1e5src_2x16ch.txt.
+FUSED_DRAM_BYTES_PER_INSTANCE = (2.5270e9 + 2.3306e9) / 16
 # k_mlp_wa on the learned-beam sample (one launch = one instance of 350 beams x
 # 50,013 live sources): 53.7 MB read + 500.0 MB written, summarised in
 # profiles/k_mlp_wa_learned_350beams_1e5src.txt.
