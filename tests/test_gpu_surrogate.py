@@ -242,6 +242,38 @@ def test_simulate_with_other_network_shapes(n_ant, cfg):
     assert rel_err(V[0, 0], Vo) <= 3e-2
 
 
+def test_surrogate_edge_cases():
+    # the learned beam with no live source (every instance's WA and V zero)
+    # and with one live source (a 32-source block holding one valid row)
+    w = workload(n_ant=12, n_src=2000)
+    sim = simulator(w)
+    sim.surrogate_create()
+    sim.surrogate_train(steps=100, batch=4096, lr0=2e-3, lr1=1e-4, seed=8)
+    net = oracle_net(sim, *grid_meta(w))
+    sim.set_beam_surrogate(True)
+    lst, f = float(w.lsts[0]), float(w.freqs[0])
+    sim.init_sky([0.0, 2.0], [np.pi / 3, np.pi / 3], [1.0, 3.0], nu_ref=w.nu_ref)  # never rises at HERA
+    V = sim.simulate([lst], [f], "fp16x3").cpu().numpy()
+    assert sim.last_live_counts(1)[0] == 0
+    assert np.all(V == 0)
+    ra, dec, flux = np.array([lst + 0.05]), np.array([w.lat + 0.1]), np.array([2.0])
+    sim.init_sky(ra, dec, flux, nu_ref=w.nu_ref)
+    V = sim.simulate([lst], [f], "fp16x3").cpu().numpy()[0, 0]
+    assert sim.last_live_counts(1)[0] == 1
+    P = oracle.Problem(ra=ra, dec=dec, flux_ref=flux, enu=w.enu, lat=w.lat, beam=("uniform",), nu_ref=w.nu_ref,
+                       beam_idx=w.beam_idx)
+
+    def beam_fn(az, za, nu):
+        n = az.size
+        out = np.empty((w.n_ant, 2, 2, n), dtype=np.complex128)
+        for b in range(w.n_ant):
+            y = mlp.forward(net, np.full(n, b), az, za, np.full(n, nu))
+            out[b] = (y[:, 0::2] + 1j * y[:, 1::2]).T.reshape(2, 2, n)
+        return out
+    Vo = oracle.vis_with_beam_fn(P, lst, f, beam_fn)
+    assert rel_err(V, Vo) <= 3e-2
+
+
 def test_surrogate_of_one_unpolarised_beam():
     # every antenna on one single-feed, single-axis gridded beam: the network
     # has one embedding row and 2 outputs (one complex gain), so a tile holds 1
