@@ -389,9 +389,10 @@ mv_status mv_surrogate_create(mv_ctx *ctx, const mv_mlp_config *cfg);
  * (step i draws the batch of counter i: beams stratified over the batch,
  * (az, za, nu) uniform, targets the gridded beams' Keys-cubic interpolation).
  * loss_first / loss_last (may be NULL) receive the MSE of the first and last
- * step.  The first call for a batch size of at least 12 steps times a few
- * splits of the SMs between the training launches and the sampler of the
- * next step (which runs beside them) over its first steps and keeps the
+ * step.  The first call for a batch size with enough steps (12; 15 when the
+ * batch takes more than four rounds of 128-row tiles on the SMs) times three
+ * or four splits of the SMs between the training launches and the sampler of
+ * the next step (which runs beside them) over its first steps and keeps the
  * fastest for that batch size.  Synchronises. */
 mv_status mv_surrogate_train(mv_ctx *ctx, int steps, int batch, float lr0, float lr1, uint64_t seed,
                              double *loss_first, double *loss_last);

@@ -885,7 +885,10 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
     // block does not fit beside a training CTA, so neither waits for the
     // other).  Candidate splits: the fewest SMs that walk the batch's 128-row
     // tiles in the fewest rounds (leaving at least 8 to the sampler), every SM
-    // but 8, and the fewest for one round more (more SMs for the sampler).
+    // but 8, the fewest for one round more (more SMs for the sampler), and the
+    // fewest for the rounds two thirds of the SMs take when that is over 4
+    // (the sampler's time grows with the batch over its SMs, so large batches
+    // balance near there).
     // With enough steps each runs three steps, the last two timed (their
     // samples drawn beside the same split), and the fastest stays (and is
     // kept for later calls with this batch size).
@@ -893,8 +896,10 @@ cudaError_t surrogate_train(Surrogate* S, const Model& m, const float2* grid, do
     const int most = std::max(1, S->n_sms - 8);
     auto split_for = [&](int rounds) { return std::min(most, std::max(1, (tiles + rounds - 1) / rounds)); };
     const int r0 = (tiles + most - 1) / most;
-    int cand[3], nc = 0;
-    for (int b : {split_for(r0), most, split_for(r0 + 1)}) {
+    const int two_thirds = std::max(1, 2 * S->n_sms / 3);
+    const int r23 = (tiles + two_thirds - 1) / two_thirds;
+    int cand[4], nc = 0;
+    for (int b : {split_for(r0), most, split_for(r0 + 1), r0 > 4 ? split_for(r23) : split_for(r0)}) {
         bool seen = false;
         for (int i = 0; i < nc; ++i) seen = seen || cand[i] == b;
         if (!seen) cand[nc++] = b;
